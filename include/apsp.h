@@ -1,0 +1,231 @@
+/*
+ * apsp.h -- C ABI of the GB300 warm-start all-pairs-shortest-path library.
+ *
+ * The library keeps the APSP matrix D of a dense weighted graph (directed or
+ * undirected, non-negative weights) resident in device memory and keeps it
+ * exact while the graph changes by one node or one edge at a time, following
+ * "Solving the all pairs shortest path problem after minor update of a large
+ * dense graph" (arXiv 2412.15122):
+ *
+ *   - adding a node: Corollary 1, Corollary 2 and Theorem 3 (Section 3.1);
+ *   - removing a node: the need_update_list of Section 3.2 (Theorem 4 /
+ *     Corollary 3), the Cost of Eq. (equ:cost_defi) and the warm/cold choice of
+ *     Algorithm 5;
+ *   - changing an edge weight: the result Algorithm 6 defines (the APSP
+ *     matrix of the graph with the new weight), computed by direct exact
+ *     formulas for decreases and by affected-pair detection plus restricted
+ *     re-relaxation for increases;
+ *   - cold recomputation: blocked min-plus Floyd-Warshall.
+ *
+ * Conventions shared by every call:
+ *   - Node ids are stable slot indices in [0, capacity).  At init slots
+ *     0..n-1 are live.  A removed node leaves a dead slot; a new node takes the
+ *     lowest dead slot, else the next never-used slot.
+ *   - Matrices passed in or out are dense row-major with a leading dimension
+ *     given in elements.  W[i][j] is the weight of edge i -> j.
+ *   - Element type is int32 (APSP_I32) or float (APSP_F32), chosen at init.
+ *     A missing edge / unreachable pair is APSP_INF_I32 (int32) or +infinity
+ *     (float).  Int32 inputs >= APSP_INF_I32 are read as missing.  Weights must
+ *     be >= 0 (Section 1: w maps edges to non-negative reals), else
+ *     APSP_E_NEGATIVE; NaN is APSP_E_ARG.  Int32 callers must keep every finite
+ *     shortest-path length below APSP_INF_I32; longer sums saturate to it.
+ *   - Host buffers are owned by the caller and only read (or written) during
+ *     the call.  All device memory is owned by the library and freed by
+ *     apsp_destroy.
+ *   - Every call on one handle is ordered on the handle's CUDA stream and
+ *     returns once the work is enqueued; calls that return data to the host
+ *     (apsp_query*, apsp_copy_*, apsp_last_stats, apsp_sync) wait for it.
+ *     A handle must not be used from two host threads at once; different
+ *     handles may be used concurrently.
+ *   - Errors are status codes, never exceptions.  A failure detected by a
+ *     kernel (for example a bounded wait that timed out, or invalid weights
+ *     passed as device pointers) is recorded on the device and returned by
+ *     the next call that waits for the stream.
+ */
+#ifndef APSP_H
+#define APSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct apsp_graph apsp_graph;
+
+typedef enum { APSP_I32 = 0, APSP_F32 = 1 } apsp_dtype;
+
+/* init flags */
+enum {
+    APSP_DIRECTED = 0u,
+    APSP_UNDIRECTED = 1u,     /* W must be symmetric; every update keeps D symmetric */
+    APSP_D_GIVEN = 4u,        /* D_or_null holds the APSP matrix of W (trusted, not recomputed) */
+    APSP_DEVICE_INPUT = 8u    /* W / D_or_null are device pointers */
+};
+
+typedef enum {
+    APSP_OK = 0,
+    APSP_E_ARG = 1,          /* bad argument (null pointer, bad size, NaN, u == v, ...) */
+    APSP_E_NODE = 2,         /* node id out of range or not live */
+    APSP_E_NEGATIVE = 3,     /* a negative weight */
+    APSP_E_CAPACITY = 4,     /* no free slot for a new node */
+    APSP_E_NOMEM = 5,        /* device or pinned host allocation failed */
+    APSP_E_CUDA = 6,         /* a CUDA runtime error */
+    APSP_E_TIMEOUT = 7,      /* a bounded device-side wait gave up; D may be stale */
+    APSP_E_BUSY = 8,         /* resource in use */
+    APSP_E_UNSUPPORTED = 9   /* configuration not supported by this build */
+} apsp_status;
+
+#define APSP_INF_I32 0x3FFFFFFF
+/* Largest capacity: one row of D plus per-row scratch must fit the 227 KB of
+ * shared memory of one CTA. */
+#define APSP_MAX_CAPACITY 18432
+
+/* What the last update did (apsp_last_stats). */
+typedef enum {
+    APSP_OP_NONE = 0, APSP_OP_INIT = 1, APSP_OP_ADD = 2, APSP_OP_REMOVE = 3,
+    APSP_OP_DECREASE = 4, APSP_OP_INCREASE = 5, APSP_OP_SAME = 6, APSP_OP_RECOMPUTE = 7
+} apsp_op;
+
+typedef enum {
+    APSP_PATH_NONE = 0,      /* no D work (weight unchanged) */
+    APSP_PATH_SWEEP = 1,     /* O(n^2) (or smaller) relaxation sweep, no affected set */
+    APSP_PATH_TRIVIAL = 2,   /* detection found no affected pair (e.g. non-tight edge) */
+    APSP_PATH_WARM = 3,      /* affected pairs re-relaxed */
+    APSP_PATH_COLD = 4       /* full blocked Floyd-Warshall */
+} apsp_path;
+
+/* warm/cold dispatch for node removal and edge increase */
+typedef enum {
+    APSP_DISPATCH_DELTA = 0,        /* Algorithm 5's rule: cold iff Cost > delta */
+    APSP_DISPATCH_ALWAYS_WARM = 1,
+    APSP_DISPATCH_ALWAYS_COLD = 2,
+    APSP_DISPATCH_MODEL = 3         /* learned cost model (apsp_set_model); falls back to DELTA without one */
+} apsp_dispatch;
+
+typedef struct {
+    int32_t op;               /* apsp_op */
+    int32_t path;             /* apsp_path */
+    int32_t node;             /* node added / removed, or edge source */
+    int32_t node2;            /* edge target, else -1 */
+    int32_t n_live;           /* live nodes after the update */
+    int32_t affected_rows;    /* non-empty items of need_update_list (Section 3.2) */
+    int64_t affected_pairs;   /* pairs re-relaxed */
+    int32_t sweep_rows;       /* rows touched by a relaxation sweep */
+    int32_t passes;           /* re-relaxation passes until no pair changed */
+    int32_t overflow;         /* 1 if the affected set exceeded the scratch capacity (forces cold) */
+    int32_t cold_reason;      /* 0 warm, 1 Cost rule, 2 model, 3 forced, 4 overflow */
+    float cost;               /* Cost = affected_rows / (N - 1), Eq. (equ:cost_defi) */
+    float model_warm;         /* model's predicted log2 microseconds, warm / cold (0 if unused) */
+    float model_cold;
+} apsp_stats;
+
+typedef struct {
+    int32_t n_live, n_slots, capacity, ld;  /* n_slots = 1 + highest slot ever used */
+    int32_t dtype;                          /* apsp_dtype */
+    uint32_t flags;
+    int64_t device_bytes;                   /* device memory held by the handle */
+} apsp_info;
+
+/* ----- lifecycle ------------------------------------------------------- */
+
+/* Create a graph of n live nodes (slots 0..n-1) with room for `capacity`
+ * slots (n <= capacity <= APSP_MAX_CAPACITY).  W: n x n, row-major, leading
+ * dimension n, host memory unless APSP_DEVICE_INPUT; its diagonal is ignored
+ * (read as 0).  D is computed by blocked Floyd-Warshall on the device, or
+ * taken from D_or_null when APSP_D_GIVEN is set.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream); every later call on the
+ * handle runs on it.  On success *g owns its device memory until
+ * apsp_destroy. */
+apsp_status apsp_init(apsp_graph **g, const void *W, int32_t n, int32_t capacity,
+                      apsp_dtype dtype, uint32_t flags, const void *D_or_null,
+                      void *cuda_stream);
+apsp_status apsp_destroy(apsp_graph *g);
+
+/* Optional: route the library's device allocations through a caller's
+ * allocator (for example a framework's caching allocator).  Affects handles
+ * created afterwards.  Pass NULLs to restore cudaMalloc / cudaFree. */
+typedef void *(*apsp_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*apsp_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+apsp_status apsp_set_allocator(apsp_alloc_fn alloc, apsp_free_fn free_fn, void *ctx);
+
+/* ----- updates (Sections 3.1-3.3) ---------------------------------------- */
+
+/* Add a node p (Section 3.1; Corollaries 1, 2, Theorem 3).  in_w[t] is the
+ * weight of edge t -> p and out_w[t] of p -> t, both arrays of `capacity`
+ * elements indexed by slot, host memory; entries at dead slots and at p are
+ * ignored.  Undirected graphs: in_w may be NULL or must equal out_w.  The
+ * new node's slot is written to *new_id. */
+apsp_status apsp_add_node(apsp_graph *g, const void *in_w, const void *out_w, int32_t *new_id);
+/* Same with in_w / out_w in device memory (read on the stream). */
+apsp_status apsp_add_node_device(apsp_graph *g, const void *in_w, const void *out_w, int32_t *new_id);
+
+/* Remove node v (Section 3.2, Algorithm 5): detect the need_update_list,
+ * compute Cost, then re-relax the listed pairs (warm) or recompute D by
+ * Floyd-Warshall (cold), as the dispatch mode decides on the device. */
+apsp_status apsp_remove_node(apsp_graph *g, int32_t v);
+
+/* Set the weight of edge u -> v (and v -> u for undirected graphs) to *w
+ * (host pointer to one element of the graph's dtype; APSP_INF_I32 / +inf
+ * deletes the edge).  The result is the APSP matrix of the modified graph,
+ * the quantity Algorithm 6 (Section 3.3) computes. */
+apsp_status apsp_update_edge(apsp_graph *g, int32_t u, int32_t v, const void *w);
+
+/* Recompute D from the current weights by blocked Floyd-Warshall (the cold
+ * path, also used as the comparison baseline). */
+apsp_status apsp_recompute(apsp_graph *g);
+
+/* ----- queries ------------------------------------------------------------ */
+
+/* Distance u -> v into *dist_out (host, one element of the dtype).  Waits. */
+apsp_status apsp_query(apsp_graph *g, int32_t u, int32_t v, void *dist_out);
+/* count distances: pairs uv[2*i], uv[2*i+1] (host int32), results into out
+ * (host, count elements).  Waits. */
+apsp_status apsp_query_batch(apsp_graph *g, const int32_t *uv, int32_t count, void *out);
+
+/* Copy the n_slots x n_slots top-left block of D (or W) to dst with leading
+ * dimension ld_dst (elements); dst is device memory if dst_on_device, else
+ * host.  Dead slots read as missing.  Waits. */
+apsp_status apsp_copy_D(apsp_graph *g, void *dst, int64_t ld_dst, int32_t dst_on_device);
+apsp_status apsp_copy_W(apsp_graph *g, void *dst, int64_t ld_dst, int32_t dst_on_device);
+/* alive[s] = 1 for a live slot s, 0 otherwise; `capacity` bytes, host. */
+apsp_status apsp_copy_alive(apsp_graph *g, uint8_t *alive);
+
+apsp_status apsp_info_get(apsp_graph *g, apsp_info *info);
+/* Statistics of the last update.  Waits. */
+apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *stats);
+/* Wait for all work on the handle's stream; returns any deferred device error. */
+apsp_status apsp_sync(apsp_graph *g);
+
+/* ----- dispatch ----------------------------------------------------------- */
+
+/* Choose how removals and edge increases pick warm or cold (default:
+ * APSP_DISPATCH_DELTA with delta = 1.0, i.e. cold only when the affected set
+ * overflows the scratch capacity). */
+apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta);
+
+/* ----- instrumentation ---------------------------------------------------- */
+
+/* Number of kernels this handle has launched so far. */
+int64_t apsp_launch_count(apsp_graph *g);
+/* When on, every kernel launch is bracketed by CUDA events on the handle's
+ * stream and its time is accumulated per kernel name. */
+apsp_status apsp_profile_enable(apsp_graph *g, int32_t on);
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} apsp_profile_entry;
+/* Waits, then copies up to cap entries; *count = number of distinct kernels. */
+apsp_status apsp_profile_read(apsp_graph *g, apsp_profile_entry *out, int32_t cap, int32_t *count);
+apsp_status apsp_profile_reset(apsp_graph *g);
+
+const char *apsp_status_string(apsp_status s);
+/* Library version, e.g. "0.1.0". */
+const char *apsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APSP_H */

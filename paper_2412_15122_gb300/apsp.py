@@ -1,0 +1,392 @@
+"""Python binding of the C ABI in include/apsp.h (ctypes, marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+compute of its own: it converts numpy arrays / torch tensors to pointers,
+checks the returned status and raises ``ApspError`` on failure.  The CUDA
+library must have been built (``paper_2412_15122_gb300.build.build()``);
+loading fails loudly otherwise.
+
+``Graph`` is a small object wrapper over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapsp_gb300.so")
+
+APSP_I32, APSP_F32 = 0, 1
+APSP_DIRECTED, APSP_UNDIRECTED, APSP_D_GIVEN, APSP_DEVICE_INPUT = 0, 1, 4, 8
+APSP_INF_I32 = 0x3FFFFFFF
+APSP_MAX_CAPACITY = 18432
+
+STATUS = {0: "APSP_OK", 1: "APSP_E_ARG", 2: "APSP_E_NODE", 3: "APSP_E_NEGATIVE", 4: "APSP_E_CAPACITY",
+          5: "APSP_E_NOMEM", 6: "APSP_E_CUDA", 7: "APSP_E_TIMEOUT", 8: "APSP_E_BUSY", 9: "APSP_E_UNSUPPORTED"}
+OPS = {0: "none", 1: "init", 2: "add", 3: "remove", 4: "decrease", 5: "increase", 6: "same", 7: "recompute"}
+PATHS = {0: "none", 1: "sweep", 2: "trivial", 3: "warm", 4: "cold"}
+DISPATCH = {"delta": 0, "warm": 1, "cold": 2, "model": 3}
+
+
+class ApspError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_status_string(status)})")
+
+
+class apsp_stats(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("path", ctypes.c_int32), ("node", ctypes.c_int32),
+                ("node2", ctypes.c_int32), ("n_live", ctypes.c_int32), ("affected_rows", ctypes.c_int32),
+                ("affected_pairs", ctypes.c_int64), ("sweep_rows", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("overflow", ctypes.c_int32), ("cold_reason", ctypes.c_int32), ("cost", ctypes.c_float),
+                ("model_warm", ctypes.c_float), ("model_cold", ctypes.c_float)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["op"] = OPS.get(self.op, self.op)
+        d["path"] = PATHS.get(self.path, self.path)
+        return d
+
+
+class apsp_info(ctypes.Structure):
+    _fields_ = [("n_live", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("capacity", ctypes.c_int32),
+                ("ld", ctypes.c_int32), ("dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class apsp_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"the CUDA library {LIB_PATH} is not built; run paper_2412_15122_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "apsp_init": [ctypes.POINTER(P), P, I32, I32, I32, U32, P, P],
+        "apsp_destroy": [P],
+        "apsp_set_allocator": [ALLOC_FN, FREE_FN, P],
+        "apsp_add_node": [P, P, P, ctypes.POINTER(I32)],
+        "apsp_add_node_device": [P, P, P, ctypes.POINTER(I32)],
+        "apsp_remove_node": [P, I32],
+        "apsp_update_edge": [P, I32, I32, P],
+        "apsp_recompute": [P],
+        "apsp_query": [P, I32, I32, P],
+        "apsp_query_batch": [P, P, I32, P],
+        "apsp_copy_D": [P, P, I64, I32],
+        "apsp_copy_W": [P, P, I64, I32],
+        "apsp_copy_alive": [P, P],
+        "apsp_info_get": [P, ctypes.POINTER(apsp_info)],
+        "apsp_last_stats": [P, ctypes.POINTER(apsp_stats)],
+        "apsp_sync": [P],
+        "apsp_set_dispatch": [P, I32, ctypes.c_double],
+        "apsp_profile_enable": [P, I32],
+        "apsp_profile_read": [P, ctypes.POINTER(apsp_profile_entry), I32, ctypes.POINTER(I32)],
+        "apsp_profile_reset": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.apsp_launch_count.argtypes = [P]
+    lib.apsp_launch_count.restype = I64
+    lib.apsp_status_string.argtypes = [ctypes.c_int]
+    lib.apsp_status_string.restype = ctypes.c_char_p
+    lib.apsp_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def lib():
+    return _load()
+
+
+def _status_string(s: int) -> str:
+    try:
+        return _load().apsp_status_string(s).decode()
+    except Exception:
+        return "?"
+
+
+def _check(s: int, where: str):
+    if s != 0:
+        raise ApspError(s, where)
+
+
+def _np_dtype(dtype: int):
+    return np.float32 if dtype == APSP_F32 else np.int32
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---------------------------------------------------------------------------
+# one function per C entry point
+# ---------------------------------------------------------------------------
+
+def apsp_status_string(s: int) -> str:
+    return _status_string(s)
+
+
+def apsp_version() -> str:
+    return _load().apsp_version().decode()
+
+
+def apsp_init(W, n: int, capacity: int, dtype: int, flags: int = 0, D=None, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(_load().apsp_init(ctypes.byref(h), _ptr(W), n, capacity, dtype, flags, _ptr(D), _stream_ptr(stream)),
+           "apsp_init")
+    return h.value
+
+
+def apsp_destroy(g: int):
+    _check(_load().apsp_destroy(g), "apsp_destroy")
+
+
+def apsp_add_node(g: int, in_w, out_w) -> int:
+    nid = ctypes.c_int32()
+    _check(_load().apsp_add_node(g, _ptr(in_w), _ptr(out_w), ctypes.byref(nid)), "apsp_add_node")
+    return nid.value
+
+
+def apsp_add_node_device(g: int, in_w, out_w) -> int:
+    nid = ctypes.c_int32()
+    _check(_load().apsp_add_node_device(g, _ptr(in_w), _ptr(out_w), ctypes.byref(nid)), "apsp_add_node_device")
+    return nid.value
+
+
+def apsp_remove_node(g: int, v: int):
+    _check(_load().apsp_remove_node(g, v), "apsp_remove_node")
+
+
+def apsp_update_edge(g: int, u: int, v: int, w, dtype: int):
+    buf = np.array([w], dtype=_np_dtype(dtype))
+    _check(_load().apsp_update_edge(g, u, v, buf.ctypes.data), "apsp_update_edge")
+
+
+def apsp_recompute(g: int):
+    _check(_load().apsp_recompute(g), "apsp_recompute")
+
+
+def apsp_query(g: int, u: int, v: int, dtype: int):
+    buf = np.zeros(1, dtype=_np_dtype(dtype))
+    _check(_load().apsp_query(g, u, v, buf.ctypes.data), "apsp_query")
+    return buf[0]
+
+
+def apsp_query_batch(g: int, uv: np.ndarray, dtype: int) -> np.ndarray:
+    uv = np.ascontiguousarray(uv, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros(len(uv), dtype=_np_dtype(dtype))
+    _check(_load().apsp_query_batch(g, uv.ctypes.data, len(uv), out.ctypes.data), "apsp_query_batch")
+    return out
+
+
+def apsp_copy_D(g: int, dst, ld: int, on_device: bool):
+    _check(_load().apsp_copy_D(g, _ptr(dst), ld, 1 if on_device else 0), "apsp_copy_D")
+
+
+def apsp_copy_W(g: int, dst, ld: int, on_device: bool):
+    _check(_load().apsp_copy_W(g, _ptr(dst), ld, 1 if on_device else 0), "apsp_copy_W")
+
+
+def apsp_copy_alive(g: int, capacity: int) -> np.ndarray:
+    out = np.zeros(capacity, dtype=np.uint8)
+    _check(_load().apsp_copy_alive(g, out.ctypes.data), "apsp_copy_alive")
+    return out.astype(bool)
+
+
+def apsp_info_get(g: int) -> dict:
+    i = apsp_info()
+    _check(_load().apsp_info_get(g, ctypes.byref(i)), "apsp_info_get")
+    return {k: getattr(i, k) for k, _ in i._fields_}
+
+
+def apsp_last_stats(g: int) -> dict:
+    s = apsp_stats()
+    _check(_load().apsp_last_stats(g, ctypes.byref(s)), "apsp_last_stats")
+    return s.as_dict()
+
+
+def apsp_sync(g: int):
+    _check(_load().apsp_sync(g), "apsp_sync")
+
+
+def apsp_set_dispatch(g: int, mode, delta: float = 1.0):
+    m = DISPATCH[mode] if isinstance(mode, str) else int(mode)
+    _check(_load().apsp_set_dispatch(g, m, float(delta)), "apsp_set_dispatch")
+
+
+def apsp_launch_count(g: int) -> int:
+    return int(_load().apsp_launch_count(g))
+
+
+def apsp_profile_enable(g: int, on: bool):
+    _check(_load().apsp_profile_enable(g, 1 if on else 0), "apsp_profile_enable")
+
+
+def apsp_profile_read(g: int) -> dict:
+    cap = 64
+    arr = (apsp_profile_entry * cap)()
+    cnt = ctypes.c_int32()
+    _check(_load().apsp_profile_read(g, arr, cap, ctypes.byref(cnt)), "apsp_profile_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(cnt.value, cap))}
+
+
+def apsp_profile_reset(g: int):
+    _check(_load().apsp_profile_reset(g), "apsp_profile_reset")
+
+
+_torch_alloc_refs = None
+
+
+def apsp_set_allocator_torch():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_alloc_refs
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _torch_alloc_refs = (a, f)
+    _check(_load().apsp_set_allocator(a, f, None), "apsp_set_allocator")
+
+
+def apsp_set_allocator_default():
+    global _torch_alloc_refs
+    _check(_load().apsp_set_allocator(ALLOC_FN(0), FREE_FN(0), None), "apsp_set_allocator")
+    _torch_alloc_refs = None
+
+
+# ---------------------------------------------------------------------------
+# object wrapper
+# ---------------------------------------------------------------------------
+
+class Graph:
+    """A device-resident graph and its APSP matrix (one C handle)."""
+
+    def __init__(self, W, capacity: Optional[int] = None, *, undirected: bool = False, D=None,
+                 stream=None, device_input: bool = False):
+        n = int(W.shape[0])
+        if hasattr(W, "dtype") and str(W.dtype) in ("float32", "torch.float32"):
+            self.dtype = APSP_F32
+        else:
+            self.dtype = APSP_I32
+        flags = (APSP_UNDIRECTED if undirected else 0) | (APSP_D_GIVEN if D is not None else 0) | \
+            (APSP_DEVICE_INPUT if device_input else 0)
+        self.capacity = int(capacity or n)
+        self.undirected = undirected
+        self.np_dtype = _np_dtype(self.dtype)
+        if not device_input:
+            W = np.ascontiguousarray(W, dtype=self.np_dtype)
+            if D is not None:
+                D = np.ascontiguousarray(D, dtype=self.np_dtype)
+        self.h = apsp_init(W, n, self.capacity, self.dtype, flags, D, stream)
+
+    def close(self):
+        if self.h:
+            apsp_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # updates
+    def add_node(self, in_w, out_w) -> int:
+        if hasattr(out_w, "data_ptr") and getattr(out_w, "is_cuda", False):
+            return apsp_add_node_device(self.h, in_w, out_w)
+        full_in = None if in_w is None else self._slot_vec(in_w)
+        return apsp_add_node(self.h, full_in, self._slot_vec(out_w))
+
+    def _slot_vec(self, w):
+        w = np.asarray(w, dtype=self.np_dtype)
+        if len(w) == self.capacity:
+            return np.ascontiguousarray(w)
+        out = np.full(self.capacity, self.inf, dtype=self.np_dtype)
+        out[:len(w)] = w
+        return out
+
+    def remove_node(self, v: int):
+        apsp_remove_node(self.h, v)
+
+    def update_edge(self, u: int, v: int, w):
+        apsp_update_edge(self.h, u, v, w, self.dtype)
+
+    def recompute(self):
+        apsp_recompute(self.h)
+
+    # queries
+    @property
+    def inf(self):
+        return np.float32(np.inf) if self.dtype == APSP_F32 else np.int32(APSP_INF_I32)
+
+    def query(self, u: int, v: int):
+        return apsp_query(self.h, u, v, self.dtype)
+
+    def query_batch(self, uv):
+        return apsp_query_batch(self.h, uv, self.dtype)
+
+    def info(self) -> dict:
+        return apsp_info_get(self.h)
+
+    def D(self) -> np.ndarray:
+        m = self.info()["n_slots"]
+        out = np.empty((m, m), dtype=self.np_dtype)
+        apsp_copy_D(self.h, out, m, False)
+        return out
+
+    def W(self) -> np.ndarray:
+        m = self.info()["n_slots"]
+        out = np.empty((m, m), dtype=self.np_dtype)
+        apsp_copy_W(self.h, out, m, False)
+        return out
+
+    def alive(self) -> np.ndarray:
+        return apsp_copy_alive(self.h, self.capacity)[: self.info()["n_slots"]]
+
+    def stats(self) -> dict:
+        return apsp_last_stats(self.h)
+
+    def sync(self):
+        apsp_sync(self.h)
+
+    def set_dispatch(self, mode, delta: float = 1.0):
+        apsp_set_dispatch(self.h, mode, delta)
+
+    def launches(self) -> int:
+        return apsp_launch_count(self.h)

@@ -1,0 +1,149 @@
+// Shared device-side definitions for the warm-start APSP kernels (sm_103a).
+//
+// Min-plus arithmetic for the two element types, the per-graph control
+// block that kernels use to pass counts and decisions along a stream without
+// host round trips, and a grid-wide barrier with a bounded wait for the
+// cooperative repair kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace apsp {
+
+constexpr int32_t INF_I32 = 0x3FFFFFFF;
+
+// Relative slack of the fp32 tightness test.  A pair whose stored distance
+// equals a path through the removed node / changed edge up to this relative
+// rounding error is treated as affected: a missed pair would keep a stale,
+// too-small distance, while an extra one only costs a recomputation.  2^-16
+// covers the rounding of sums along paths of up to 128 edges in fp32.
+constexpr float F32_TIGHT_REL = 1.0f / 65536.0f;
+
+template <typename T> struct MinPlus;
+
+template <> struct MinPlus<int32_t> {
+    using V4 = int4;
+    __host__ __device__ static constexpr int32_t inf() { return INF_I32; }
+    __device__ static bool finite(int32_t a) { return a < INF_I32; }
+    // a, b <= INF: a + b <= 2*INF fits in int32; saturate to INF.
+    __device__ static int32_t add(int32_t a, int32_t b) { return min(a + b, INF_I32); }
+    // min(a + b, c) for a, b, c <= INF.  Stays <= c <= INF.
+    __device__ static int32_t add_min(int32_t a, int32_t b, int32_t c) { return __viaddmin_s32(a, b, c); }
+    __device__ static int32_t mn(int32_t a, int32_t b) { return min(a, b); }
+    // `via` is the length of a path through the removed node / changed edge,
+    // `d` the stored distance (via >= d for an exact D): tight iff equal.
+    __device__ static bool tight(int32_t via, int32_t d) { return via <= d; }
+    // ordered bit pattern for atomicMin
+    __device__ static int32_t key(int32_t a) { return a; }
+    __device__ static int32_t unkey(int32_t a) { return a; }
+};
+
+template <> struct MinPlus<float> {
+    using V4 = float4;
+    __host__ __device__ static constexpr float inf() { return __builtin_huge_valf(); }
+    __device__ static bool finite(float a) { return a < inf(); }
+    __device__ static float add(float a, float b) { return a + b; }
+    __device__ static float add_min(float a, float b, float c) { return fminf(a + b, c); }
+    __device__ static float mn(float a, float b) { return fminf(a, b); }
+    __device__ static bool tight(float via, float d) { return via <= d + d * F32_TIGHT_REL; }
+    // non-negative floats (and +inf) order like their bit patterns as int32
+    __device__ static int32_t key(float a) { return __float_as_int(a); }
+    __device__ static float unkey(int32_t a) { return __int_as_float(a); }
+};
+
+template <typename V> __device__ __forceinline__ V ldcg4(const V *p) { return __ldcg(p); }
+
+// Error bits, OR-ed into Ctl::err by kernels and turned into an
+// apsp_status by the host at the next point where it waits for the stream.
+enum : uint32_t {
+    ERR_TIMEOUT = 1u,     // a bounded wait gave up
+    ERR_NEGATIVE = 2u,    // negative weight in device-side input
+    ERR_NAN = 4u,         // NaN in device-side input
+    ERR_NOT_SYMMETRIC = 8u,
+    ERR_PASSES = 16u      // re-relaxation did not settle within the pass cap
+};
+
+// Decision codes written by the repair kernel.
+enum : int32_t { PATH_NONE = 0, PATH_SWEEP = 1, PATH_TRIVIAL = 2, PATH_WARM = 3, PATH_COLD = 4 };
+
+// Per-graph control block in device memory.  Cleared (except `err`) before
+// each update; read back by the host only for statistics.
+struct Ctl {
+    // produced by the prepass / detection of the current update
+    int32_t r_count;          // rows in the prepass row list
+    int32_t n_rows;           // distinct affected rows (need_update_list items)
+    int32_t n_items;          // work items (row, up to ITEM_PAIRS pairs)
+    int32_t overflow;         // affected set did not fit the scratch
+    unsigned long long n_pairs;
+    int32_t n_live_before;    // N of Eq. (equ:cost_defi)
+    int32_t trivial;          // 1 when the edge was not tight (increase)
+    // produced by the repair kernel
+    int32_t path;
+    int32_t passes;
+    int32_t cold_reason;
+    float cost;
+    float model_warm, model_cold;
+    // grid barrier and pass bookkeeping of the repair kernel
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int32_t item_next[2];
+    int32_t changed[2];
+    int32_t stop;
+    int32_t pad_;
+    uint32_t err;             // sticky until the host reads it
+};
+
+constexpr int ITEM_PAIRS = 32;          // affected pairs per re-relaxation work item
+constexpr int MAX_PASSES = 48;          // path doubling needs <= log2(hops) + 1 passes
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperatively launched grid (all CTAs resident).
+// The last CTA to arrive runs `leader()` before releasing the others, so the
+// leader can publish decisions that every CTA reads after the barrier.  The
+// wait is bounded: after BARRIER_TIMEOUT_NS the CTA records ERR_TIMEOUT and
+// returns false; callers then leave the kernel.
+template <typename Leader>
+__device__ bool grid_barrier(Ctl *ctl, Leader leader) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *genp = &ctl->bar_gen;
+        unsigned int gen = *genp;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            leader();
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            unsigned int spins = 0;
+            while (*genp == gen) {
+                __nanosleep(64);
+                if ((++spins & 1023u) == 0 && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                    atomicOr(&ctl->err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (ok && (*(volatile uint32_t *)&ctl->err & ERR_TIMEOUT)) ok = 0;
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+struct NoLeader { __device__ void operator()() const {} };
+
+}  // namespace apsp

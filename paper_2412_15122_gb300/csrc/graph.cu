@@ -1,0 +1,761 @@
+// C ABI of the warm-start APSP library (declared in include/apsp.h).
+//
+// Owns the per-graph device state, the slot allocator, a host mirror of the
+// weight matrix (so an edge update knows its old weight without a device
+// round trip), pinned staging for host inputs, deferred device errors and
+// launch instrumentation.  All compute runs in the kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "apsp.h"
+#include "launch.h"
+
+using apsp::Ctl;
+using apsp::Dev;
+using apsp::LaunchCtx;
+using apsp::RepairCfg;
+
+namespace {
+
+apsp_alloc_fn g_alloc = nullptr;
+apsp_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct apsp_graph {
+    int dtype = APSP_I32;
+    uint32_t flags = 0;
+    bool undirected = false;
+    int n_live = 0, hwm = 0, cap = 0;
+    int64_t ld = 0;
+    size_t esz = 4;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 1;
+
+    // device state
+    void *W = nullptr, *D = nullptr, *DT = nullptr;
+    int32_t *alive = nullptr;
+    void *w_in = nullptr, *w_out = nullptr, *x = nullptr, *x2 = nullptr, *y = nullptr, *y2 = nullptr;
+    int32_t *vin_k = nullptr, *vout_k = nullptr, *rlist = nullptr, *pairs = nullptr;
+    int4 *items = nullptr;
+    Ctl *ctl = nullptr;
+    float *model = nullptr;
+    int64_t pair_cap = 0;
+    int32_t item_cap = 0;
+    apsp_alloc_fn alloc_fn = nullptr;
+    apsp_free_fn free_fn = nullptr;
+    void *alloc_ctx = nullptr;
+    std::vector<std::pair<void *, size_t>> allocs;
+    int64_t dev_bytes = 0;
+
+    // host side
+    std::vector<uint8_t> alive_h;
+    std::vector<char> Wh;        // cap x cap mirror of W
+    void *pin = nullptr;         // pinned: 2 * cap elements (add_node staging)
+    cudaEvent_t pin_ev = nullptr;
+    bool pin_pending = false;
+    void *pin_fetch = nullptr;   // pinned: 2 * cap elements (mirror of device-input adds)
+    cudaEvent_t fetch_ev = nullptr;
+    int fetch_pending_p = -1;
+    void *pin_small = nullptr;   // pinned scratch for queries / control block
+    int64_t pin_small_bytes = 0;
+
+    // dispatch
+    int mode = APSP_DISPATCH_DELTA;
+    float delta = 1.0f;
+    bool has_model = false;
+
+    apsp_stats last{};
+    LaunchCtx lc;
+
+    // instrumentation
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    cudaEvent_t cur_a = nullptr;
+    std::map<std::string, std::pair<int64_t, double>> prof_acc;
+};
+
+namespace {
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int span_of(const apsp_graph *g) { return (int)std::min<int64_t>(round_up(std::max(g->hwm, 1), 32), g->ld); }
+
+cudaEvent_t take_event(apsp_graph *g) {
+    if (!g->ev_pool.empty()) {
+        cudaEvent_t e = g->ev_pool.back();
+        g->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void flush_profile(apsp_graph *g) {
+    if (g->pending.empty()) return;
+    cudaStreamSynchronize(g->stream);
+    for (auto &r : g->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &acc = g->prof_acc[r.name];
+        acc.first += 1;
+        acc.second += ms;
+        g->ev_pool.push_back(r.a);
+        g->ev_pool.push_back(r.b);
+    }
+    g->pending.clear();
+}
+
+void hook_pre(void *ctx, const char *) {
+    apsp_graph *g = (apsp_graph *)ctx;
+    g->launches++;
+    if (g->prof) {
+        if (g->pending.size() > 8192) flush_profile(g);
+        g->cur_a = take_event(g);
+        cudaEventRecord(g->cur_a, g->stream);
+    }
+}
+
+void hook_post(void *ctx, const char *name) {
+    apsp_graph *g = (apsp_graph *)ctx;
+    if (g->prof) {
+        cudaEvent_t b = take_event(g);
+        cudaEventRecord(b, g->stream);
+        g->pending.push_back({name, g->cur_a, b});
+    }
+}
+
+apsp_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return APSP_OK;
+    if (e == cudaErrorMemoryAllocation) return APSP_E_NOMEM;
+    return APSP_E_CUDA;
+}
+
+void *dalloc(apsp_graph *g, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (g->alloc_fn) {
+        p = g->alloc_fn(bytes, (void *)g->stream, g->alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) {
+        g->allocs.push_back({p, bytes});
+        g->dev_bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+void release(apsp_graph *g) {
+    cudaStreamSynchronize(g->stream);
+    for (auto &a : g->allocs) {
+        if (g->free_fn) g->free_fn(a.first, a.second, (void *)g->stream, g->alloc_ctx);
+        else cudaFree(a.first);
+    }
+    g->allocs.clear();
+    if (g->pin) cudaFreeHost(g->pin);
+    if (g->pin_fetch) cudaFreeHost(g->pin_fetch);
+    if (g->pin_small) cudaFreeHost(g->pin_small);
+    if (g->pin_ev) cudaEventDestroy(g->pin_ev);
+    if (g->fetch_ev) cudaEventDestroy(g->fetch_ev);
+    for (auto &r : g->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : g->ev_pool) cudaEventDestroy(e);
+}
+
+// Reads the control block (waiting for the stream) and turns a sticky device
+// error into a status; clears it.
+apsp_status sync_ctl(apsp_graph *g, Ctl *out) {
+    Ctl *h = (Ctl *)g->pin_small;
+    cudaError_t e = cudaMemcpyAsync(h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (out) *out = *h;
+    uint32_t err = h->err;
+    if (err) {
+        cudaMemsetAsync(&g->ctl->err, 0, sizeof(uint32_t), g->stream);
+        cudaStreamSynchronize(g->stream);
+        if (err & apsp::ERR_TIMEOUT) return APSP_E_TIMEOUT;
+        if (err & apsp::ERR_PASSES) return APSP_E_TIMEOUT;
+        if (err & apsp::ERR_NEGATIVE) return APSP_E_NEGATIVE;
+        return APSP_E_ARG;
+    }
+    return APSP_OK;
+}
+
+template <typename T> Dev<T> dev_of(apsp_graph *g) {
+    Dev<T> d;
+    d.W = (T *)g->W;
+    d.D = (T *)g->D;
+    d.DT = (T *)g->DT;
+    d.ld = g->ld;
+    d.span = span_of(g);
+    d.undirected = g->undirected ? 1 : 0;
+    d.alive = g->alive;
+    d.w_in = (T *)g->w_in;
+    d.w_out = (T *)g->w_out;
+    d.vin_k = g->vin_k;
+    d.vout_k = g->vout_k;
+    d.x = (T *)g->x;
+    d.x2 = (T *)g->x2;
+    d.y = (T *)g->y;
+    d.y2 = (T *)g->y2;
+    d.rlist = g->rlist;
+    d.items = g->items;
+    d.pairs = g->pairs;
+    d.ctl = g->ctl;
+    d.pair_cap = g->pair_cap;
+    d.item_cap = g->item_cap;
+    return d;
+}
+
+cudaError_t reset_ctl(apsp_graph *g) {
+    return cudaMemsetAsync(g->ctl, 0, offsetof(Ctl, err), g->stream);
+}
+
+template <typename T> T inf_of() { return (T)apsp::MinPlus<T>::inf(); }
+
+// Host-side check of a weight; returns 0 ok, else a status.  Int32 values
+// above INF are clamped to INF (missing).
+template <typename T> apsp_status check_weight(T &w) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (std::isnan(w)) return APSP_E_ARG;
+        if (w < 0.f) return APSP_E_NEGATIVE;
+        if (w == 0.f) w = 0.f;
+    } else {
+        if (w < 0) return APSP_E_NEGATIVE;
+        if (w > apsp::INF_I32) w = apsp::INF_I32;
+    }
+    return APSP_OK;
+}
+
+template <typename T> T &mirror(apsp_graph *g, int i, int j) { return ((T *)g->Wh.data())[(int64_t)i * g->cap + j]; }
+
+// Applies a pending device-input add_node to the host mirror (waits for the
+// small D2H copy of its weight vectors only).
+template <typename T> void settle_fetch(apsp_graph *g) {
+    if (g->fetch_pending_p < 0) return;
+    cudaEventSynchronize(g->fetch_ev);
+    const int p = g->fetch_pending_p;
+    const T *in = (const T *)g->pin_fetch;
+    const T *out = in + g->cap;
+    for (int t = 0; t < g->cap; ++t) {
+        T wi = inf_of<T>(), wo = inf_of<T>();
+        if (t != p && g->alive_h[t]) {
+            wi = in[t];
+            wo = out[t];
+            if (check_weight<T>(wi) != APSP_OK || check_weight<T>(wo) != APSP_OK) wi = wo = inf_of<T>();
+        }
+        mirror<T>(g, t, p) = wi;
+        mirror<T>(g, p, t) = wo;
+    }
+    mirror<T>(g, p, p) = (T)0;
+    g->fetch_pending_p = -1;
+}
+
+template <typename T> RepairCfg repair_cfg(apsp_graph *g, int n_before, float type_feat, float dw) {
+    RepairCfg c;
+    c.mode = g->mode;
+    c.delta = g->delta;
+    c.n_live_before = n_before;
+    c.has_model = g->has_model ? 1 : 0;
+    c.model = g->model;
+    c.feat_type = type_feat;
+    c.feat_dw = dw;
+    return c;
+}
+
+int pick_slot(apsp_graph *g) {
+    for (int s = 0; s < g->hwm; ++s)
+        if (!g->alive_h[s]) return s;
+    return g->hwm < g->cap ? g->hwm : -1;
+}
+
+// ---------------------------------------------------------------------------
+// typed implementations
+// ---------------------------------------------------------------------------
+
+template <typename T>
+apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
+    cudaError_t e;
+    const size_t esz = sizeof(T);
+    const int64_t ld = g->ld;
+    const size_t mat = (size_t)ld * ld * esz;
+    g->W = dalloc(g, mat);
+    g->D = dalloc(g, mat);
+    if (!g->undirected) g->DT = dalloc(g, mat);
+    g->alive = (int32_t *)dalloc(g, ld * 4);
+    g->w_in = dalloc(g, ld * esz);
+    g->w_out = dalloc(g, ld * esz);
+    g->x = dalloc(g, ld * esz);
+    g->x2 = dalloc(g, ld * esz);
+    g->y = dalloc(g, ld * esz);
+    g->y2 = dalloc(g, ld * esz);
+    g->vin_k = (int32_t *)dalloc(g, ld * 4);
+    g->vout_k = (int32_t *)dalloc(g, ld * 4);
+    g->rlist = (int32_t *)dalloc(g, ld * 4);
+    g->pair_cap = std::min<int64_t>((int64_t)ld * 512, (int64_t)1 << 30);
+    g->item_cap = (int32_t)(g->pair_cap / apsp::ITEM_PAIRS + ld);
+    g->pairs = (int32_t *)dalloc(g, g->pair_cap * 4);
+    g->items = (int4 *)dalloc(g, (size_t)g->item_cap * sizeof(int4));
+    g->ctl = (Ctl *)dalloc(g, sizeof(Ctl));
+    g->model = (float *)dalloc(g, apsp::MLP_NPARAM * sizeof(float));
+    if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
+        !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->ctl || !g->model)
+        return APSP_E_NOMEM;
+    if (cudaMallocHost(&g->pin, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
+    if (cudaMallocHost(&g->pin_fetch, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
+    g->pin_small_bytes = std::max<int64_t>(sizeof(Ctl), 1 << 16);
+    if (cudaMallocHost(&g->pin_small, g->pin_small_bytes) != cudaSuccess) return APSP_E_NOMEM;
+    cudaEventCreateWithFlags(&g->pin_ev, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&g->fetch_ev, cudaEventDisableTiming);
+
+    if ((e = apsp::setup_shapes<T>(g->lc, ld, g->undirected ? 1 : 0)) != cudaSuccess) return cuda_status(e);
+    const LaunchCtx &c = g->lc;
+    const T inf = inf_of<T>();
+    if ((e = apsp::run_fill<T>(c, (T *)g->W, inf, ld * ld)) != cudaSuccess) return cuda_status(e);
+    if ((e = apsp::run_fill<T>(c, (T *)g->D, inf, ld * ld)) != cudaSuccess) return cuda_status(e);
+    if (g->DT && (e = apsp::run_fill<T>(c, (T *)g->DT, inf, ld * ld)) != cudaSuccess) return cuda_status(e);
+    cudaMemsetAsync(g->alive, 0, ld * 4, g->stream);
+    cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream);
+    if (n > 0) apsp::run_fill<int32_t>(c, g->alive, 1, n);
+    const cudaMemcpyKind kind = (g->flags & APSP_DEVICE_INPUT) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n > 0) {
+        e = cudaMemcpy2DAsync(g->W, ld * esz, W, (size_t)n * esz, (size_t)n * esz, n, kind, g->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        apsp::run_sanitize<T>(c, (T *)g->W, ld, n, g->undirected ? 1 : 0, g->ctl);
+    }
+    g->hwm = n;
+    g->n_live = n;
+    Dev<T> d = dev_of<T>(g);
+    if ((g->flags & APSP_D_GIVEN) && n > 0) {
+        e = cudaMemcpy2DAsync(g->D, ld * esz, Dgiven, (size_t)n * esz, (size_t)n * esz, n, kind, g->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        apsp::run_sanitize<T>(c, (T *)g->D, ld, n, 0, g->ctl);
+        if ((e = apsp::run_transpose<T>(c, d)) != cudaSuccess) return cuda_status(e);
+    } else if (n > 0) {
+        if ((e = apsp::run_fw<T>(c, d)) != cudaSuccess) return cuda_status(e);
+    }
+    // host mirror of W
+    g->alive_h.assign(g->cap, 0);
+    for (int i = 0; i < n; ++i) g->alive_h[i] = 1;
+    g->Wh.assign((size_t)g->cap * g->cap * esz, 0);
+    {
+        T *wh = (T *)g->Wh.data();
+        std::fill(wh, wh + (size_t)g->cap * g->cap, inf);
+        if (n > 0) {
+            e = cudaMemcpy2DAsync(wh, (size_t)g->cap * esz, g->W, ld * esz, (size_t)n * esz, n, cudaMemcpyDeviceToHost, g->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    apsp_status st = sync_ctl(g, nullptr);
+    if (st != APSP_OK) return st;
+    g->last = apsp_stats{};
+    g->last.op = APSP_OP_INIT;
+    g->last.path = APSP_PATH_COLD;
+    g->last.node = g->last.node2 = -1;
+    g->last.n_live = n;
+    return APSP_OK;
+}
+
+template <typename T>
+apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t *new_id, bool device_input) {
+    if (!out_w || !new_id) return APSP_E_ARG;
+    if (!in_w) {
+        if (!g->undirected) return APSP_E_ARG;
+        in_w = out_w;
+    }
+    settle_fetch<T>(g);
+    const int p = pick_slot(g);
+    if (p < 0) return APSP_E_CAPACITY;
+    const int cap = g->cap;
+    const T *din, *dout;
+    if (!device_input) {
+        const T *hi = (const T *)in_w, *ho = (const T *)out_w;
+        for (int t = 0; t < cap; ++t) {
+            if (t == p || !g->alive_h[t]) continue;
+            T a = hi[t], b = ho[t];
+            apsp_status s1 = check_weight<T>(a), s2 = check_weight<T>(b);
+            if (s1 != APSP_OK) return s1;
+            if (s2 != APSP_OK) return s2;
+            if (g->undirected && !(a == b)) return APSP_E_ARG;
+        }
+        if (g->pin_pending) cudaEventSynchronize(g->pin_ev);
+        T *pin_in = (T *)g->pin, *pin_out = pin_in + cap;
+        std::memcpy(pin_in, hi, cap * sizeof(T));
+        std::memcpy(pin_out, ho, cap * sizeof(T));
+        cudaMemcpyAsync(g->x, pin_in, cap * sizeof(T), cudaMemcpyHostToDevice, g->stream);
+        cudaMemcpyAsync(g->y, pin_out, cap * sizeof(T), cudaMemcpyHostToDevice, g->stream);
+        cudaEventRecord(g->pin_ev, g->stream);
+        g->pin_pending = true;
+        din = (const T *)g->x;
+        dout = (const T *)g->y;
+        for (int t = 0; t < cap; ++t) {
+            T a = inf_of<T>(), b = inf_of<T>();
+            if (t != p && g->alive_h[t]) {
+                a = hi[t];
+                b = ho[t];
+                check_weight<T>(a);
+                check_weight<T>(b);
+            }
+            mirror<T>(g, t, p) = a;
+            mirror<T>(g, p, t) = b;
+        }
+        mirror<T>(g, p, p) = (T)0;
+    } else {
+        din = (const T *)in_w;
+        dout = (const T *)out_w;
+        T *f_in = (T *)g->pin_fetch;
+        cudaMemcpyAsync(f_in, din, cap * sizeof(T), cudaMemcpyDeviceToHost, g->stream);
+        cudaMemcpyAsync(f_in + cap, dout, cap * sizeof(T), cudaMemcpyDeviceToHost, g->stream);
+        cudaEventRecord(g->fetch_ev, g->stream);
+    }
+    g->hwm = std::max(g->hwm, p + 1);
+    reset_ctl(g);
+    Dev<T> d = dev_of<T>(g);
+    cudaError_t e = apsp::run_insert<T>(g->lc, d, din, dout, cap, p);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->alive_h[p] = 1;
+    g->n_live++;
+    if (device_input) g->fetch_pending_p = p;
+    *new_id = p;
+    g->last = apsp_stats{};
+    g->last.op = APSP_OP_ADD;
+    g->last.path = APSP_PATH_SWEEP;
+    g->last.node = p;
+    g->last.node2 = -1;
+    g->last.n_live = g->n_live;
+    return APSP_OK;
+}
+
+template <typename T> apsp_status remove_impl(apsp_graph *g, int v) {
+    settle_fetch<T>(g);
+    if (v < 0 || v >= g->cap || !g->alive_h[v]) return APSP_E_NODE;
+    reset_ctl(g);
+    Dev<T> d = dev_of<T>(g);
+    RepairCfg cfg = repair_cfg<T>(g, g->n_live, 1.0f / 3.0f, 0.0f);
+    cudaError_t e = apsp::run_remove<T>(g->lc, d, v, cfg);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->alive_h[v] = 0;
+    for (int t = 0; t < g->cap; ++t) {
+        mirror<T>(g, t, v) = inf_of<T>();
+        mirror<T>(g, v, t) = inf_of<T>();
+    }
+    g->n_live--;
+    g->last = apsp_stats{};
+    g->last.op = APSP_OP_REMOVE;
+    g->last.path = -1;  // decided on the device
+    g->last.node = v;
+    g->last.node2 = -1;
+    g->last.n_live = g->n_live;
+    return APSP_OK;
+}
+
+template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const void *wp) {
+    settle_fetch<T>(g);
+    if (!wp) return APSP_E_ARG;
+    if (u < 0 || v < 0 || u >= g->cap || v >= g->cap || !g->alive_h[u] || !g->alive_h[v]) return APSP_E_NODE;
+    if (u == v) return APSP_E_ARG;
+    T w = *(const T *)wp;
+    apsp_status s = check_weight<T>(w);
+    if (s != APSP_OK) return s;
+    const T w_old = mirror<T>(g, u, v);
+    g->last = apsp_stats{};
+    g->last.node = u;
+    g->last.node2 = v;
+    g->last.n_live = g->n_live;
+    if (w == w_old) {
+        g->last.op = APSP_OP_SAME;
+        g->last.path = APSP_PATH_NONE;
+        return APSP_OK;
+    }
+    reset_ctl(g);
+    Dev<T> d = dev_of<T>(g);
+    cudaError_t e;
+    if (w < w_old) {
+        e = apsp::run_decrease<T>(g->lc, d, u, v, w);
+        g->last.op = APSP_OP_DECREASE;
+        g->last.path = APSP_PATH_SWEEP;
+    } else {
+        float dw = (std::isfinite((double)w) && (double)w < apsp::INF_I32 && (double)w_old > 0)
+                       ? (float)(((double)w - (double)w_old) / (double)w_old) : 1.0f;
+        RepairCfg cfg = repair_cfg<T>(g, g->n_live, 1.0f, dw);
+        e = apsp::run_increase<T>(g->lc, d, u, v, w_old, w, cfg);
+        g->last.op = APSP_OP_INCREASE;
+        g->last.path = -1;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    mirror<T>(g, u, v) = w;
+    if (g->undirected) mirror<T>(g, v, u) = w;
+    return APSP_OK;
+}
+
+template <typename T> apsp_status recompute_impl(apsp_graph *g) {
+    settle_fetch<T>(g);
+    Dev<T> d = dev_of<T>(g);
+    cudaError_t e = apsp::run_fw<T>(g->lc, d);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->last = apsp_stats{};
+    g->last.op = APSP_OP_RECOMPUTE;
+    g->last.path = APSP_PATH_COLD;
+    g->last.node = g->last.node2 = -1;
+    g->last.n_live = g->n_live;
+    return APSP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *apsp_version(void) { return "0.1.0"; }
+
+const char *apsp_status_string(apsp_status s) {
+    switch (s) {
+    case APSP_OK: return "ok";
+    case APSP_E_ARG: return "invalid argument";
+    case APSP_E_NODE: return "node id out of range or not live";
+    case APSP_E_NEGATIVE: return "negative weight";
+    case APSP_E_CAPACITY: return "no free slot";
+    case APSP_E_NOMEM: return "out of memory";
+    case APSP_E_CUDA: return "CUDA error";
+    case APSP_E_TIMEOUT: return "bounded device wait timed out";
+    case APSP_E_BUSY: return "busy";
+    case APSP_E_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+apsp_status apsp_set_allocator(apsp_alloc_fn alloc, apsp_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return APSP_E_ARG;
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return APSP_OK;
+}
+
+apsp_status apsp_init(apsp_graph **out, const void *W, int32_t n, int32_t capacity, apsp_dtype dtype,
+                      uint32_t flags, const void *D_or_null, void *cuda_stream) {
+    if (!out) return APSP_E_ARG;
+    *out = nullptr;
+    if (n < 0 || capacity < 1 || n > capacity || capacity > APSP_MAX_CAPACITY) return APSP_E_ARG;
+    if (dtype != APSP_I32 && dtype != APSP_F32) return APSP_E_ARG;
+    if (flags & ~(uint32_t)(APSP_UNDIRECTED | APSP_D_GIVEN | APSP_DEVICE_INPUT)) return APSP_E_ARG;
+    if (n > 0 && !W) return APSP_E_ARG;
+    if ((flags & APSP_D_GIVEN) && !D_or_null) return APSP_E_ARG;
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1 || cudaGetDevice(&dev) != cudaSuccess) return APSP_E_CUDA;
+    apsp_graph *g = new apsp_graph();
+    g->dtype = dtype;
+    g->flags = flags;
+    g->undirected = (flags & APSP_UNDIRECTED) != 0;
+    g->cap = capacity;
+    g->ld = round_up(capacity, 128);
+    g->esz = 4;
+    g->stream = (cudaStream_t)cuda_stream;
+    g->alloc_fn = g_alloc;
+    g->free_fn = g_free;
+    g->alloc_ctx = g_alloc_ctx;
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    g->lc.stream = g->stream;
+    g->lc.num_sms = g->num_sms;
+    g->lc.hook = apsp::Hook{hook_pre, hook_post, g};
+    apsp_status st = dtype == APSP_F32 ? init_impl<float>(g, W, n, D_or_null) : init_impl<int32_t>(g, W, n, D_or_null);
+    if (st != APSP_OK) {
+        release(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return APSP_OK;
+}
+
+apsp_status apsp_destroy(apsp_graph *g) {
+    if (!g) return APSP_E_ARG;
+    release(g);
+    delete g;
+    return APSP_OK;
+}
+
+apsp_status apsp_add_node(apsp_graph *g, const void *in_w, const void *out_w, int32_t *new_id) {
+    if (!g) return APSP_E_ARG;
+    return g->dtype == APSP_F32 ? add_impl<float>(g, in_w, out_w, new_id, false) : add_impl<int32_t>(g, in_w, out_w, new_id, false);
+}
+
+apsp_status apsp_add_node_device(apsp_graph *g, const void *in_w, const void *out_w, int32_t *new_id) {
+    if (!g) return APSP_E_ARG;
+    return g->dtype == APSP_F32 ? add_impl<float>(g, in_w, out_w, new_id, true) : add_impl<int32_t>(g, in_w, out_w, new_id, true);
+}
+
+apsp_status apsp_remove_node(apsp_graph *g, int32_t v) {
+    if (!g) return APSP_E_ARG;
+    return g->dtype == APSP_F32 ? remove_impl<float>(g, v) : remove_impl<int32_t>(g, v);
+}
+
+apsp_status apsp_update_edge(apsp_graph *g, int32_t u, int32_t v, const void *w) {
+    if (!g) return APSP_E_ARG;
+    return g->dtype == APSP_F32 ? edge_impl<float>(g, u, v, w) : edge_impl<int32_t>(g, u, v, w);
+}
+
+apsp_status apsp_recompute(apsp_graph *g) {
+    if (!g) return APSP_E_ARG;
+    return g->dtype == APSP_F32 ? recompute_impl<float>(g) : recompute_impl<int32_t>(g);
+}
+
+apsp_status apsp_query(apsp_graph *g, int32_t u, int32_t v, void *dist_out) {
+    if (!g || !dist_out) return APSP_E_ARG;
+    if (u < 0 || v < 0 || u >= g->cap || v >= g->cap || !g->alive_h[u] || !g->alive_h[v]) return APSP_E_NODE;
+    char *h = (char *)g->pin_small + sizeof(Ctl);
+    cudaError_t e = cudaMemcpyAsync(h, (const char *)g->D + ((int64_t)u * g->ld + v) * g->esz, g->esz,
+                                    cudaMemcpyDeviceToHost, g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    apsp_status st = sync_ctl(g, nullptr);
+    std::memcpy(dist_out, h, g->esz);
+    return st;
+}
+
+apsp_status apsp_query_batch(apsp_graph *g, const int32_t *uv, int32_t count, void *out) {
+    if (!g || (count > 0 && (!uv || !out)) || count < 0) return APSP_E_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        int u = uv[2 * i], v = uv[2 * i + 1];
+        if (u < 0 || v < 0 || u >= g->cap || v >= g->cap || !g->alive_h[u] || !g->alive_h[v]) return APSP_E_NODE;
+    }
+    const int64_t room = (g->pin_small_bytes - (int64_t)sizeof(Ctl)) / (int64_t)g->esz;
+    char *h = (char *)g->pin_small + sizeof(Ctl);
+    for (int32_t b0 = 0; b0 < count; b0 += (int32_t)room) {
+        int32_t nb = (int32_t)std::min<int64_t>(room, count - b0);
+        for (int32_t i = 0; i < nb; ++i) {
+            int u = uv[2 * (b0 + i)], v = uv[2 * (b0 + i) + 1];
+            cudaMemcpyAsync(h + i * g->esz, (const char *)g->D + ((int64_t)u * g->ld + v) * g->esz, g->esz,
+                            cudaMemcpyDeviceToHost, g->stream);
+        }
+        apsp_status st = sync_ctl(g, nullptr);
+        if (st != APSP_OK) return st;
+        std::memcpy((char *)out + (size_t)b0 * g->esz, h, (size_t)nb * g->esz);
+    }
+    return APSP_OK;
+}
+
+static apsp_status copy_mat(apsp_graph *g, const void *src, void *dst, int64_t ld_dst, int32_t on_dev) {
+    if (!g || !dst || ld_dst < g->hwm) return APSP_E_ARG;
+    if (g->hwm > 0) {
+        cudaError_t e = cudaMemcpy2DAsync(dst, ld_dst * g->esz, src, g->ld * g->esz, (size_t)g->hwm * g->esz, g->hwm,
+                                          on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return sync_ctl(g, nullptr);
+}
+
+apsp_status apsp_copy_D(apsp_graph *g, void *dst, int64_t ld_dst, int32_t on_dev) { return g ? copy_mat(g, g->D, dst, ld_dst, on_dev) : APSP_E_ARG; }
+apsp_status apsp_copy_W(apsp_graph *g, void *dst, int64_t ld_dst, int32_t on_dev) { return g ? copy_mat(g, g->W, dst, ld_dst, on_dev) : APSP_E_ARG; }
+
+apsp_status apsp_copy_alive(apsp_graph *g, uint8_t *alive) {
+    if (!g || !alive) return APSP_E_ARG;
+    std::memcpy(alive, g->alive_h.data(), g->cap);
+    return APSP_OK;
+}
+
+apsp_status apsp_info_get(apsp_graph *g, apsp_info *info) {
+    if (!g || !info) return APSP_E_ARG;
+    info->n_live = g->n_live;
+    info->n_slots = g->hwm;
+    info->capacity = g->cap;
+    info->ld = (int32_t)g->ld;
+    info->dtype = g->dtype;
+    info->flags = g->flags;
+    info->device_bytes = g->dev_bytes;
+    return APSP_OK;
+}
+
+apsp_status apsp_sync(apsp_graph *g) {
+    if (!g) return APSP_E_ARG;
+    return sync_ctl(g, nullptr);
+}
+
+apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *s) {
+    if (!g || !s) return APSP_E_ARG;
+    Ctl c;
+    apsp_status st = sync_ctl(g, &c);
+    *s = g->last;
+    const int op = g->last.op;
+    if (op == APSP_OP_REMOVE || op == APSP_OP_INCREASE) {
+        s->affected_rows = c.n_rows;
+        s->affected_pairs = (int64_t)c.n_pairs;
+        s->overflow = c.overflow;
+        s->passes = c.passes;
+        s->cold_reason = c.cold_reason;
+        s->cost = c.cost;
+        s->model_warm = c.model_warm;
+        s->model_cold = c.model_cold;
+        s->sweep_rows = c.r_count;
+        s->path = c.path == apsp::PATH_COLD ? APSP_PATH_COLD
+                : c.path == apsp::PATH_WARM ? APSP_PATH_WARM : APSP_PATH_TRIVIAL;
+        if (op == APSP_OP_REMOVE && c.path == 0) s->path = APSP_PATH_TRIVIAL;
+    } else if (op == APSP_OP_DECREASE) {
+        s->sweep_rows = c.r_count;
+        s->path = c.r_count > 0 ? APSP_PATH_SWEEP : APSP_PATH_TRIVIAL;
+    }
+    return st;
+}
+
+apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta) {
+    if (!g || mode < APSP_DISPATCH_DELTA || mode > APSP_DISPATCH_MODEL || !(delta >= 0.0)) return APSP_E_ARG;
+    g->mode = mode;
+    g->delta = (float)delta;
+    return APSP_OK;
+}
+
+int64_t apsp_launch_count(apsp_graph *g) { return g ? g->launches : -1; }
+
+apsp_status apsp_profile_enable(apsp_graph *g, int32_t on) {
+    if (!g) return APSP_E_ARG;
+    g->prof = on != 0;
+    return APSP_OK;
+}
+
+apsp_status apsp_profile_read(apsp_graph *g, apsp_profile_entry *out, int32_t cap, int32_t *count) {
+    if (!g || !count || (cap > 0 && !out)) return APSP_E_ARG;
+    flush_profile(g);
+    int32_t i = 0;
+    for (auto &kv : g->prof_acc) {
+        if (i < cap) {
+            std::memset(&out[i], 0, sizeof(apsp_profile_entry));
+            std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = kv.second.first;
+            out[i].total_ms = kv.second.second;
+        }
+        ++i;
+    }
+    *count = i;
+    return APSP_OK;
+}
+
+apsp_status apsp_profile_reset(apsp_graph *g) {
+    if (!g) return APSP_E_ARG;
+    flush_profile(g);
+    g->prof_acc.clear();
+    return APSP_OK;
+}
+
+}  // extern "C"

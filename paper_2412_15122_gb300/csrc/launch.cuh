@@ -1,0 +1,132 @@
+// Host-side launch sequences for each update type.  Instantiated for int32
+// and float in kern_i32.cu / kern_f32.cu; graph.cu calls them through the
+// declarations in launch.h.
+#pragma once
+
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace apsp {
+
+template <typename F> static inline cudaError_t launch(const LaunchCtx &c, const char *name, F &&f) {
+    c.hook.begin(name);
+    f();
+    c.hook.end(name);
+    return cudaGetLastError();
+}
+
+static inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+template <typename T> cudaError_t run_fill(const LaunchCtx &c, T *p, T v, int64_t n) {
+    int g = (int)std::min<int64_t>(cdiv(n, 256), (int64_t)c.num_sms * 8);
+    if (g < 1) g = 1;
+    return launch(c, "fill", [&] { k_fill<T><<<g, 256, 0, c.stream>>>(p, v, n); });
+}
+
+template <typename T> cudaError_t run_sanitize(const LaunchCtx &c, T *M, int64_t ld, int n, int check_sym, Ctl *ctl) {
+    int g = std::max(1, (int)std::min<int64_t>(cdiv((int64_t)n * n, 256), (int64_t)c.num_sms * 8));
+    return launch(c, "sanitize", [&] { k_sanitize<T><<<g, 256, 0, c.stream>>>(M, ld, n, check_sym, ctl); });
+}
+
+template <typename T> cudaError_t run_transpose(const LaunchCtx &c, const Dev<T> &d) {
+    if (!d.DT) return cudaSuccess;
+    int tiles = d.span / 32;
+    int g = std::max(1, std::min(tiles * tiles, c.num_sms * 16));
+    return launch(c, "transpose", [&] { k_transpose<T><<<g, dim3(32, 8), 0, c.stream>>>(d.D, d.DT, d.ld, d.span); });
+}
+
+// Cold solver: D = W, then nb rounds of the three phases, then DT = D^T.
+template <typename T> cudaError_t run_fw(const LaunchCtx &c, const Dev<T> &d) {
+    const int nb = cdiv(d.span, FW_B);
+    cudaError_t e = cudaMemcpyAsync(d.D, d.W, (size_t)nb * FW_B * d.ld * sizeof(T), cudaMemcpyDeviceToDevice, c.stream);
+    if (e != cudaSuccess) return e;
+    for (int kb = 0; kb < nb; ++kb) {
+        if ((e = launch(c, "fw_phase1", [&] { k_fw_p1<T><<<1, FW_THREADS, 0, c.stream>>>(d.D, d.ld, kb); })) != cudaSuccess) return e;
+        if (nb == 1) break;
+        if ((e = launch(c, "fw_phase2", [&] { k_fw_p2<T><<<2 * (nb - 1), FW_THREADS, 0, c.stream>>>(d.D, d.ld, kb, nb); })) != cudaSuccess) return e;
+        if ((e = launch(c, "fw_phase3", [&] { k_fw_p3<T><<<(nb - 1) * (nb - 1), FW_THREADS, 0, c.stream>>>(d.D, d.ld, kb, nb); })) != cudaSuccess) return e;
+    }
+    return run_transpose<T>(c, d);
+}
+
+template <typename T>
+cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
+    cudaError_t e;
+    if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
+    dim3 g(cdiv(d.span, INS_CB), cdiv(d.span, INS_RB));
+    if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d); })) != cudaSuccess) return e;
+    int gr = std::min(d.span, c.num_sms * 4);
+    size_t sm = (size_t)d.span * sizeof(T);
+    return launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p); });
+}
+
+template <typename T> cudaError_t run_decrease(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w) {
+    cudaError_t e;
+    if ((e = launch(c, "decrease_prepass", [&] { k_dec_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w); })) != cudaSuccess) return e;
+    return launch(c, "decrease_sweep", [&] { k_dec_sweep<T><<<c.num_sms * 2, 256, 0, c.stream>>>(d, w); });
+}
+
+template <typename T> static size_t detect_smem(const Dev<T> &d) {
+    return (size_t)d.span * sizeof(T) * (d.undirected ? 2 : 1) + (size_t)d.span * sizeof(int32_t);
+}
+
+template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d, const RepairCfg &cfg) {
+    Dev<T> dd = d;
+    RepairCfg cc = cfg;
+    void *args[] = {(void *)&dd, (void *)&cc};
+    cudaError_t le = cudaSuccess;
+    cudaError_t e = launch(c, "repair", [&] {
+        le = cudaLaunchCooperativeKernel((void *)k_repair<T>, dim3(c.repair_grid), dim3(256), args, c.repair_smem, c.stream);
+    });
+    return le != cudaSuccess ? le : e;
+}
+
+template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
+    cudaError_t e;
+    if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
+    if ((e = launch(c, "detect", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 0, k, -1, (T)0, (T)0); })) != cudaSuccess) return e;
+    if ((e = launch(c, "tombstone", [&] { k_tombstone<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
+    return run_repair<T>(c, d, cfg);
+}
+
+template <typename T>
+cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_old, T w_new, const RepairCfg &cfg) {
+    cudaError_t e;
+    if ((e = launch(c, "increase_prepass", [&] { k_inc_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w_old, w_new); })) != cudaSuccess) return e;
+    if ((e = launch(c, "detect", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
+    return run_repair<T>(c, d, cfg);
+}
+
+// Occupancy-derived launch shapes for a graph of leading dimension ld.
+template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int undirected) {
+    cudaError_t e;
+    size_t row = (size_t)ld * sizeof(T);
+    size_t fw = sizeof(FwSmem<T>) > sizeof(FwDiagSmem<T>) ? sizeof(FwSmem<T>) : sizeof(FwDiagSmem<T>);
+    c.repair_smem = std::max(row, fw);
+    if ((e = cudaFuncSetAttribute(k_repair<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.repair_smem)) != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_repair<T>, 256, c.repair_smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    c.repair_grid = per_sm * c.num_sms;
+    size_t det = (size_t)ld * sizeof(T) * (undirected ? 2 : 1) + (size_t)ld * sizeof(int32_t);
+    if ((e = cudaFuncSetAttribute(k_detect<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)det)) != cudaSuccess) return e;
+    int det_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_detect<T>, 256, det)) != cudaSuccess) return e;
+    c.detect_grid = std::max(1, det_sm) * c.num_sms;
+    if ((e = cudaFuncSetAttribute(k_insert_relax<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+#define APSP_INSTANTIATE(T)                                                                                   \
+    template cudaError_t run_fill<T>(const LaunchCtx &, T *, T, int64_t);                                     \
+    template cudaError_t run_sanitize<T>(const LaunchCtx &, T *, int64_t, int, int, Ctl *);                   \
+    template cudaError_t run_transpose<T>(const LaunchCtx &, const Dev<T> &);                                 \
+    template cudaError_t run_fw<T>(const LaunchCtx &, const Dev<T> &);                                        \
+    template cudaError_t run_insert<T>(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int);    \
+    template cudaError_t run_decrease<T>(const LaunchCtx &, const Dev<T> &, int, int, T);                     \
+    template cudaError_t run_remove<T>(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);            \
+    template cudaError_t run_increase<T>(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &); \
+    template cudaError_t run_repair<T>(const LaunchCtx &, const Dev<T> &, const RepairCfg &);                 \
+    template cudaError_t setup_shapes<T>(LaunchCtx &, int64_t, int);
+
+}  // namespace apsp

@@ -1,0 +1,32 @@
+// Declarations of the per-update launch sequences (defined in launch.cuh,
+// instantiated for int32 and float in kern_i32.cu / kern_f32.cu).
+#pragma once
+
+#include <algorithm>
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace apsp {
+
+struct LaunchCtx {
+    cudaStream_t stream = nullptr;
+    Hook hook{nullptr, nullptr, nullptr};
+    int num_sms = 1;
+    int repair_grid = 1;
+    size_t repair_smem = 0;
+    int detect_grid = 1;
+};
+
+template <typename T> cudaError_t run_fill(const LaunchCtx &, T *, T, int64_t);
+template <typename T> cudaError_t run_sanitize(const LaunchCtx &, T *, int64_t, int, int, Ctl *);
+template <typename T> cudaError_t run_transpose(const LaunchCtx &, const Dev<T> &);
+template <typename T> cudaError_t run_fw(const LaunchCtx &, const Dev<T> &);
+template <typename T> cudaError_t run_insert(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int);
+template <typename T> cudaError_t run_decrease(const LaunchCtx &, const Dev<T> &, int, int, T);
+template <typename T> cudaError_t run_remove(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);
+template <typename T> cudaError_t run_increase(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &);
+template <typename T> cudaError_t run_repair(const LaunchCtx &, const Dev<T> &, const RepairCfg &);
+template <typename T> cudaError_t setup_shapes(LaunchCtx &, int64_t, int);
+
+}  // namespace apsp

@@ -221,6 +221,34 @@ typedef struct {
 apsp_status apsp_profile_read(apsp_graph *g, apsp_profile_entry *out, int32_t cap, int32_t *count);
 apsp_status apsp_profile_reset(apsp_graph *g);
 
+/* ----- insertion without allocation ---------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they add a node (a request handler that
+ * must not block on cudaMalloc, which synchronises the device; a framework
+ * that owns all device memory through its own pool; a fixed memory budget).
+ *
+ * Adds node p to a caller-owned APSP matrix D in place, as apsp_add_node does
+ * (Section 3.1): D (device, 16-byte aligned, leading dimension ld elements, a
+ * multiple of 4 and >= n_slots) holds on entry the APSP matrix of the live
+ * slots among the first n_slots (row and column p are ignored); on return it
+ * also holds row and column p.  alive (device, n_slots int32: 1 = live, p must
+ * be 0 and is not changed), in_w / out_w (device, n_slots weights t -> p and
+ * p -> t) are only read.  n_slots must be a multiple of 4 in
+ * [4, APSP_NOALLOC_MAX_SLOTS] (APSP_E_CAPACITY above the maximum, APSP_E_ARG
+ * otherwise); negative or NaN weights are read as missing edges.
+ *
+ * Scratch lives in one fixed library-owned device array of
+ * 4 * APSP_NOALLOC_MAX_SLOTS * 4 bytes (256 KiB) that every GPU loading the
+ * library holds until the process exits; the call allocates nothing and does
+ * not wait for the GPU.  The first call on a device looks up the array's
+ * device address, so make it before any CUDA stream capture.  All calls share
+ * the array (each re-initialises it): calls whose work overlaps on the GPU
+ * race and must be serialised by the caller. */
+#define APSP_NOALLOC_MAX_SLOTS 16384
+apsp_status apsp_add_node_noalloc(void *D, int64_t ld, int32_t n_slots, const int32_t *alive,
+                                  apsp_dtype dtype, const void *in_w, const void *out_w,
+                                  int32_t p, void *cuda_stream);
+
 const char *apsp_status_string(apsp_status s);
 /* Library version, e.g. "0.1.0". */
 const char *apsp_version(void);

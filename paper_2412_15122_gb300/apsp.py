@@ -96,6 +96,7 @@ def _load():
         "apsp_profile_enable": [P, I32],
         "apsp_profile_read": [P, ctypes.POINTER(apsp_profile_entry), I32, ctypes.POINTER(I32)],
         "apsp_profile_reset": [P],
+        "apsp_add_node_noalloc": [P, I64, I32, P, I32, P, P, I32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -263,6 +264,12 @@ def apsp_profile_read(g: int) -> dict:
 
 def apsp_profile_reset(g: int):
     _check(_load().apsp_profile_reset(g), "apsp_profile_reset")
+
+
+def apsp_add_node_noalloc(D, ld: int, n_slots: int, alive, dtype: int, in_w, out_w, p: int, stream=None):
+    """Insertion on a caller-owned device matrix without any allocation (see apsp.h)."""
+    _check(_load().apsp_add_node_noalloc(_ptr(D), ld, n_slots, _ptr(alive), dtype, _ptr(in_w), _ptr(out_w), p,
+                                         _stream_ptr(stream)), "apsp_add_node_noalloc")
 
 
 _torch_alloc_refs = None

@@ -38,7 +38,7 @@ SEED = 2
 METRIC = "warm-start APSP updates/s at n=8192 vs GPU cold FW; sweep HBM GB/s vs peak"
 UNIT = "updates/s"
 WORKLOAD = "n=8192 directed complete graph, int32 weights U[1,1e6], mixed updates 25% add / 25% remove / 25% decrease (w/2) / 25% increase (4w), uniform targets, one call per update"
-SWEEP_KERNELS = ("insert_reduce", "insert_relax", "detect")
+SWEEP_KERNELS = ("insert_reduce", "insert_relax", "detect_remove")
 
 
 def peaks():
@@ -189,6 +189,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=1024)
+    ap.add_argument("--no-stats", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -230,22 +231,27 @@ def main():
         if dist:
             dist.barrier()
 
-    # ---- value: inputs resident in HBM --------------------------------------
-    g = Graph(W, CAP, stream=stream)
+    # ---- value: inputs resident in HBM ----------------------------------------
+    U = args.updates
     dvec = {id(op): (torch.from_numpy(op[1]).cuda(), torch.from_numpy(op[2]).cuda())
             for op in ops_value if op[0] == "add"}
-    torch.cuda.synchronize()
-    U = args.updates
-    for s in range(args.warmup):
-        for op in ops_value[s * U:(s + 1) * U]:
-            issue(g, op, dvec)
-    g.sync()
-    A.apsp_profile_enable(g.h, True)
-    A.apsp_profile_reset(g.h)
-    launches0 = g.launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    with Clocks(local) as clk:
+
+    def device_pass(profile: bool, want_clocks: bool):
+        g = Graph(W, CAP, stream=stream)
+        torch.cuda.synchronize()
+        for s in range(args.warmup):
+            for op in ops_value[s * U:(s + 1) * U]:
+                issue(g, op, dvec)
+        g.sync()
+        if profile:
+            A.apsp_profile_enable(g.h, True)
+            A.apsp_profile_reset(g.h)
+        launches0 = g.launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        clk = Clocks(local) if want_clocks else None
+        if clk:
+            clk.__enter__()
         ev0.record(stream)
         for s in range(args.warmup, args.warmup + args.steps):
             for op in ops_value[s * U:(s + 1) * U]:
@@ -253,27 +259,54 @@ def main():
         ev1.record(stream)
         g.sync()
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    gpu_launches = g.launches() - launches0
-    prof = A.apsp_profile_read(g.h)
-    A.apsp_profile_enable(g.h, False)
+        if clk:
+            clk.__exit__(None, None, None)
+        ms = ev0.elapsed_time(ev1)
+        nl = g.launches() - launches0
+        prof = A.apsp_profile_read(g.h) if profile else {}
+        cold = None
+        if not profile:
+            # cold FW on the final graph (the comparison baseline)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            g.recompute()
+            c1.record(stream)
+            g.sync()
+            cold = c0.elapsed_time(c1)
+        span = g.info()["n_slots"]
+        g.close()
+        return ms, nl, prof, cold, span, clk
+
+    ms, gpu_launches, _, cold_ms, span, clk = device_pass(profile=False, want_clocks=True)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     n_updates = args.steps * U * world
     value = n_updates / (ms / 1000.0)
+    prof_ms, _, prof, _, _, _ = device_pass(profile=True, want_clocks=False)
 
-    # cold FW on the final graph (the comparison baseline)
-    torch.cuda.synchronize()
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    g.recompute()
-    c1.record(stream)
-    g.sync()
-    cold_ms = c0.elapsed_time(c1)
-    span = g.info()["n_slots"]
-    g.close()
+    # ---- statistics of the workload (untimed, one wait per update) -----------
+    stats = {}
+    if rank == 0 and not args.no_stats:
+        g = Graph(W, CAP, stream=stream)
+        for op in ops_value[: (args.warmup + args.steps) * U]:
+            issue(g, op, dvec)
+            st = g.stats()
+            k = stats.setdefault(st["op"], {"count": 0, "paths": {}, "pairs": 0, "rows": 0, "passes": 0,
+                                             "sweep_rows": 0, "max_pairs": 0})
+            k["count"] += 1
+            k["paths"][st["path"]] = k["paths"].get(st["path"], 0) + 1
+            k["pairs"] += st["affected_pairs"]
+            k["rows"] += st["affected_rows"]
+            k["passes"] += st["passes"]
+            k["sweep_rows"] += st["sweep_rows"]
+            k["max_pairs"] = max(k["max_pairs"], st["affected_pairs"])
+        g.close()
+        for k in stats.values():
+            c = max(1, k["count"])
+            for f in ("pairs", "rows", "passes", "sweep_rows"):
+                k["avg_" + f] = round(k.pop(f) / c, 2)
     del dvec
 
     # ---- e2e: host buffers through the C ABI ---------------------------------
@@ -346,6 +379,8 @@ def main():
             "clocks": clk.summary(),
             "gpu_launches": gpu_launches,
             "cold_fw_ms": cold_ms,
+            "profiled_pass_ms": prof_ms,
+            "update_stats": stats,
             "warm_updates_per_cold_fw": value * cold_ms / 1000.0,
             "top_kernel": {"name": top[0], "launches": top[1][0], "total_ms": top[1][1]},
             "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in sorted(prof.items())},

@@ -39,8 +39,14 @@ template <typename T> struct Dev {
     int32_t *vin_k, *vout_k;  // Corollary 2 / Corollary 1 vectors as ordered keys
     T *x, *x2, *y, *y2;       // staged rows / columns of the current update
     int32_t *rlist;           // prepass row list
-    int4 *items;              // (row, first pair, pair count, 0)
+    int4 *items;              // (row, first pair, pair count | row's pair count << 8, row's first pair)
     int32_t *pairs;           // affected column per pair, grouped by row
+    int32_t *col_count;       // affected pairs per column (span)
+    int32_t *col_start;       // exclusive prefix of col_count (span + 1)
+    int32_t *col_fill;        // fill cursor per column (span)
+    int32_t *colrows;         // affected row per pair, grouped by column
+    uint8_t *rowchg;          // 3 x ld: rows changed in a pass (triple-buffered)
+    uint8_t *colchg;          // 3 x ld: columns changed in a pass
     Ctl *ctl;
     int64_t pair_cap;
     int32_t item_cap;
@@ -67,6 +73,83 @@ __device__ __forceinline__ void warp_append(bool flag, int i, int32_t *list, int
     if (lane == leader) base = atomicAdd(count, __popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (flag) list[base + __popc(m & ((1u << lane) - 1))] = i;
+}
+
+// Rows of up to ROW_NV * 1024 elements are swept by 256 threads that first
+// load their whole share of the row (ROW_NV 16-byte vectors each) so every
+// load of the row is in flight at once, then consume it.
+constexpr int ROW_NV = 20;
+static_assert(ROW_NV * 1024 >= 18432, "a row of the largest capacity must fit");
+
+template <typename V4>
+__device__ __forceinline__ void load_row_regs(V4 (&rv)[ROW_NV], const V4 *row, int nv4) {
+#pragma unroll
+    for (int k = 0; k < ROW_NV; ++k) {
+        const int c4 = threadIdx.x + 256 * k;
+        if (c4 < nv4) rv[k] = row[c4];
+    }
+}
+
+// Warp-per-row sweeps.  A warp walks a row in batches of SWEEP_B 16-byte
+// vectors per lane (SWEEP_B * 512 bytes in flight per warp), calling
+// f(c4, v) for every vector; no CTA-wide barriers are involved.
+constexpr int SWEEP_B = 8;
+
+template <typename V4, int B = SWEEP_B, typename F>
+__device__ __forceinline__ void warp_row_sweep(const V4 *row, int nv4, F &&f) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < nv4; base += 32 * B) {
+        V4 v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int c4 = base + b * 32 + lane;
+            if (c4 < nv4) v[b] = __ldcs(row + c4);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int c4 = base + b * 32 + lane;
+            if (c4 < nv4) f(c4, v[b]);
+        }
+    }
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Exclusive prefix of v over the lanes of a warp; *total = sum over the warp.
+__device__ __forceinline__ int warp_exclusive_scan(int v, int *total) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// Stages a vector of `span` elements into shared memory (all threads of the
+// CTA); each thread issues up to 8 loads before its first store.
+template <typename T> __device__ __forceinline__ void stage_vec(T *dst, const T *src, int span) {
+    using V4 = typename MinPlus<T>::V4;
+    const int nv = span / 4;
+    for (int base = 0; base < nv; base += 8 * (int)blockDim.x) {
+        V4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int c4 = base + k * blockDim.x + threadIdx.x;
+            if (c4 < nv) v[k] = __ldcg(reinterpret_cast<const V4 *>(src) + c4);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int c4 = base + k * blockDim.x + threadIdx.x;
+            if (c4 < nv) reinterpret_cast<V4 *>(dst)[c4] = v[k];
+        }
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -170,45 +253,51 @@ __global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int c
 // One pass over D computing both vectors of the new node:
 //   out[r] = min_t w(p, t) + D[t][r]     (Corollary 1, column reduction)
 //   in[t]  = min_r D[t][r] + w(r, p)     (Corollary 2, row reduction)
-// Tile: 256 rows x 512 columns per CTA; each lane owns 16 columns; partial
-// results meet in global memory through atomicMin on ordered keys.
-constexpr int INS_RB = 256, INS_CB = 512;
+// Grid: (column band of INS_CB columns) x (row range); the launcher picks the
+// number of row ranges so the grid is one wave over the SMs.  Each lane owns
+// 16 columns; partial results meet in global memory through atomicMin on
+// ordered keys (one per row per band, one per column per row range).
+constexpr int INS_CB = 512;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d) {
+__global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d, int rows_per_cta) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     __shared__ T red[8][INS_CB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int c0 = blockIdx.x * INS_CB, r0 = blockIdx.y * INS_RB;
+    const int c0 = blockIdx.x * INS_CB;
+    const int r0 = blockIdx.y * rows_per_cta;
+    const int r1 = min(d.span, r0 + rows_per_cta);
     T win[16], col[16];
+    bool cin[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q) {
+        cin[q] = c0 + q * 128 + lane * 4 < d.span;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             int c = c0 + q * 128 + lane * 4 + e;
             win[q * 4 + e] = c < d.span ? d.w_in[c] : M::inf();
             col[q * 4 + e] = M::inf();
         }
+    }
 #pragma unroll 2
-    for (int t = 0; t < INS_RB / 8; ++t) {
-        int row = r0 + w + 8 * t;
-        if (row >= d.span) break;
+    for (int row = r0 + w; row < r1; row += 8) {
         if (!d.alive[row]) continue;
-        T wo = d.w_out[row];
+        const T wo = d.w_out[row];
+        const T *Dr = d.D + (int64_t)row * d.ld + c0 + lane * 4;
+        V4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (cin[q]) v[q] = *reinterpret_cast<const V4 *>(Dr + q * 128);
         T racc = M::inf();
-        const T *Dr = d.D + (int64_t)row * d.ld;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            int c = c0 + q * 128 + lane * 4;
-            if (c < d.span) {
-                V4 v = *reinterpret_cast<const V4 *>(Dr + c);
-                T e4[4] = {v.x, v.y, v.z, v.w};
+            if (!cin[q]) continue;
+            T e4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    col[q * 4 + e] = M::add_min(wo, e4[e], col[q * 4 + e]);
-                    racc = M::add_min(e4[e], win[q * 4 + e], racc);
-                }
+            for (int e = 0; e < 4; ++e) {
+                col[q * 4 + e] = M::add_min(wo, e4[e], col[q * 4 + e]);
+                racc = M::add_min(e4[e], win[q * 4 + e], racc);
             }
         }
         racc = warp_min(racc);
@@ -228,39 +317,41 @@ __global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d) {
 }
 
 // Theorem 3 sweep: D[i][j] = min(D[i][j], in[i] + out[j]), then row p = out,
-// column p = in, D[p][p] = 0, and the weights of p.  Rows are visited in the
-// reverse of the reduction's order so its last rows are still in L2.
+// column p = in, D[p][p] = 0, and the weights of p.  One warp per row, rows in
+// the reverse of the reduction's order (its last rows may still be in L2);
+// out[] (as ordered keys) is staged once per CTA in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_insert_relax(Dev<T> d, int p) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *so = reinterpret_cast<T *>(smem_raw);
     const int span = d.span;
-    for (int c = threadIdx.x; c < span; c += blockDim.x) so[c] = M::unkey(d.vout_k[c]);
+    int32_t *sok = reinterpret_cast<int32_t *>(smem_raw);
+    stage_vec<int32_t>(sok, d.vout_k, span);
     __syncthreads();
-    const V4 *so4 = reinterpret_cast<const V4 *>(so);
-    for (int r = blockIdx.x; r < span; r += gridDim.x) {
+    const int4 *ok4 = reinterpret_cast<const int4 *>(sok);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < span; r += nwarps) {
         const int row = span - 1 - r;
+        T *Dr = d.D + (int64_t)row * d.ld;
         if (row == p) {
-            for (int c = threadIdx.x; c < span; c += blockDim.x) {
-                T o = c == p ? (T)0 : so[c];
-                d.D[(int64_t)p * d.ld + c] = o;
+            for (int c = lane; c < span; c += 32) {
+                T o = c == p ? (T)0 : M::unkey(sok[c]);
+                Dr[c] = o;
                 d.W[(int64_t)p * d.ld + c] = c == p ? (T)0 : d.w_out[c];
                 if (d.DT) d.DT[(int64_t)c * d.ld + p] = o;
             }
-            if (threadIdx.x == 0) d.alive[p] = 1;
+            if (lane == 0) d.alive[p] = 1;
             continue;
         }
         if (!d.alive[row]) continue;
         const T vi = M::unkey(d.vin_k[row]);
         if (!M::finite(vi)) continue;
-        T *Dr = d.D + (int64_t)row * d.ld;
-        for (int c4 = threadIdx.x; c4 < span / 4; c4 += blockDim.x) {
-            V4 v = *reinterpret_cast<const V4 *>(Dr + 4 * c4);
-            V4 o = so4[c4];
+        warp_row_sweep<V4>(reinterpret_cast<const V4 *>(Dr), span / 4, [&](int c4, V4 v) {
+            const int4 o = ok4[c4];
             T dv[4] = {v.x, v.y, v.z, v.w};
-            T ov[4] = {o.x, o.y, o.z, o.w};
+            const T ov[4] = {M::unkey(o.x), M::unkey(o.y), M::unkey(o.z), M::unkey(o.w)};
             bool any = false;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -273,11 +364,11 @@ __global__ void __launch_bounds__(256) k_insert_relax(Dev<T> d, int p) {
             }
             if (any) {
                 V4 nv; nv.x = dv[0]; nv.y = dv[1]; nv.z = dv[2]; nv.w = dv[3];
-                *reinterpret_cast<V4 *>(Dr + 4 * c4) = nv;
+                reinterpret_cast<V4 *>(Dr)[c4] = nv;
             }
-        }
-        __syncthreads();  // the vector holding column p is written above
-        if (threadIdx.x == 0) {
+        });
+        __syncwarp();  // the vector holding column p may have been stored above
+        if (lane == 0) {
             Dr[p] = vi;
             d.W[(int64_t)row * d.ld + p] = d.w_in[row];
             if (d.DT) d.DT[(int64_t)p * d.ld + row] = vi;
@@ -318,19 +409,19 @@ __global__ void k_dec_prepass(Dev<T> d, int u, int v, T w) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_dec_sweep(Dev<T> d, T w) {
+__global__ void __launch_bounds__(256, 3) k_dec_sweep(Dev<T> d, T w) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     const int nrows = *(volatile int32_t *)&d.ctl->r_count;
     const V4 *y4 = reinterpret_cast<const V4 *>(d.y);
     const V4 *y24 = reinterpret_cast<const V4 *>(d.y2);
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += nwarps) {
         const int i = d.rlist[r];
         const T a1 = M::add(d.x[i], w);
         const T a2 = d.undirected ? M::add(d.x2[i], w) : M::inf();
         T *Dr = d.D + (int64_t)i * d.ld;
-        for (int c4 = threadIdx.x; c4 < d.span / 4; c4 += blockDim.x) {
-            V4 v = *reinterpret_cast<const V4 *>(Dr + 4 * c4);
+        warp_row_sweep<V4>(reinterpret_cast<const V4 *>(Dr), d.span / 4, [&](int c4, V4 v) {
             V4 yv = y4[c4];
             T dv[4] = {v.x, v.y, v.z, v.w};
             T yy[4] = {yv.x, yv.y, yv.z, yv.w};
@@ -351,9 +442,9 @@ __global__ void __launch_bounds__(256) k_dec_sweep(Dev<T> d, T w) {
             }
             if (any) {
                 V4 nv; nv.x = dv[0]; nv.y = dv[1]; nv.z = dv[2]; nv.w = dv[3];
-                *reinterpret_cast<V4 *>(Dr + 4 * c4) = nv;
+                reinterpret_cast<V4 *>(Dr)[c4] = nv;
             }
-        }
+        });
     }
 }
 
@@ -371,12 +462,24 @@ __global__ void __launch_bounds__(256) k_dec_sweep(Dev<T> d, T w) {
 // `pairs`, and are cut into work items of ITEM_PAIRS pairs.
 // --------------------------------------------------------------------------
 
+// Clears the per-update column lists and change flags of slot i.
+template <typename T> __device__ __forceinline__ void clear_repair_scratch(const Dev<T> &d, int i) {
+    d.col_count[i] = 0;
+    d.col_fill[i] = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        d.rowchg[b * d.ld + i] = 0;
+        d.colchg[b * d.ld + i] = 0;
+    }
+}
+
 template <typename T>
 __global__ void k_rm_gather(Dev<T> d, int k) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.span) return;
     d.x[i] = col_src(d, k, i);                 // D[i][k]
     d.y[i] = d.D[(int64_t)k * d.ld + i];       // D[k][i]
+    clear_repair_scratch(d, i);
 }
 
 template <typename T>
@@ -391,6 +494,7 @@ __global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
     }
     bool in_r = false;
     if (i < d.span) {
+        clear_repair_scratch(d, i);
         d.y[i] = d.D[(int64_t)v * d.ld + i];
         if (d.undirected) d.y2[i] = d.D[(int64_t)u * d.ld + i];
         if (tight_edge && d.alive[i]) {
@@ -407,93 +511,159 @@ __global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
     warp_append(in_r, i, d.rlist, &d.ctl->r_count);
 }
 
+constexpr int DETECT_B = 8;
+constexpr int UNIT_PAIRS = 4;                              // pairs per work unit in passes >= 2
+constexpr int UNITS_PER_ITEM = 32 / UNIT_PAIRS;
+constexpr int DETECT_HB = 256;  // per-warp buffer of a row's affected columns
+
+// Is the pair tight through the removed node / changed edge?  `via` is the
+// length of the path through it, `dd` the stored distance.  For integers the
+// sum is exact and via >= dd, so tight means equal; unreachable pairs never
+// count (they stay unreachable).
+template <typename T> __device__ __forceinline__ bool tight_hit(T via, T dd) {
+    return MinPlus<T>::tight(via, dd) && MinPlus<T>::finite(dd);
+}
+
 // kind 0: removal of node a (rows: every live row != a)
 // kind 1: increase of edge a -> b from w_old to w_new (rows: prepass list)
+// One warp per row, 8 vectors per lane in flight.  A row's affected columns
+// are appended in column order to a per-warp shared buffer (ballot + prefix
+// sum); one packed atomic reserves their slots; a row with more than
+// DETECT_HB of them is written by a second scan instead.
 template <typename T>
-__global__ void __launch_bounds__(256) k_detect(Dev<T> d, int kind, int a, int b, T w_old, T w_new) {
+__global__ void __launch_bounds__(256, 2) k_detect(Dev<T> d, int kind, int a, int b, T w_old, T w_new) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int32_t hbuf[8][DETECT_HB];
     const int span = d.span;
+    const bool two = kind == 1 && d.undirected;
     T *ys = reinterpret_cast<T *>(smem_raw);
     T *y2s = ys + span;
-    int32_t *hits = reinterpret_cast<int32_t *>(y2s + (d.undirected ? span : 0));
-    __shared__ int cnt_s, base_s, item_s, ovf_s;
-    for (int c = threadIdx.x; c < span; c += blockDim.x) {
-        ys[c] = d.y[c];
-        if (d.undirected) y2s[c] = d.y2[c];
-    }
-    if (threadIdx.x == 0) cnt_s = 0;
+    stage_vec<T>(ys, d.y, span);
+    if (two) stage_vec<T>(y2s, d.y2, span);
     __syncthreads();
+    const V4 *ys4 = reinterpret_cast<const V4 *>(ys);
+    const V4 *y2s4 = reinterpret_cast<const V4 *>(y2s);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t *hb = hbuf[wib];
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
     const int nrows = kind == 0 ? span : *(volatile int32_t *)&d.ctl->r_count;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int nv4 = span / 4;
+    int rows_hit = 0;
+    for (int r = blockIdx.x * (blockDim.x >> 5) + wib; r < nrows; r += nwarps) {
         const int i = kind == 0 ? r : d.rlist[r];
         if (kind == 0 && (i == a || !d.alive[i])) continue;
         const T xi = d.x[i];
-        const T x2i = (kind == 1 && d.undirected) ? d.x2[i] : M::inf();
+        const T x2i = two ? d.x2[i] : M::inf();
         const T s1 = kind == 0 ? xi : M::add(xi, w_old);
         const T s2 = M::add(x2i, w_old);
         if (!M::finite(s1) && !M::finite(s2)) continue;
         const T *Dr = d.D + (int64_t)i * d.ld;
         const T *Wr = d.W + (int64_t)i * d.ld;
-        for (int c4 = threadIdx.x; c4 < span / 4; c4 += blockDim.x) {
-            V4 v = *reinterpret_cast<const V4 *>(Dr + 4 * c4);
-            T dv[4] = {v.x, v.y, v.z, v.w};
+        const int ci = i >> 2, ca = kind == 0 ? (a >> 2) : -1;
+        // tightness bits of one vector (before excluding the diagonal, the
+        // removed node and pairs with a tight direct edge)
+        auto raw4 = [&](int c4, const V4 &v) -> unsigned {
+            const V4 y = ys4[c4];
+            unsigned m = (unsigned)tight_hit<T>(s1 + y.x, v.x) | (unsigned)tight_hit<T>(s1 + y.y, v.y) << 1 |
+                         (unsigned)tight_hit<T>(s1 + y.z, v.z) << 2 | (unsigned)tight_hit<T>(s1 + y.w, v.w) << 3;
+            if (two) {
+                const V4 y2 = y2s4[c4];
+                m |= (unsigned)tight_hit<T>(s2 + y2.x, v.x) | (unsigned)tight_hit<T>(s2 + y2.y, v.y) << 1 |
+                     (unsigned)tight_hit<T>(s2 + y2.z, v.z) << 2 | (unsigned)tight_hit<T>(s2 + y2.w, v.w) << 3;
+            }
+            return m;
+        };
+        auto refine = [&](int c4, const V4 &v, unsigned m) -> unsigned {
+            if (c4 == ci) m &= ~(1u << (i & 3));
+            if (c4 == ca) m &= ~(1u << (a & 3));
+            const T dv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
+                if (!(m >> e & 1u)) continue;
                 const int j = 4 * c4 + e;
-                const T dd = dv[e];
-                if (j == i || !M::finite(dd)) continue;
-                bool hit;
-                if (kind == 0) {
-                    hit = j != a && M::tight(M::add(s1, ys[j]), dd);
-                } else {
-                    hit = M::tight(M::add(s1, ys[j]), dd) ||
-                          (d.undirected && M::tight(M::add(s2, y2s[j]), dd));
-                }
-                if (hit) {
-                    const bool changed_edge = kind == 1 && ((i == a && j == b) || (d.undirected && i == b && j == a));
-                    if (!changed_edge && Wr[j] == dd) hit = false;  // direct edge is a shortest path
-                }
-                if (hit) hits[atomicAdd(&cnt_s, 1)] = j;
+                const bool changed_edge = kind == 1 && ((i == a && j == b) || (d.undirected && i == b && j == a));
+                if (!changed_edge && __ldg(Wr + j) == dv[e]) m &= ~(1u << e);  // direct edge is a shortest path
             }
+            return m;
+        };
+        // one scan of the row: count, and buffer up to DETECT_HB columns
+        auto scan = [&](bool write_direct, long long base, auto &&emit) -> int {
+            int n = 0;
+            for (int c0 = 0; c0 < nv4; c0 += 32 * DETECT_B) {
+                V4 v[DETECT_B];
+                unsigned m[DETECT_B];
+#pragma unroll
+                for (int bb = 0; bb < DETECT_B; ++bb) {
+                    const int c4 = c0 + bb * 32 + lane;
+                    if (c4 < nv4) v[bb] = __ldcs(reinterpret_cast<const V4 *>(Dr) + c4);
+                }
+                unsigned any = 0;
+#pragma unroll
+                for (int bb = 0; bb < DETECT_B; ++bb) {
+                    const int c4 = c0 + bb * 32 + lane;
+                    m[bb] = c4 < nv4 ? raw4(c4, v[bb]) : 0u;
+                    any |= m[bb];
+                }
+                if (__ballot_sync(0xffffffffu, any != 0) == 0) continue;
+#pragma unroll
+                for (int bb = 0; bb < DETECT_B; ++bb) {
+                    const int c4 = c0 + bb * 32 + lane;
+                    const unsigned mm = m[bb] ? refine(c4, v[bb], m[bb]) : 0u;
+                    if (__ballot_sync(0xffffffffu, mm != 0) == 0) continue;
+                    int tot;
+                    int off = n + warp_exclusive_scan(__popc(mm), &tot);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (!(mm >> e & 1u)) continue;
+                        if (write_direct) emit(off, 4 * c4 + e);
+                        else if (off < DETECT_HB) hb[off] = 4 * c4 + e;
+                        ++off;
+                    }
+                    n += tot;
+                }
+            }
+            return n;
+        };
+        auto no_emit = [](int, int) {};
+        const int n = scan(false, 0, no_emit);
+        if (n == 0) continue;
+        ++rows_hit;
+        const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
+        unsigned long long old = 0;
+        if (lane == 0) old = atomicAdd(&d.ctl->alloc, ((unsigned long long)n << 24) | (unsigned long long)nit);
+        old = __shfl_sync(0xffffffffu, old, 0);
+        const long long base = (long long)(old >> 24);
+        const int ib = (int)(old & 0xFFFFFFull);
+        if (base + n > d.pair_cap || ib + nit > d.item_cap) {
+            if (lane == 0) atomicOr(&d.ctl->overflow, 1);
+            continue;
         }
-        __syncthreads();
-        const int n = cnt_s;
-        __syncthreads();  // every thread has read n before cnt_s is reset
-        if (n > 0) {
-            if (threadIdx.x == 0) {
-                cnt_s = 0;
-                const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
-                unsigned long long base = atomicAdd(&d.ctl->n_pairs, (unsigned long long)n);
-                int ib = atomicAdd(&d.ctl->n_items, nit);
-                atomicAdd(&d.ctl->n_rows, 1);
-                int ovf = (base + n > (unsigned long long)d.pair_cap) || (ib + nit > d.item_cap);
-                if (ovf) atomicOr(&d.ctl->overflow, 1);
-                base_s = (int)(ovf ? 0 : base);
-                item_s = ib;
-                ovf_s = ovf;
-            }
-            __syncthreads();
-            if (!ovf_s) {
-                const int base = base_s;
-                const T wn_x = kind == 1 ? M::add(xi, w_new) : M::inf();
-                const T wn_x2 = kind == 1 ? M::add(x2i, w_new) : M::inf();
-                for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                    const int j = hits[t];
-                    d.pairs[base + t] = j;
-                    T init = Wr[j];  // direct edge (new weight if it is the changed edge)
-                    if (kind == 1) init = M::mn(init, M::mn(M::add(wn_x, ys[j]), M::add(wn_x2, d.undirected ? y2s[j] : M::inf())));
-                    d.D[(int64_t)i * d.ld + j] = init;
-                    if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
-                }
-                const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
-                for (int t = threadIdx.x; t < nit; t += blockDim.x)
-                    d.items[item_s + t] = make_int4(i, base + t * ITEM_PAIRS, min(ITEM_PAIRS, n - t * ITEM_PAIRS), 0);
-            }
-            __syncthreads();  // hits[] is reused by the next row
+        const T wn_x = kind == 1 ? M::add(xi, w_new) : M::inf();
+        const T wn_x2 = kind == 1 ? M::add(x2i, w_new) : M::inf();
+        auto emit = [&](int t, int j) {
+            d.pairs[base + t] = j;
+            // achievable upper bound: the direct edge, or the old path with the
+            // changed edge at its new weight
+            T init = __ldg(Wr + j);
+            if (kind == 1) init = M::mn(init, M::mn(M::add(wn_x, ys[j]), M::add(wn_x2, two ? y2s[j] : M::inf())));
+            d.D[(int64_t)i * d.ld + j] = init;
+            if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
+            atomicAdd(&d.col_count[j], 1);
+        };
+        __syncwarp();
+        if (n <= DETECT_HB) {
+            for (int t = lane; t < n; t += 32) emit(t, hb[t]);
+        } else {
+            scan(true, base, emit);  // rare wide row: second scan writes at reserved offsets
         }
+        for (int t = lane; t < nit; t += 32)
+            d.items[ib + t] = make_int4(i, (int)base + t * ITEM_PAIRS,
+                                        min(ITEM_PAIRS, n - t * ITEM_PAIRS) | (n << 8), (int)base);
+        __syncwarp();  // hb is reused by the next row
     }
+    if (lane == 0 && rows_hit) atomicAdd(&d.ctl->n_rows, rows_hit);
 }
 
 // Removal: node k's row and column become missing, slot k dead.
@@ -538,69 +708,233 @@ struct RepairCfg {
     float feat_dw;       // relative weight change
 };
 
+// Exclusive prefix sum of in[0..n) into out[0..n] by one CTA.
+__device__ inline void cta_exclusive_scan(const int32_t *in, int32_t *out, int n) {
+    __shared__ int32_t part[256];
+    const int t = threadIdx.x;
+    const int per = (n + 255) / 256;
+    const int b = min(n, t * per), e = min(n, b + per);
+    int s = 0;
+    for (int k = b; k < e; ++k) s += __ldcg(in + k);
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = t ? part[t - 1] : 0;
+    for (int k = b; k < e; ++k) {
+        out[k] = run;
+        run += __ldcg(in + k);
+    }
+    if (t == 255) out[n] = part[255];
+    __syncthreads();
+}
+
+// Lowers D[i][j] (and DT[j][i]) to v if v is smaller and records the change
+// for pass `pass`; returns whether it lowered it.  An atomic min on the
+// ordered key: in pass 1 different warps handle different x-chunks of the
+// same pair at the same time, and a plain compare-then-store could let a
+// worse chunk result overwrite a better one.
 template <typename T>
-__device__ void repair_warm(Dev<T> &d, int n_items, T *row_s) {
+__device__ __forceinline__ bool relax_write(Dev<T> &d, int i, int j, T v, int pass) {
+    using M = MinPlus<T>;
+    const int32_t key = M::key(v);
+    const int32_t old = atomicMin(reinterpret_cast<int32_t *>(d.D + (int64_t)i * d.ld + j), key);
+    if (key >= old) return false;
+    if (d.DT) atomicMin(reinterpret_cast<int32_t *>(d.DT + (int64_t)j * d.ld + i), key);
+    const int buf = pass % 3;
+    d.rowchg[buf * d.ld + i] = 1;
+    d.colchg[buf * d.ld + j] = 1;
+    return true;
+}
+
+template <typename T>
+__device__ void repair_warm(Dev<T> &d, int n_items) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     Ctl *ctl = d.ctl;
-    __shared__ int item_sh;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int span = d.span;
-    const T *cols = d.DT ? d.DT : d.D;
-    int pass = 0;
-    for (; pass < MAX_PASSES; ++pass) {
-        const int par = pass & 1;
+    const T *cols = d.DT ? d.DT : d.D;   // row j of `cols` is column j of D
+    const int nchunk = (span + PASS1_CHUNK - 1) / PASS1_CHUNK;
+    constexpr int CV = PASS1_CHUNK / 128;  // 16-byte vectors per lane per chunk
+
+    // Column lists (which rows are affected in each column) for the
+    // semi-naive passes: prefix sums now, filled during pass 1.
+    if (blockIdx.x == 0) cta_exclusive_scan(d.col_count, d.col_start, span);
+    if (!grid_barrier(ctl, NoLeader{})) return;
+
+    // Pass 1: every pair against every intermediate x, x taken in chunks so
+    // the rows and columns touched by all warps at once stay in L2.  One warp
+    // per work item (a row and up to ITEM_PAIRS of its pairs); the row chunk
+    // stays in registers and two pairs' column chunks are loaded at a time.
+    bool changed = false;
+    for (int c = 0; c < nchunk; ++c) {
+        const int x0 = c * PASS1_CHUNK;
+        const int nv = (min(span, x0 + PASS1_CHUNK) - x0) / 4;
         while (true) {
-            if (threadIdx.x == 0) item_sh = atomicAdd(&ctl->item_next[par], 1);
-            __syncthreads();
-            const int it = item_sh;
+            int it = 0;
+            if (lane == 0) it = atomicAdd(&ctl->chunk_next[c], 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
             if (it >= n_items) break;
             const int4 item = d.items[it];
             const int i = item.x;
+            const int cnt = item.z & 0xff;
             T *Dr = d.D + (int64_t)i * d.ld;
-            V4 *row4 = reinterpret_cast<V4 *>(row_s);
-            for (int c4 = threadIdx.x; c4 < span / 4; c4 += blockDim.x)
-                row4[c4] = __ldcg(reinterpret_cast<const V4 *>(Dr) + c4);
-            __syncthreads();
-            bool changed = false;
-            for (int q = warp; q < item.z; q += nwarps) {
-                const int j = d.pairs[item.y + q];
-                const V4 *cj = reinterpret_cast<const V4 *>(cols + (int64_t)j * d.ld);
-                T acc0 = M::inf(), acc1 = M::inf();
-#pragma unroll 4
-                for (int c4 = lane; c4 < span / 4; c4 += 32) {
-                    V4 av = row4[c4];
-                    V4 bv = __ldcg(cj + c4);
-                    acc0 = M::add_min(av.x, bv.x, acc0);
-                    acc1 = M::add_min(av.y, bv.y, acc1);
-                    acc0 = M::add_min(av.z, bv.z, acc0);
-                    acc1 = M::add_min(av.w, bv.w, acc1);
+            V4 rv[CV];
+#pragma unroll
+            for (int k = 0; k < CV; ++k)
+                if (lane + 32 * k < nv) rv[k] = __ldcg(reinterpret_cast<const V4 *>(Dr + x0) + lane + 32 * k);
+            for (int q = 0; q < cnt; q += 2) {
+                const bool second = q + 1 < cnt;
+                const int j0 = d.pairs[item.y + q];
+                const int j1 = second ? d.pairs[item.y + q + 1] : j0;
+                const V4 *c0 = reinterpret_cast<const V4 *>(cols + (int64_t)j0 * d.ld + x0);
+                const V4 *c1 = reinterpret_cast<const V4 *>(cols + (int64_t)j1 * d.ld + x0);
+                V4 a[CV], b[CV];
+#pragma unroll
+                for (int k = 0; k < CV; ++k) {
+                    if (lane + 32 * k < nv) {
+                        a[k] = __ldcg(c0 + lane + 32 * k);
+                        if (second) b[k] = __ldcg(c1 + lane + 32 * k);
+                    }
                 }
-                T acc = warp_min(M::mn(acc0, acc1));
+                T acc0 = M::inf(), acc1 = M::inf();
+#pragma unroll
+                for (int k = 0; k < CV; ++k) {
+                    if (lane + 32 * k < nv) {
+                        acc0 = M::add_min(rv[k].x, a[k].x, acc0);
+                        acc0 = M::add_min(rv[k].y, a[k].y, acc0);
+                        acc0 = M::add_min(rv[k].z, a[k].z, acc0);
+                        acc0 = M::add_min(rv[k].w, a[k].w, acc0);
+                        if (second) {
+                            acc1 = M::add_min(rv[k].x, b[k].x, acc1);
+                            acc1 = M::add_min(rv[k].y, b[k].y, acc1);
+                            acc1 = M::add_min(rv[k].z, b[k].z, acc1);
+                            acc1 = M::add_min(rv[k].w, b[k].w, acc1);
+                        }
+                    }
+                }
+                acc0 = warp_min(acc0);
+                acc1 = warp_min(acc1);
                 if (lane == 0) {
-                    T cur = __ldcg(Dr + j);
-                    if (acc < cur) {
-                        Dr[j] = acc;
-                        if (d.DT) d.DT[(int64_t)j * d.ld + i] = acc;
-                        changed = true;
+                    if (acc0 < __ldcg(Dr + j0) && relax_write(d, i, j0, acc0, 1)) changed = true;
+                    if (c == 0) d.colrows[__ldcg(d.col_start + j0) + atomicAdd(&d.col_fill[j0], 1)] = i;
+                    if (second) {
+                        if (acc1 < __ldcg(Dr + j1) && relax_write(d, i, j1, acc1, 1)) changed = true;
+                        if (c == 0) d.colrows[__ldcg(d.col_start + j1) + atomicAdd(&d.col_fill[j1], 1)] = i;
                     }
                 }
             }
-            if (changed) *(volatile int32_t *)&ctl->changed[par] = 1;
-            __syncthreads();
         }
-        const bool ok = grid_barrier(ctl, [&]() {
-            volatile Ctl *c = ctl;
-            int ch = c->changed[par];
-            c->stop = ch == 0;
-            c->changed[par ^ 1] = 0;
-            c->item_next[par ^ 1] = 0;
-            c->passes = pass + 1;
-        });
-        if (!ok) return;
-        if (*(volatile int32_t *)&ctl->stop) break;
     }
-    if (pass == MAX_PASSES && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, ERR_PASSES);
+    if (changed) *(volatile int32_t *)&ctl->changed[1] = 1;
+    int pass = 1;
+    auto leader = [&]() {
+        volatile Ctl *cv = ctl;
+        const int par = pass & 1;
+        cv->stop = cv->changed[par] == 0;
+        cv->changed[par ^ 1] = 0;
+        cv->item_next[par ^ 1] = 0;
+        cv->passes = pass;
+    };
+    if (!grid_barrier(ctl, leader)) return;
+
+    // Passes >= 2 (semi-naive): only affected entries change, so a pair can
+    // improve only through x in its row's or its column's affected list, and
+    // only if that row or column changed in the previous pass.
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int full_limit = max(64, span / 4);
+    for (pass = 2; pass <= MAX_PASSES && !*(volatile int32_t *)&ctl->stop; ++pass) {
+        const uint8_t *rprev = d.rowchg + ((pass - 1) % 3) * d.ld;
+        const uint8_t *cprev = d.colchg + ((pass - 1) % 3) * d.ld;
+        uint8_t *rclr = d.rowchg + ((pass + 1) % 3) * d.ld;
+        uint8_t *cclr = d.colchg + ((pass + 1) % 3) * d.ld;
+        for (int64_t t = gtid; t < span; t += gsz) { rclr[t] = 0; cclr[t] = 0; }
+        const int par = pass & 1;
+        changed = false;
+        unsigned long long evals = 0;
+        const int n_units = n_items * UNITS_PER_ITEM;
+        while (true) {
+            int un = 0;
+            if (lane == 0) un = atomicAdd(&ctl->item_next[par], 1);
+            un = __shfl_sync(0xffffffffu, un, 0);
+            if (un >= n_units) break;
+            const int4 item = d.items[un / UNITS_PER_ITEM];
+            const int q0 = (un % UNITS_PER_ITEM) * UNIT_PAIRS;
+            const int i = item.x;
+            const int cnt = item.z & 0xff;
+            if (q0 >= cnt) continue;
+            const int row_cnt = item.z >> 8;
+            const bool rch = __ldcg(rprev + i) != 0;
+            const T *Dr = d.D + (int64_t)i * d.ld;
+            const int32_t *Ai = d.pairs + item.w;
+            for (int q = q0; q < min(cnt, q0 + UNIT_PAIRS); ++q) {
+                const int j = d.pairs[item.y + q];
+                if (!rch && __ldcg(cprev + j) == 0) continue;
+                const int cb = __ldcg(d.col_start + j), ce = __ldcg(d.col_start + j + 1);
+                const T *cj = cols + (int64_t)j * d.ld;
+                T acc = M::inf();
+                if (row_cnt + (ce - cb) <= full_limit) {
+                    // x over the row's affected columns (sorted) and the
+                    // column's affected rows, 4 independent gathers per lane
+                    T a1 = M::inf(), a2 = M::inf(), a3 = M::inf();
+                    int t = lane;
+                    for (; t + 96 < row_cnt; t += 128) {
+                        const int x0 = __ldcg(Ai + t), x1 = __ldcg(Ai + t + 32), x2 = __ldcg(Ai + t + 64),
+                                  x3 = __ldcg(Ai + t + 96);
+                        acc = M::add_min(__ldcg(Dr + x0), __ldcg(cj + x0), acc);
+                        a1 = M::add_min(__ldcg(Dr + x1), __ldcg(cj + x1), a1);
+                        a2 = M::add_min(__ldcg(Dr + x2), __ldcg(cj + x2), a2);
+                        a3 = M::add_min(__ldcg(Dr + x3), __ldcg(cj + x3), a3);
+                    }
+                    for (; t < row_cnt; t += 32) {
+                        const int x = __ldcg(Ai + t);
+                        acc = M::add_min(__ldcg(Dr + x), __ldcg(cj + x), acc);
+                    }
+                    t = cb + lane;
+                    for (; t + 96 < ce; t += 128) {
+                        const int x0 = __ldcg(d.colrows + t), x1 = __ldcg(d.colrows + t + 32),
+                                  x2 = __ldcg(d.colrows + t + 64), x3 = __ldcg(d.colrows + t + 96);
+                        acc = M::add_min(__ldcg(Dr + x0), __ldcg(cj + x0), acc);
+                        a1 = M::add_min(__ldcg(Dr + x1), __ldcg(cj + x1), a1);
+                        a2 = M::add_min(__ldcg(Dr + x2), __ldcg(cj + x2), a2);
+                        a3 = M::add_min(__ldcg(Dr + x3), __ldcg(cj + x3), a3);
+                    }
+                    for (; t < ce; t += 32) {
+                        const int x = __ldcg(d.colrows + t);
+                        acc = M::add_min(__ldcg(Dr + x), __ldcg(cj + x), acc);
+                    }
+                    acc = M::mn(M::mn(acc, a1), M::mn(a2, a3));
+                } else {
+                    const V4 *r4 = reinterpret_cast<const V4 *>(Dr);
+                    const V4 *c4 = reinterpret_cast<const V4 *>(cj);
+#pragma unroll 8
+                    for (int v = lane; v < span / 4; v += 32) {
+                        V4 av = __ldcg(r4 + v), bv = __ldcg(c4 + v);
+                        acc = M::add_min(av.x, bv.x, acc);
+                        acc = M::add_min(av.y, bv.y, acc);
+                        acc = M::add_min(av.z, bv.z, acc);
+                        acc = M::add_min(av.w, bv.w, acc);
+                    }
+                }
+                acc = warp_min(acc);
+                if (lane == 0) {
+                    ++evals;
+                    if (acc < __ldcg(Dr + j) && relax_write(d, i, j, acc, pass)) changed = true;
+                }
+            }
+        }
+        if (changed) *(volatile int32_t *)&ctl->changed[par] = 1;
+        if (evals) atomicAdd(&ctl->pairs_evaluated, evals);
+        if (!grid_barrier(ctl, leader)) return;
+    }
+    if (pass > MAX_PASSES && !*(volatile int32_t *)&ctl->stop && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicOr(&ctl->err, ERR_PASSES);
 }
 
 template <typename T>
@@ -643,44 +977,75 @@ __device__ void repair_cold(Dev<T> &d, unsigned char *smem) {
 }
 
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_repair(Dev<T> d, RepairCfg cfg) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Ctl *ctl = d.ctl;
-    const int trivial = *(volatile int32_t *)&ctl->trivial;
-    const int n_items = *(volatile int32_t *)&ctl->n_items;
-    const int ovf = *(volatile int32_t *)&ctl->overflow;
-    const int rows = *(volatile int32_t *)&ctl->n_rows;
-    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-    if (trivial || (n_items == 0 && !ovf)) {
-        if (lead) ctl->path = PATH_TRIVIAL;
-        return;
-    }
-    const float cost = (float)rows / (float)max(1, cfg.n_live_before - 1);
-    int cold_reason = 0;
-    float pw = 0.f, pc = 0.f;
-    if (ovf) cold_reason = 4;
-    else if (cfg.mode == 2) cold_reason = 3;
-    else if (cfg.mode == 3 && cfg.has_model) {
+// Warm / cold decision for the current update, computed identically by
+// every CTA of both repair kernels from the control block (deterministic
+// arithmetic, so all of them agree).  Returns -1 when there is nothing to
+// repair, 0 for warm, else the cold reason (1 Cost rule, 2 model, 3 forced,
+// 4 scratch overflow).
+__device__ inline int repair_decide(const Ctl *ctl, const RepairCfg &cfg, float *cost, float *pw, float *pc,
+                                    int *n_items) {
+    const int trivial = *(volatile const int32_t *)&ctl->trivial;
+    const unsigned long long alloc = *(volatile const unsigned long long *)&ctl->alloc;
+    const int ovf = *(volatile const int32_t *)&ctl->overflow;
+    const int rows = *(volatile const int32_t *)&ctl->n_rows;
+    *n_items = (int)(alloc & 0xFFFFFFull);
+    *pw = *pc = 0.f;
+    *cost = 0.f;
+    if (trivial || (*n_items == 0 && !ovf)) return -1;
+    *cost = (float)rows / (float)max(1, cfg.n_live_before - 1);
+    if (ovf) return 4;
+    if (cfg.mode == 2) return 3;
+    if (cfg.mode == 1) return 0;
+    if (cfg.mode == 3 && cfg.has_model) {
         const float n = (float)max(2, cfg.n_live_before);
-        const unsigned long long np = *(volatile unsigned long long *)&ctl->n_pairs;
-        float feat[MLP_IN] = {cfg.feat_type, log2f(n), cfg.feat_dw, (float)np / (n * n), cost,
-                              (float)rows / n};
+        const float np = (float)(alloc >> 24);
+        float feat[MLP_IN] = {cfg.feat_type, log2f(n), cfg.feat_dw, np / (n * n), *cost, (float)rows / n};
         __shared__ float out[MLP_OUT];
         mlp_predict_cta(cfg.model, feat, out);
-        pw = out[0];
-        pc = out[1];
-        if (pc < pw) cold_reason = 2;
-    } else if (cfg.mode != 1 && cost > cfg.delta) cold_reason = 1;
-    if (lead) {
+        *pw = out[0];
+        *pc = out[1];
+        return *pc < *pw ? 2 : 0;
+    }
+    return *cost > cfg.delta ? 1 : 0;
+}
+
+__device__ inline void repair_record(Ctl *ctl, int reason, float cost, float pw, float pc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->cost = cost;
-        ctl->cold_reason = cold_reason;
+        ctl->cold_reason = reason < 0 ? 0 : reason;
         ctl->model_warm = pw;
         ctl->model_cold = pc;
-        ctl->path = cold_reason ? PATH_COLD : PATH_WARM;
+        ctl->path = reason < 0 ? PATH_TRIVIAL : (reason ? PATH_COLD : PATH_WARM);
+        ctl->n_items = (int)(ctl->alloc & 0xFFFFFFull);
+        ctl->n_pairs = ctl->alloc >> 24;
     }
-    if (cold_reason) repair_cold<T>(d, smem_raw);
-    else repair_warm<T>(d, n_items, reinterpret_cast<T *>(smem_raw));
+}
+
+// Warm repair (cooperative launch): restricted re-relaxation.
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_repair_warm(Dev<T> d, RepairCfg cfg) {
+    float cost, pw, pc;
+    int n_items;
+    const int reason = repair_decide(d.ctl, cfg, &cost, &pw, &pc, &n_items);
+    if (reason != 0) {
+        if (reason < 0) repair_record(d.ctl, reason, cost, pw, pc);
+        return;
+    }
+    repair_record(d.ctl, reason, cost, pw, pc);
+    repair_warm<T>(d, n_items);
+}
+
+// Cold repair (cooperative launch): persistent blocked Floyd-Warshall,
+// running only when the decision says cold.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_repair_cold(Dev<T> d, RepairCfg cfg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float cost, pw, pc;
+    int n_items;
+    const int reason = repair_decide(d.ctl, cfg, &cost, &pw, &pc, &n_items);
+    if (reason <= 0) return;
+    repair_record(d.ctl, reason, cost, pw, pc);
+    repair_cold<T>(d, smem_raw);
 }
 
 }  // namespace apsp

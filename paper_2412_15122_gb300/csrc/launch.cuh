@@ -53,10 +53,14 @@ template <typename T>
 cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
     cudaError_t e;
     if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
-    dim3 g(cdiv(d.span, INS_CB), cdiv(d.span, INS_RB));
-    if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d); })) != cudaSuccess) return e;
-    int gr = std::min(d.span, c.num_sms * 4);
-    size_t sm = (size_t)d.span * sizeof(T);
+    // one wave: about 3 CTAs per SM split into column bands x row ranges
+    const int bands = cdiv(d.span, INS_CB);
+    const int ranges = std::max(1, std::min(cdiv(d.span, 8), (3 * c.num_sms + bands - 1) / bands));
+    const int rows_per = cdiv(d.span, ranges);
+    dim3 g(bands, cdiv(d.span, rows_per));
+    if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d, rows_per); })) != cudaSuccess) return e;
+    int gr = c.relax_grid;
+    size_t sm = (size_t)d.span * sizeof(int32_t);
     return launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p); });
 }
 
@@ -67,16 +71,23 @@ template <typename T> cudaError_t run_decrease(const LaunchCtx &c, const Dev<T> 
 }
 
 template <typename T> static size_t detect_smem(const Dev<T> &d) {
-    return (size_t)d.span * sizeof(T) * (d.undirected ? 2 : 1) + (size_t)d.span * sizeof(int32_t);
+    return (size_t)d.span * sizeof(T) * (d.undirected ? 2 : 1);
 }
 
+// Both repair kernels are launched; the one whose path the device-side
+// decision did not choose returns at once.
 template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d, const RepairCfg &cfg) {
     Dev<T> dd = d;
     RepairCfg cc = cfg;
     void *args[] = {(void *)&dd, (void *)&cc};
     cudaError_t le = cudaSuccess;
-    cudaError_t e = launch(c, "repair", [&] {
-        le = cudaLaunchCooperativeKernel((void *)k_repair<T>, dim3(c.repair_grid), dim3(256), args, c.repair_smem, c.stream);
+    cudaError_t e = launch(c, "repair_warm", [&] {
+        le = cudaLaunchCooperativeKernel((void *)k_repair_warm<T>, dim3(c.warm_grid), dim3(256), args, 0, c.stream);
+    });
+    if (le != cudaSuccess) return le;
+    if (e != cudaSuccess) return e;
+    e = launch(c, "repair_cold", [&] {
+        le = cudaLaunchCooperativeKernel((void *)k_repair_cold<T>, dim3(c.repair_grid), dim3(256), args, c.repair_smem, c.stream);
     });
     return le != cudaSuccess ? le : e;
 }
@@ -84,7 +95,7 @@ template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d
 template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
-    if ((e = launch(c, "detect", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 0, k, -1, (T)0, (T)0); })) != cudaSuccess) return e;
+    if ((e = launch(c, "detect_remove", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 0, k, -1, (T)0, (T)0); })) != cudaSuccess) return e;
     if ((e = launch(c, "tombstone", [&] { k_tombstone<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
     return run_repair<T>(c, d, cfg);
 }
@@ -93,7 +104,7 @@ template <typename T>
 cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_old, T w_new, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "increase_prepass", [&] { k_inc_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w_old, w_new); })) != cudaSuccess) return e;
-    if ((e = launch(c, "detect", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
+    if ((e = launch(c, "detect_increase", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
     return run_repair<T>(c, d, cfg);
 }
 
@@ -102,18 +113,26 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     cudaError_t e;
     size_t row = (size_t)ld * sizeof(T);
     size_t fw = sizeof(FwSmem<T>) > sizeof(FwDiagSmem<T>) ? sizeof(FwSmem<T>) : sizeof(FwDiagSmem<T>);
-    c.repair_smem = std::max(row, fw);
-    if ((e = cudaFuncSetAttribute(k_repair<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.repair_smem)) != cudaSuccess) return e;
+    c.repair_smem = std::max<size_t>(fw, 32 * 33 * sizeof(T));
+    if ((e = cudaFuncSetAttribute(k_repair_cold<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.repair_smem)) != cudaSuccess) return e;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_repair<T>, 256, c.repair_smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_repair_cold<T>, 256, c.repair_smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     c.repair_grid = per_sm * c.num_sms;
-    size_t det = (size_t)ld * sizeof(T) * (undirected ? 2 : 1) + (size_t)ld * sizeof(int32_t);
+    int warm_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&warm_sm, k_repair_warm<T>, 256, 0)) != cudaSuccess) return e;
+    if (warm_sm < 1) return cudaErrorInvalidConfiguration;
+    c.warm_grid = warm_sm * c.num_sms;
+    size_t det = row * (undirected ? 2 : 1);
     if ((e = cudaFuncSetAttribute(k_detect<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)det)) != cudaSuccess) return e;
     int det_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_detect<T>, 256, det)) != cudaSuccess) return e;
     c.detect_grid = std::max(1, det_sm) * c.num_sms;
-    if ((e = cudaFuncSetAttribute(k_insert_relax<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row)) != cudaSuccess) return e;
+    size_t rel = (size_t)ld * sizeof(int32_t);
+    if ((e = cudaFuncSetAttribute(k_insert_relax<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rel)) != cudaSuccess) return e;
+    int rel_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rel_sm, k_insert_relax<T>, 256, rel)) != cudaSuccess) return e;
+    c.relax_grid = std::max(1, rel_sm) * c.num_sms;
     return cudaSuccess;
 }
 

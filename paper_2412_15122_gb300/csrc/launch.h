@@ -16,6 +16,8 @@ struct LaunchCtx {
     int repair_grid = 1;
     size_t repair_smem = 0;
     int detect_grid = 1;
+    int relax_grid = 1;
+    int warm_grid = 1;
 };
 
 template <typename T> cudaError_t run_fill(const LaunchCtx &, T *, T, int64_t);

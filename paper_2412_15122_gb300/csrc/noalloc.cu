@@ -133,8 +133,12 @@ apsp_status run(T *D, int64_t ld, int n_slots, const int32_t *alive, const T *in
     d.w_out = w_out;
     d.vin_k = vin_k;
     d.vout_k = vout_k;
-    dim3 g((span + apsp::INS_CB - 1) / apsp::INS_CB, (span + apsp::INS_RB - 1) / apsp::INS_RB);
-    apsp::k_insert_reduce<T><<<g, 256, 0, s>>>(d);
+    const int bands = (span + apsp::INS_CB - 1) / apsp::INS_CB;
+    int ranges = (3 * sms + bands - 1) / bands;
+    ranges = ranges < 1 ? 1 : (ranges > (span + 7) / 8 ? (span + 7) / 8 : ranges);
+    const int rows_per = (span + ranges - 1) / ranges;
+    dim3 g(bands, (span + rows_per - 1) / rows_per);
+    apsp::k_insert_reduce<T><<<g, 256, 0, s>>>(d, rows_per);
     k_na_relax<T><<<span < sms * 4 ? span : sms * 4, 256, 0, s>>>(D, ld, span, p, alive, vin_k, vout_k);
     return cudaGetLastError() == cudaSuccess ? APSP_OK : APSP_E_CUDA;
 }

@@ -384,3 +384,18 @@ def test_scale_n8192_sampled_rows(fp):
         else:
             assert np.array_equal(D[r], O.to_i32(row)), f"row {r}"
     g.close()
+
+
+@pytest.mark.parametrize("fp", [False, True])
+def test_chunked_repair_n2048_full_check(fp):
+    # Several x-chunks per pass-1 evaluation, so different warps relax the same
+    # pair concurrently; wide rows (sources of tight edges) make it frequent.
+    n, cap = 2048, 2048 + 32
+    W = synth.lognormal_digraph_f32(n, 12) if fp else synth.complete_digraph_i32(n, 1, 10**6, 12)
+    g = G(W, cap)
+    mir = Mirror(W, cap)
+    for up in synth.mixed_updates(n, 24, 12, fractions=(0.1, 0.3, 0.1, 0.5), capacity=cap, w_lo=1, w_hi=10**6,
+                                  tight=True, weights="lognormal" if fp else "int"):
+        apply(g, mir, up)
+    assert_same(g, mir, "after 24 updates")
+    g.close()

@@ -34,6 +34,12 @@ template <> struct MinPlus<int32_t> {
     // `via` is the length of a path through the removed node / changed edge,
     // `d` the stored distance (via >= d for an exact D): tight iff equal.
     __device__ static bool tight(int32_t via, int32_t d) { return via <= d; }
+    // via - d for the batch screen (>= 0 for an exact APSP matrix; 0 = tight)
+    __device__ static int32_t slack(int32_t via, int32_t d) { return via - d; }
+    __device__ static bool slack_tight(int32_t s) { return s <= 0; }
+    // staged path-leg values: an unreachable leg becomes INF + 1 so that no
+    // sum through it can equal a stored distance
+    __device__ static int32_t leg(int32_t y) { return y >= INF_I32 ? INF_I32 + 1 : y; }
     // ordered bit pattern for atomicMin
     __device__ static int32_t key(int32_t a) { return a; }
     __device__ static int32_t unkey(int32_t a) { return a; }
@@ -47,6 +53,10 @@ template <> struct MinPlus<float> {
     __device__ static float add_min(float a, float b, float c) { return fminf(a + b, c); }
     __device__ static float mn(float a, float b) { return fminf(a, b); }
     __device__ static bool tight(float via, float d) { return via <= d + d * F32_TIGHT_REL; }
+    // <= 0 when tight within the relative slack (NaN, from inf - inf, is not)
+    __device__ static float slack(float via, float d) { return via - fmaf(d, F32_TIGHT_REL, d); }
+    __device__ static bool slack_tight(float s) { return s <= 0.f; }
+    __device__ static float leg(float y) { return y; }
     // non-negative floats (and +inf) order like their bit patterns as int32
     __device__ static int32_t key(float a) { return __float_as_int(a); }
     __device__ static float unkey(int32_t a) { return __int_as_float(a); }

@@ -316,64 +316,82 @@ __global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d, int rows_per_ct
     }
 }
 
-// Theorem 3 sweep: D[i][j] = min(D[i][j], in[i] + out[j]), then row p = out,
-// column p = in, D[p][p] = 0, and the weights of p.  One warp per row, rows in
-// the reverse of the reduction's order (its last rows may still be in L2);
-// out[] (as ordered keys) is staged once per CTA in shared memory.
+// Theorem 3 sweep: D[i][j] = min(D[i][j], in[i] + out[j]).  One warp per
+// row; out[] is staged once per CTA in shared memory.  Each lane streams 8
+// vectors at a time and only builds a 32-bit mask of the entries that
+// improve; those few entries are then written one by one (the new value is
+// in[i] + out[j]; the row data is no longer needed).  A dead row and p
+// itself have in[] = missing, so one load decides whether a row is swept.
+// Row p and column p are never improved by the sweep (their candidates are
+// missing), so they are written afterwards by k_insert_finish.
 template <typename T>
-__global__ void __launch_bounds__(256) k_insert_relax(Dev<T> d, int p) {
+__global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int span = d.span;
-    int32_t *sok = reinterpret_cast<int32_t *>(smem_raw);
-    stage_vec<int32_t>(sok, d.vout_k, span);
+    // vout_k holds ordered keys whose bit patterns are the values themselves
+    T *so = reinterpret_cast<T *>(smem_raw);
+    V4 *so4w = reinterpret_cast<V4 *>(smem_raw);
+    const V4 *src4 = reinterpret_cast<const V4 *>(d.vout_k);
+    const int nv4 = span / 4;
+    for (int c = threadIdx.x; c < nv4; c += blockDim.x) so4w[c] = src4[c];
     __syncthreads();
-    const int4 *ok4 = reinterpret_cast<const int4 *>(sok);
+    const V4 *so4 = reinterpret_cast<const V4 *>(so);
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < span; r += nwarps) {
-        const int row = span - 1 - r;
-        T *Dr = d.D + (int64_t)row * d.ld;
-        if (row == p) {
-            for (int c = lane; c < span; c += 32) {
-                T o = c == p ? (T)0 : M::unkey(sok[c]);
-                Dr[c] = o;
-                d.W[(int64_t)p * d.ld + c] = c == p ? (T)0 : d.w_out[c];
-                if (d.DT) d.DT[(int64_t)c * d.ld + p] = o;
-            }
-            if (lane == 0) d.alive[p] = 1;
-            continue;
-        }
-        if (!d.alive[row]) continue;
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < span; row += nwarps) {
         const T vi = M::unkey(d.vin_k[row]);
         if (!M::finite(vi)) continue;
-        warp_row_sweep<V4>(reinterpret_cast<const V4 *>(Dr), span / 4, [&](int c4, V4 v) {
-            const int4 o = ok4[c4];
-            T dv[4] = {v.x, v.y, v.z, v.w};
-            const T ov[4] = {M::unkey(o.x), M::unkey(o.y), M::unkey(o.z), M::unkey(o.w)};
-            bool any = false;
+        T *Dr = d.D + (int64_t)row * d.ld;
+        const V4 *Dr4 = reinterpret_cast<const V4 *>(Dr);
+        for (int c0 = 0; c0 < nv4; c0 += 32 * SWEEP_B) {
+            V4 v[SWEEP_B];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                T cand = vi + ov[e];
-                if (cand < dv[e]) {
-                    dv[e] = cand;
-                    any = true;
-                    if (d.DT) d.DT[(int64_t)(4 * c4 + e) * d.ld + row] = cand;
+            for (int bb = 0; bb < SWEEP_B; ++bb) {
+                const int c4 = c0 + bb * 32 + lane;
+                if (c4 < nv4) v[bb] = Dr4[c4];
+            }
+            unsigned mask = 0;
+#pragma unroll
+            for (int bb = 0; bb < SWEEP_B; ++bb) {
+                const int c4 = c0 + bb * 32 + lane;
+                if (c4 < nv4) {
+                    const V4 o = so4[c4];
+                    mask |= ((unsigned)(vi + o.x < v[bb].x) | (unsigned)(vi + o.y < v[bb].y) << 1 |
+                             (unsigned)(vi + o.z < v[bb].z) << 2 | (unsigned)(vi + o.w < v[bb].w) << 3) << (4 * bb);
                 }
             }
-            if (any) {
-                V4 nv; nv.x = dv[0]; nv.y = dv[1]; nv.z = dv[2]; nv.w = dv[3];
-                reinterpret_cast<V4 *>(Dr)[c4] = nv;
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int j = 4 * (c0 + (bit >> 2) * 32 + lane) + (bit & 3);
+                const T cand = vi + so[j];
+                Dr[j] = cand;
+                if (d.DT) d.DT[(int64_t)j * d.ld + row] = cand;
             }
-        });
-        __syncwarp();  // the vector holding column p may have been stored above
-        if (lane == 0) {
-            Dr[p] = vi;
-            d.W[(int64_t)row * d.ld + p] = d.w_in[row];
-            if (d.DT) d.DT[(int64_t)p * d.ld + row] = vi;
         }
     }
+}
+
+// Row p = out (Corollary 1), column p = in (Corollary 2), D[p][p] = 0, the
+// weights of p, and p becomes live.
+template <typename T>
+__global__ void k_insert_finish(Dev<T> d, int p) {
+    using M = MinPlus<T>;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d.span) return;
+    const T o = c == p ? (T)0 : M::unkey(d.vout_k[c]);
+    const T in = c == p ? (T)0 : M::unkey(d.vin_k[c]);
+    d.D[(int64_t)p * d.ld + c] = o;
+    d.D[(int64_t)c * d.ld + p] = in;
+    d.W[(int64_t)p * d.ld + c] = c == p ? (T)0 : d.w_out[c];
+    d.W[(int64_t)c * d.ld + p] = c == p ? (T)0 : d.w_in[c];
+    if (d.DT) {
+        d.DT[(int64_t)c * d.ld + p] = o;
+        d.DT[(int64_t)p * d.ld + c] = in;
+    }
+    if (c == p) d.alive[p] = 1;
 }
 
 // --------------------------------------------------------------------------
@@ -511,37 +529,117 @@ __global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
     warp_append(in_r, i, d.rlist, &d.ctl->r_count);
 }
 
-constexpr int DETECT_B = 8;
 constexpr int UNIT_PAIRS = 4;                              // pairs per work unit in passes >= 2
 constexpr int UNITS_PER_ITEM = 32 / UNIT_PAIRS;
 constexpr int DETECT_HB = 256;  // per-warp buffer of a row's affected columns
 
-// Is the pair tight through the removed node / changed edge?  `via` is the
-// length of the path through it, `dd` the stored distance.  For integers the
-// sum is exact and via >= dd, so tight means equal; unreachable pairs never
-// count (they stay unreachable).
-template <typename T> __device__ __forceinline__ bool tight_hit(T via, T dd) {
-    return MinPlus<T>::tight(via, dd) && MinPlus<T>::finite(dd);
+// Second scan of a row with more affected pairs than the warp buffer holds:
+// the same test, writing each pair at the row's reserved offsets with the
+// direct-edge weights of the batch fetched together.  Out of line so the hot
+// scan keeps its registers.
+template <typename T, bool TWO>
+__device__ __noinline__ void det_wide_write(const Dev<T> &d, int kind, int i, int a, long long base, T s1, T s2,
+                                            bool use1, bool use2, T wn_x, T wn_x2, const T *ys, const T *y2s) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    const int lane = threadIdx.x & 31;
+    const int nv4 = d.span / 4;
+    const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+    const V4 *Wr4 = reinterpret_cast<const V4 *>(d.W + (int64_t)i * d.ld);
+    const V4 *ys4 = reinterpret_cast<const V4 *>(ys);
+    const V4 *y2s4 = reinterpret_cast<const V4 *>(y2s);
+    const int ci = i >> 2, cia = i & 3;
+    const int ca = kind == 0 ? (a >> 2) : -1, caa = a & 3;
+    constexpr int B = 4;
+    int n = 0;
+    for (int c0 = 0; c0 < nv4; c0 += 32 * B) {
+        V4 v[B], wv[B];
+#pragma unroll
+        for (int bb = 0; bb < B; ++bb) {
+            const int c4 = c0 + bb * 32 + lane;
+            if (c4 < nv4) {
+                v[bb] = Dr4[c4];
+                wv[bb] = __ldg(Wr4 + c4);
+            }
+        }
+        unsigned mask = 0;
+#pragma unroll
+        for (int bb = 0; bb < B; ++bb) {
+            const int c4 = c0 + bb * 32 + lane;
+            if (c4 < nv4) {
+                unsigned m = 0;
+                if (use1) {
+                    const V4 y = ys4[c4];
+                    m |= (unsigned)M::slack_tight(M::slack(s1 + y.x, v[bb].x)) |
+                         (unsigned)M::slack_tight(M::slack(s1 + y.y, v[bb].y)) << 1 |
+                         (unsigned)M::slack_tight(M::slack(s1 + y.z, v[bb].z)) << 2 |
+                         (unsigned)M::slack_tight(M::slack(s1 + y.w, v[bb].w)) << 3;
+                }
+                if (TWO && use2) {
+                    const V4 y = y2s4[c4];
+                    m |= (unsigned)M::slack_tight(M::slack(s2 + y.x, v[bb].x)) |
+                         (unsigned)M::slack_tight(M::slack(s2 + y.y, v[bb].y)) << 1 |
+                         (unsigned)M::slack_tight(M::slack(s2 + y.z, v[bb].z)) << 2 |
+                         (unsigned)M::slack_tight(M::slack(s2 + y.w, v[bb].w)) << 3;
+                }
+                if (c4 == ci) m &= ~(1u << cia);
+                if (c4 == ca) m &= ~(1u << caa);
+                mask |= m << (4 * bb);
+            }
+        }
+        int tot;
+        int off = n + warp_exclusive_scan(__popc(mask), &tot);
+#pragma unroll
+        for (int bb = 0; bb < B; ++bb) {
+            const T wv4[4] = {wv[bb].x, wv[bb].y, wv[bb].z, wv[bb].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (!(mask >> (4 * bb + e) & 1u)) continue;
+                const int j = 4 * (c0 + bb * 32 + lane) + e;
+                T init = wv4[e];
+                if (kind == 1)
+                    init = M::mn(init, M::mn(M::add(wn_x, M::mn(ys[j], M::inf())),
+                                             M::add(wn_x2, TWO ? M::mn(y2s[j], M::inf()) : M::inf())));
+                d.pairs[base + off] = j;
+                d.D[(int64_t)i * d.ld + j] = init;
+                if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
+                atomicAdd(&d.col_count[j], 1);
+                ++off;
+            }
+        }
+        n += tot;
+    }
 }
 
-// kind 0: removal of node a (rows: every live row != a)
-// kind 1: increase of edge a -> b from w_old to w_new (rows: prepass list)
-// One warp per row, 8 vectors per lane in flight.  A row's affected columns
-// are appended in column order to a per-warp shared buffer (ballot + prefix
-// sum); one packed atomic reserves their slots; a row with more than
-// DETECT_HB of them is written by a second scan instead.
-template <typename T>
-__global__ void __launch_bounds__(256, 2) k_detect(Dev<T> d, int kind, int a, int b, T w_old, T w_new) {
+// kind 0: removal of node a (rows: every live row != a).  Affected pairs are
+//   exactly the need_update_list of Section 3.2: (i, j), i != j, both != a,
+//   listed unless D[i][j] < D[i][a] + D[a][j] (Corollary 3).
+// kind 1: increase of edge a -> b from w_old to w_new (rows: prepass list):
+//   the same test with the path through the old edge.
+// One warp per row, 8 vectors per lane in flight.  Each lane turns its 8
+// vectors into a 32-bit mask of tight entries (for an exact APSP matrix a
+// path through the removed node / old edge is never shorter than the stored
+// distance, so tight means equal, or equal within the fp32 slack); batches
+// where some lane has a bit set append those columns, in order, to a
+// per-warp buffer (one prefix sum).  One packed atomic reserves the row's
+// slots; a row with more than DETECT_HB pairs is scanned a second time the
+// same way, writing at the reserved offsets.
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(256, 3) k_detect(Dev<T> d, int kind, int a, int b, T w_old, T w_new) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int32_t hbuf[8][DETECT_HB];
     const int span = d.span;
-    const bool two = kind == 1 && d.undirected;
     T *ys = reinterpret_cast<T *>(smem_raw);
     T *y2s = ys + span;
     stage_vec<T>(ys, d.y, span);
-    if (two) stage_vec<T>(y2s, d.y2, span);
+    if (TWO) stage_vec<T>(y2s, d.y2, span);
+    __syncthreads();
+    for (int c = threadIdx.x; c < span; c += blockDim.x) {
+        ys[c] = M::leg(ys[c]);
+        if (TWO) y2s[c] = M::leg(y2s[c]);
+    }
     __syncthreads();
     const V4 *ys4 = reinterpret_cast<const V4 *>(ys);
     const V4 *y2s4 = reinterpret_cast<const V4 *>(y2s);
@@ -553,115 +651,107 @@ __global__ void __launch_bounds__(256, 2) k_detect(Dev<T> d, int kind, int a, in
     int rows_hit = 0;
     for (int r = blockIdx.x * (blockDim.x >> 5) + wib; r < nrows; r += nwarps) {
         const int i = kind == 0 ? r : d.rlist[r];
-        if (kind == 0 && (i == a || !d.alive[i])) continue;
-        const T xi = d.x[i];
-        const T x2i = two ? d.x2[i] : M::inf();
+        if (kind == 0 && i == a) continue;
+        const T xi = d.x[i];  // missing for a dead row, so it is skipped below
+        const T x2i = TWO ? d.x2[i] : M::inf();
         const T s1 = kind == 0 ? xi : M::add(xi, w_old);
         const T s2 = M::add(x2i, w_old);
-        if (!M::finite(s1) && !M::finite(s2)) continue;
-        const T *Dr = d.D + (int64_t)i * d.ld;
-        const T *Wr = d.W + (int64_t)i * d.ld;
-        const int ci = i >> 2, ca = kind == 0 ? (a >> 2) : -1;
-        // tightness bits of one vector (before excluding the diagonal, the
-        // removed node and pairs with a tight direct edge)
-        auto raw4 = [&](int c4, const V4 &v) -> unsigned {
-            const V4 y = ys4[c4];
-            unsigned m = (unsigned)tight_hit<T>(s1 + y.x, v.x) | (unsigned)tight_hit<T>(s1 + y.y, v.y) << 1 |
-                         (unsigned)tight_hit<T>(s1 + y.z, v.z) << 2 | (unsigned)tight_hit<T>(s1 + y.w, v.w) << 3;
-            if (two) {
-                const V4 y2 = y2s4[c4];
-                m |= (unsigned)tight_hit<T>(s2 + y2.x, v.x) | (unsigned)tight_hit<T>(s2 + y2.y, v.y) << 1 |
-                     (unsigned)tight_hit<T>(s2 + y2.z, v.z) << 2 | (unsigned)tight_hit<T>(s2 + y2.w, v.w) << 3;
-            }
-            return m;
-        };
-        auto refine = [&](int c4, const V4 &v, unsigned m) -> unsigned {
-            if (c4 == ci) m &= ~(1u << (i & 3));
-            if (c4 == ca) m &= ~(1u << (a & 3));
-            const T dv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (!(m >> e & 1u)) continue;
-                const int j = 4 * c4 + e;
-                const bool changed_edge = kind == 1 && ((i == a && j == b) || (d.undirected && i == b && j == a));
-                if (!changed_edge && __ldg(Wr + j) == dv[e]) m &= ~(1u << e);  // direct edge is a shortest path
-            }
-            return m;
-        };
-        // one scan of the row: count, and buffer up to DETECT_HB columns
-        auto scan = [&](bool write_direct, long long base, auto &&emit) -> int {
-            int n = 0;
-            for (int c0 = 0; c0 < nv4; c0 += 32 * DETECT_B) {
-                V4 v[DETECT_B];
-                unsigned m[DETECT_B];
-#pragma unroll
-                for (int bb = 0; bb < DETECT_B; ++bb) {
-                    const int c4 = c0 + bb * 32 + lane;
-                    if (c4 < nv4) v[bb] = __ldcs(reinterpret_cast<const V4 *>(Dr) + c4);
-                }
-                unsigned any = 0;
-#pragma unroll
-                for (int bb = 0; bb < DETECT_B; ++bb) {
-                    const int c4 = c0 + bb * 32 + lane;
-                    m[bb] = c4 < nv4 ? raw4(c4, v[bb]) : 0u;
-                    any |= m[bb];
-                }
-                if (__ballot_sync(0xffffffffu, any != 0) == 0) continue;
-#pragma unroll
-                for (int bb = 0; bb < DETECT_B; ++bb) {
-                    const int c4 = c0 + bb * 32 + lane;
-                    const unsigned mm = m[bb] ? refine(c4, v[bb], m[bb]) : 0u;
-                    if (__ballot_sync(0xffffffffu, mm != 0) == 0) continue;
-                    int tot;
-                    int off = n + warp_exclusive_scan(__popc(mm), &tot);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (!(mm >> e & 1u)) continue;
-                        if (write_direct) emit(off, 4 * c4 + e);
-                        else if (off < DETECT_HB) hb[off] = 4 * c4 + e;
-                        ++off;
-                    }
-                    n += tot;
-                }
-            }
-            return n;
-        };
-        auto no_emit = [](int, int) {};
-        const int n = scan(false, 0, no_emit);
-        if (n == 0) continue;
-        ++rows_hit;
-        const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
-        unsigned long long old = 0;
-        if (lane == 0) old = atomicAdd(&d.ctl->alloc, ((unsigned long long)n << 24) | (unsigned long long)nit);
-        old = __shfl_sync(0xffffffffu, old, 0);
-        const long long base = (long long)(old >> 24);
-        const int ib = (int)(old & 0xFFFFFFull);
-        if (base + n > d.pair_cap || ib + nit > d.item_cap) {
-            if (lane == 0) atomicOr(&d.ctl->overflow, 1);
-            continue;
-        }
+        const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
+        if (!use1 && !use2) continue;
+        const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+        const int ci = i >> 2, cia = i & 3;
+        const int ca = kind == 0 ? (a >> 2) : -1, caa = a & 3;
         const T wn_x = kind == 1 ? M::add(xi, w_new) : M::inf();
         const T wn_x2 = kind == 1 ? M::add(x2i, w_new) : M::inf();
-        auto emit = [&](int t, int j) {
-            d.pairs[base + t] = j;
-            // achievable upper bound: the direct edge, or the old path with the
-            // changed edge at its new weight
-            T init = __ldg(Wr + j);
-            if (kind == 1) init = M::mn(init, M::mn(M::add(wn_x, ys[j]), M::add(wn_x2, two ? y2s[j] : M::inf())));
-            d.D[(int64_t)i * d.ld + j] = init;
-            if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
-            atomicAdd(&d.col_count[j], 1);
-        };
-        __syncwarp();
-        if (n <= DETECT_HB) {
-            for (int t = lane; t < n; t += 32) emit(t, hb[t]);
-        } else {
-            scan(true, base, emit);  // rare wide row: second scan writes at reserved offsets
+        int n = 0;
+        for (int pass = 0; pass < 1; ++pass) {
+            for (int c0 = 0; c0 < nv4; c0 += 32 * SWEEP_B) {
+                V4 v[SWEEP_B];
+#pragma unroll
+                for (int bb = 0; bb < SWEEP_B; ++bb) {
+                    const int c4 = c0 + bb * 32 + lane;
+                    if (c4 < nv4) v[bb] = Dr4[c4];
+                }
+                unsigned mask = 0;
+#pragma unroll
+                for (int bb = 0; bb < SWEEP_B; ++bb) {
+                    const int c4 = c0 + bb * 32 + lane;
+                    if (c4 < nv4) {
+                        unsigned m = 0;
+                        if (use1) {
+                            const V4 y = ys4[c4];
+                            m |= (unsigned)M::slack_tight(M::slack(s1 + y.x, v[bb].x)) |
+                                 (unsigned)M::slack_tight(M::slack(s1 + y.y, v[bb].y)) << 1 |
+                                 (unsigned)M::slack_tight(M::slack(s1 + y.z, v[bb].z)) << 2 |
+                                 (unsigned)M::slack_tight(M::slack(s1 + y.w, v[bb].w)) << 3;
+                        }
+                        if (TWO && use2) {
+                            const V4 y = y2s4[c4];
+                            m |= (unsigned)M::slack_tight(M::slack(s2 + y.x, v[bb].x)) |
+                                 (unsigned)M::slack_tight(M::slack(s2 + y.y, v[bb].y)) << 1 |
+                                 (unsigned)M::slack_tight(M::slack(s2 + y.z, v[bb].z)) << 2 |
+                                 (unsigned)M::slack_tight(M::slack(s2 + y.w, v[bb].w)) << 3;
+                        }
+                        if (c4 == ci) m &= ~(1u << cia);
+                        if (c4 == ca) m &= ~(1u << caa);
+                        mask |= m << (4 * bb);
+                    }
+                }
+                if (__ballot_sync(0xffffffffu, mask != 0) == 0) continue;
+                int tot;
+                int off = n + warp_exclusive_scan(__popc(mask), &tot);
+                for (unsigned m = mask; m; m &= m - 1) {
+                    const int bit = __ffs(m) - 1;
+                    if (off < DETECT_HB) hb[off] = 4 * (c0 + (bit >> 2) * 32 + lane) + (bit & 3);
+                    ++off;
+                }
+                n += tot;
+            }
+            if (n == 0) break;
+            // reserve the row's slots
+            const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
+            unsigned long long old = 0;
+            if (lane == 0) old = atomicAdd(&d.ctl->alloc, ((unsigned long long)n << 24) | (unsigned long long)nit);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            const long long rb = (long long)(old >> 24);
+            const int ib = (int)(old & 0xFFFFFFull);
+            if (rb + n > d.pair_cap || ib + nit > d.item_cap) {
+                if (lane == 0) atomicOr(&d.ctl->overflow, 1);
+                n = 0;
+                break;
+            }
+            ++rows_hit;
+            for (int t = lane; t < nit; t += 32)
+                d.items[ib + t] = make_int4(i, (int)rb + t * ITEM_PAIRS, min(ITEM_PAIRS, n - t * ITEM_PAIRS) | (n << 8), (int)rb);
+            __syncwarp();
+            if (n <= DETECT_HB) {
+                // up to 8 pairs per lane; their gathers are issued together
+                int jj[DETECT_HB / 32];
+                T ww[DETECT_HB / 32];
+#pragma unroll
+                for (int q = 0; q < DETECT_HB / 32; ++q) {
+                    const int t = lane + 32 * q;
+                    jj[q] = t < n ? hb[t] : -1;
+                    if (jj[q] >= 0) ww[q] = __ldg(d.W + (int64_t)i * d.ld + jj[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < DETECT_HB / 32; ++q) {
+                    if (jj[q] < 0) continue;
+                    const int j = jj[q];
+                    T init = ww[q];
+                    if (kind == 1)
+                        init = M::mn(init, M::mn(M::add(wn_x, M::mn(ys[j], M::inf())),
+                                                 M::add(wn_x2, TWO ? M::mn(y2s[j], M::inf()) : M::inf())));
+                    d.pairs[rb + lane + 32 * q] = j;
+                    d.D[(int64_t)i * d.ld + j] = init;
+                    if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
+                    atomicAdd(&d.col_count[j], 1);
+                }
+                __syncwarp();  // the buffer is reused by the next row
+                break;
+            }
+            det_wide_write<T, TWO>(d, kind, i, a, rb, s1, s2, use1, use2, wn_x, wn_x2, ys, y2s);
         }
-        for (int t = lane; t < nit; t += 32)
-            d.items[ib + t] = make_int4(i, (int)base + t * ITEM_PAIRS,
-                                        min(ITEM_PAIRS, n - t * ITEM_PAIRS) | (n << 8), (int)base);
-        __syncwarp();  // hb is reused by the next row
     }
     if (lane == 0 && rows_hit) atomicAdd(&d.ctl->n_rows, rows_hit);
 }

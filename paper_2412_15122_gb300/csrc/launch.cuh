@@ -61,7 +61,8 @@ cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, con
     if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d, rows_per); })) != cudaSuccess) return e;
     int gr = c.relax_grid;
     size_t sm = (size_t)d.span * sizeof(int32_t);
-    return launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p); });
+    if ((e = launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p); })) != cudaSuccess) return e;
+    return launch(c, "insert_finish", [&] { k_insert_finish<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, p); });
 }
 
 template <typename T> cudaError_t run_decrease(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w) {
@@ -70,8 +71,8 @@ template <typename T> cudaError_t run_decrease(const LaunchCtx &c, const Dev<T> 
     return launch(c, "decrease_sweep", [&] { k_dec_sweep<T><<<c.num_sms * 2, 256, 0, c.stream>>>(d, w); });
 }
 
-template <typename T> static size_t detect_smem(const Dev<T> &d) {
-    return (size_t)d.span * sizeof(T) * (d.undirected ? 2 : 1);
+template <typename T> static size_t detect_smem(const Dev<T> &d, bool two) {
+    return (size_t)d.span * sizeof(T) * (two ? 2 : 1);
 }
 
 // Both repair kernels are launched; the one whose path the device-side
@@ -95,7 +96,7 @@ template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d
 template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
-    if ((e = launch(c, "detect_remove", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 0, k, -1, (T)0, (T)0); })) != cudaSuccess) return e;
+    if ((e = launch(c, "detect_remove", [&] { k_detect<T, false><<<c.detect_grid, 256, detect_smem(d, false), c.stream>>>(d, 0, k, -1, (T)0, (T)0); })) != cudaSuccess) return e;
     if ((e = launch(c, "tombstone", [&] { k_tombstone<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
     return run_repair<T>(c, d, cfg);
 }
@@ -104,7 +105,11 @@ template <typename T>
 cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_old, T w_new, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "increase_prepass", [&] { k_inc_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w_old, w_new); })) != cudaSuccess) return e;
-    if ((e = launch(c, "detect_increase", [&] { k_detect<T><<<c.detect_grid, 256, detect_smem(d), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
+    if (d.undirected) {
+        if ((e = launch(c, "detect_increase", [&] { k_detect<T, true><<<c.detect2_grid, 256, detect_smem(d, true), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
+    } else {
+        if ((e = launch(c, "detect_increase", [&] { k_detect<T, false><<<c.detect_grid, 256, detect_smem(d, false), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
+    }
     return run_repair<T>(c, d, cfg);
 }
 
@@ -123,11 +128,14 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&warm_sm, k_repair_warm<T>, 256, 0)) != cudaSuccess) return e;
     if (warm_sm < 1) return cudaErrorInvalidConfiguration;
     c.warm_grid = warm_sm * c.num_sms;
-    size_t det = row * (undirected ? 2 : 1);
-    if ((e = cudaFuncSetAttribute(k_detect<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)det)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_detect<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row)) != cudaSuccess) return e;
     int det_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_detect<T>, 256, det)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_detect<T, false>, 256, row)) != cudaSuccess) return e;
     c.detect_grid = std::max(1, det_sm) * c.num_sms;
+    if ((e = cudaFuncSetAttribute(k_detect<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * row))) != cudaSuccess) return e;
+    int det2_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det2_sm, k_detect<T, true>, 256, 2 * row)) != cudaSuccess) return e;
+    c.detect2_grid = std::max(1, det2_sm) * c.num_sms;
     size_t rel = (size_t)ld * sizeof(int32_t);
     if ((e = cudaFuncSetAttribute(k_insert_relax<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rel)) != cudaSuccess) return e;
     int rel_sm = 0;

@@ -18,6 +18,7 @@ struct LaunchCtx {
     int detect_grid = 1;
     int relax_grid = 1;
     int warm_grid = 1;
+    int detect2_grid = 1;
 };
 
 template <typename T> cudaError_t run_fill(const LaunchCtx &, T *, T, int64_t);

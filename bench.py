@@ -294,18 +294,22 @@ def main():
             issue(g, op, dvec)
             st = g.stats()
             k = stats.setdefault(st["op"], {"count": 0, "paths": {}, "pairs": 0, "rows": 0, "passes": 0,
-                                             "sweep_rows": 0, "max_pairs": 0})
+                                             "sweep_rows": 0, "max_pairs": 0, "pairs_rechecked": 0,
+                                             "warm_pass1_us": 0.0, "warm_total_us": 0.0})
             k["count"] += 1
             k["paths"][st["path"]] = k["paths"].get(st["path"], 0) + 1
             k["pairs"] += st["affected_pairs"]
             k["rows"] += st["affected_rows"]
             k["passes"] += st["passes"]
             k["sweep_rows"] += st["sweep_rows"]
+            k["pairs_rechecked"] += st["pairs_rechecked"]
+            k["warm_pass1_us"] += st["warm_pass1_us"]
+            k["warm_total_us"] += st["warm_total_us"]
             k["max_pairs"] = max(k["max_pairs"], st["affected_pairs"])
         g.close()
         for k in stats.values():
             c = max(1, k["count"])
-            for f in ("pairs", "rows", "passes", "sweep_rows"):
+            for f in ("pairs", "rows", "passes", "sweep_rows", "pairs_rechecked", "warm_pass1_us", "warm_total_us"):
                 k["avg_" + f] = round(k.pop(f) / c, 2)
     del dvec
 

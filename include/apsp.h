@@ -119,6 +119,9 @@ typedef struct {
     float cost;               /* Cost = affected_rows / (N - 1), Eq. (equ:cost_defi) */
     float model_warm;         /* model's predicted log2 microseconds, warm / cold (0 if unused) */
     float model_cold;
+    int64_t pairs_rechecked;  /* pair evaluations in re-relaxation passes after the first */
+    float warm_pass1_us;      /* device time of the first re-relaxation pass */
+    float warm_total_us;      /* device time of the whole warm repair */
 } apsp_stats;
 
 typedef struct {

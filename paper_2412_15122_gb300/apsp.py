@@ -42,7 +42,8 @@ class apsp_stats(ctypes.Structure):
                 ("node2", ctypes.c_int32), ("n_live", ctypes.c_int32), ("affected_rows", ctypes.c_int32),
                 ("affected_pairs", ctypes.c_int64), ("sweep_rows", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("overflow", ctypes.c_int32), ("cold_reason", ctypes.c_int32), ("cost", ctypes.c_float),
-                ("model_warm", ctypes.c_float), ("model_cold", ctypes.c_float)]
+                ("model_warm", ctypes.c_float), ("model_cold", ctypes.c_float),
+                ("pairs_rechecked", ctypes.c_int64), ("warm_pass1_us", ctypes.c_float), ("warm_total_us", ctypes.c_float)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -104,6 +104,7 @@ struct Ctl {
     int32_t chunk_next[64];   // pass-1 work counters, one per column chunk
     unsigned long long alloc; // detection reservations: (pairs << 24) | work items
     unsigned long long pairs_evaluated;  // semi-naive pair evaluations (passes >= 2)
+    unsigned long long t_start, t_pass1, t_end;  // device timestamps (ns) of the warm repair
     uint32_t err;             // sticky until the host reads it
 };
 

@@ -724,6 +724,11 @@ apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *s) {
         s->model_warm = c.model_warm;
         s->model_cold = c.model_cold;
         s->sweep_rows = c.r_count;
+        s->pairs_rechecked = (int64_t)c.pairs_evaluated;
+        if (c.path == apsp::PATH_WARM && c.t_end > c.t_start) {
+            s->warm_pass1_us = (float)((double)(c.t_pass1 - c.t_start) * 1e-3);
+            s->warm_total_us = (float)((double)(c.t_end - c.t_start) * 1e-3);
+        }
         s->path = c.path == apsp::PATH_COLD ? APSP_PATH_COLD
                 : c.path == apsp::PATH_WARM ? APSP_PATH_WARM : APSP_PATH_TRIVIAL;
         if (op == APSP_OP_REMOVE && c.path == 0) s->path = APSP_PATH_TRIVIAL;

@@ -852,6 +852,7 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
     const int nchunk = (span + PASS1_CHUNK - 1) / PASS1_CHUNK;
     constexpr int CV = PASS1_CHUNK / 128;  // 16-byte vectors per lane per chunk
 
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer_ns();
     // Column lists (which rows are affected in each column) for the
     // semi-naive passes: prefix sums now, filled during pass 1.
     if (blockIdx.x == 0) cta_exclusive_scan(d.col_count, d.col_start, span);
@@ -930,6 +931,9 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
         cv->changed[par ^ 1] = 0;
         cv->item_next[par ^ 1] = 0;
         cv->passes = pass;
+        const unsigned long long now = globaltimer_ns();
+        if (pass == 1) cv->t_pass1 = now;
+        cv->t_end = now;
     };
     if (!grid_barrier(ctl, leader)) return;
 

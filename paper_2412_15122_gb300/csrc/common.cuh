@@ -77,6 +77,8 @@ enum : uint32_t {
 // Decision codes written by the repair kernel.
 enum : int32_t { PATH_NONE = 0, PATH_SWEEP = 1, PATH_TRIVIAL = 2, PATH_WARM = 3, PATH_COLD = 4 };
 
+constexpr int QUEUES = 16;
+
 // Per-graph control block in device memory.  Cleared (except `err`) before
 // each update; read back by the host only for statistics.
 struct Ctl {
@@ -97,11 +99,14 @@ struct Ctl {
     // grid barrier and pass bookkeeping of the repair kernel
     unsigned int bar_count;
     unsigned int bar_gen;
-    int32_t item_next[2];
     int32_t changed[2];
     int32_t stop;
-    int32_t pad_;
-    int32_t chunk_next[64];   // pass-1 work counters, one per column chunk
+    int32_t unit_alloc;       // re-relaxation units reserved by detection
+    // work queues of the re-relaxation: QUEUES counters, each on its own
+    // 128-byte line (warp w takes units from queue w % QUEUES), for pass 1
+    // and for passes >= 2 by parity
+    int32_t q1[QUEUES * 32];
+    int32_t qn[2][QUEUES * 32];
     unsigned long long alloc; // detection reservations: (pairs << 24) | work items
     unsigned long long pairs_evaluated;  // semi-naive pair evaluations (passes >= 2)
     unsigned long long t_start, t_pass1, t_end;  // device timestamps (ns) of the warm repair
@@ -109,7 +114,9 @@ struct Ctl {
 };
 
 constexpr int ITEM_PAIRS = 32;          // affected pairs per re-relaxation work item
-constexpr int PASS1_CHUNK = 512;        // columns of x per pass-1 chunk (working set stays in L2)
+constexpr int PASS1_CHUNK = 256;        // columns of x per pass-1 step (one 16-byte vector pair per lane)
+constexpr int PASS1_GROUP = 4;          // chunks per pass-1 work unit (1024 columns: the window stays in L2)
+constexpr int YSEG = 128;               // intermediates per work unit in passes >= 2
 constexpr int MAX_PASSES = 48;          // path doubling needs <= log2(hops) + 1 passes
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
 

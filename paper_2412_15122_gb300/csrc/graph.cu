@@ -50,13 +50,14 @@ struct apsp_graph {
     int32_t *alive = nullptr;
     void *w_in = nullptr, *w_out = nullptr, *x = nullptr, *x2 = nullptr, *y = nullptr, *y2 = nullptr;
     int32_t *vin_k = nullptr, *vout_k = nullptr, *rlist = nullptr, *pairs = nullptr;
-    int32_t *col_count = nullptr, *col_start = nullptr, *col_fill = nullptr, *colrows = nullptr;
-    uint8_t *rowchg = nullptr, *colchg = nullptr;
+    int32_t *pmin = nullptr, *units = nullptr;
+    uint8_t *pstamp = nullptr, *rstamp = nullptr;
     int4 *items = nullptr;
     Ctl *ctl = nullptr;
     float *model = nullptr;
     int64_t pair_cap = 0;
     int32_t item_cap = 0;
+    int32_t unit_cap = 0;
     apsp_alloc_fn alloc_fn = nullptr;
     apsp_free_fn free_fn = nullptr;
     void *alloc_ctx = nullptr;
@@ -222,15 +223,14 @@ template <typename T> Dev<T> dev_of(apsp_graph *g) {
     d.rlist = g->rlist;
     d.items = g->items;
     d.pairs = g->pairs;
-    d.col_count = g->col_count;
-    d.col_start = g->col_start;
-    d.col_fill = g->col_fill;
-    d.colrows = g->colrows;
-    d.rowchg = g->rowchg;
-    d.colchg = g->colchg;
+    d.pmin = g->pmin;
+    d.pstamp = g->pstamp;
+    d.rstamp = g->rstamp;
+    d.units = g->units;
     d.ctl = g->ctl;
     d.pair_cap = g->pair_cap;
     d.item_cap = g->item_cap;
+    d.unit_cap = g->unit_cap;
     return d;
 }
 
@@ -323,17 +323,16 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->item_cap = (int32_t)(g->pair_cap / apsp::ITEM_PAIRS + ld);
     g->pairs = (int32_t *)dalloc(g, g->pair_cap * 4);
     g->items = (int4 *)dalloc(g, (size_t)g->item_cap * sizeof(int4));
-    g->col_count = (int32_t *)dalloc(g, ld * 4);
-    g->col_start = (int32_t *)dalloc(g, (ld + 1) * 4);
-    g->col_fill = (int32_t *)dalloc(g, ld * 4);
-    g->colrows = (int32_t *)dalloc(g, g->pair_cap * 4);
-    g->rowchg = (uint8_t *)dalloc(g, 3 * ld);
-    g->colchg = (uint8_t *)dalloc(g, 3 * ld);
+    g->unit_cap = (int32_t)std::min<int64_t>(g->pair_cap, (int64_t)1 << 30);
+    g->pmin = (int32_t *)dalloc(g, g->pair_cap * 4);
+    g->pstamp = (uint8_t *)dalloc(g, g->pair_cap);
+    g->rstamp = (uint8_t *)dalloc(g, ld);
+    g->units = (int32_t *)dalloc(g, (size_t)g->unit_cap * 4);
     g->ctl = (Ctl *)dalloc(g, sizeof(Ctl));
     g->model = (float *)dalloc(g, apsp::MLP_NPARAM * sizeof(float));
     if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
         !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->ctl || !g->model ||
-        !g->col_count || !g->col_start || !g->col_fill || !g->colrows || !g->rowchg || !g->colchg)
+        !g->pmin || !g->pstamp || !g->rstamp || !g->units)
         return APSP_E_NOMEM;
     if (cudaMallocHost(&g->pin, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
     if (cudaMallocHost(&g->pin_fetch, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;

@@ -40,16 +40,15 @@ template <typename T> struct Dev {
     T *x, *x2, *y, *y2;       // staged rows / columns of the current update
     int32_t *rlist;           // prepass row list
     int4 *items;              // (row, first pair, pair count | row's pair count << 8, row's first pair)
-    int32_t *pairs;           // affected column per pair, grouped by row
-    int32_t *col_count;       // affected pairs per column (span)
-    int32_t *col_start;       // exclusive prefix of col_count (span + 1)
-    int32_t *col_fill;        // fill cursor per column (span)
-    int32_t *colrows;         // affected row per pair, grouped by column
-    uint8_t *rowchg;          // 3 x ld: rows changed in a pass (triple-buffered)
-    uint8_t *colchg;          // 3 x ld: columns changed in a pass
+    int32_t *pairs;           // affected column per pair, grouped by row (columns ascending)
+    int32_t *pmin;            // per pair: first-pass minimum as an ordered key
+    uint8_t *pstamp;          // per pair: last pass that lowered it (0: none yet)
+    uint8_t *rstamp;          // per row (ld): last pass that lowered one of its pairs
+    int32_t *units;           // work units of passes >= 2: item | intermediate segment << 24
     Ctl *ctl;
     int64_t pair_cap;
     int32_t item_cap;
+    int32_t unit_cap;
 };
 
 template <typename T> __device__ __forceinline__ T col_src(const Dev<T> &d, int row_of_T, int i) {
@@ -480,15 +479,9 @@ __global__ void __launch_bounds__(256, 3) k_dec_sweep(Dev<T> d, T w) {
 // `pairs`, and are cut into work items of ITEM_PAIRS pairs.
 // --------------------------------------------------------------------------
 
-// Clears the per-update column lists and change flags of slot i.
+// Clears the per-update row change stamp of slot i.
 template <typename T> __device__ __forceinline__ void clear_repair_scratch(const Dev<T> &d, int i) {
-    d.col_count[i] = 0;
-    d.col_fill[i] = 0;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        d.rowchg[b * d.ld + i] = 0;
-        d.colchg[b * d.ld + i] = 0;
-    }
+    d.rstamp[i] = 0;
 }
 
 template <typename T>
@@ -529,8 +522,6 @@ __global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
     warp_append(in_r, i, d.rlist, &d.ctl->r_count);
 }
 
-constexpr int UNIT_PAIRS = 4;                              // pairs per work unit in passes >= 2
-constexpr int UNITS_PER_ITEM = 32 / UNIT_PAIRS;
 constexpr int DETECT_HB = 256;  // per-warp buffer of a row's affected columns
 
 // Second scan of a row with more affected pairs than the warp buffer holds:
@@ -601,9 +592,10 @@ __device__ __noinline__ void det_wide_write(const Dev<T> &d, int kind, int i, in
                     init = M::mn(init, M::mn(M::add(wn_x, M::mn(ys[j], M::inf())),
                                              M::add(wn_x2, TWO ? M::mn(y2s[j], M::inf()) : M::inf())));
                 d.pairs[base + off] = j;
+                d.pmin[base + off] = M::key(init);
+                d.pstamp[base + off] = 0;
                 d.D[(int64_t)i * d.ld + j] = init;
                 if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
-                atomicAdd(&d.col_count[j], 1);
                 ++off;
             }
         }
@@ -710,12 +702,19 @@ __global__ void __launch_bounds__(256, 3) k_detect(Dev<T> d, int kind, int a, in
             if (n == 0) break;
             // reserve the row's slots
             const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
+            const int nseg = (n + YSEG - 1) / YSEG;
+            const int nun = nit * nseg;
             unsigned long long old = 0;
-            if (lane == 0) old = atomicAdd(&d.ctl->alloc, ((unsigned long long)n << 24) | (unsigned long long)nit);
+            int ub = 0;
+            if (lane == 0) {
+                old = atomicAdd(&d.ctl->alloc, ((unsigned long long)n << 24) | (unsigned long long)nit);
+                ub = atomicAdd(&d.ctl->unit_alloc, nun);
+            }
             old = __shfl_sync(0xffffffffu, old, 0);
+            ub = __shfl_sync(0xffffffffu, ub, 0);
             const long long rb = (long long)(old >> 24);
             const int ib = (int)(old & 0xFFFFFFull);
-            if (rb + n > d.pair_cap || ib + nit > d.item_cap) {
+            if (rb + n > d.pair_cap || ib + nit > d.item_cap || (long long)ub + nun > d.unit_cap) {
                 if (lane == 0) atomicOr(&d.ctl->overflow, 1);
                 n = 0;
                 break;
@@ -723,6 +722,8 @@ __global__ void __launch_bounds__(256, 3) k_detect(Dev<T> d, int kind, int a, in
             ++rows_hit;
             for (int t = lane; t < nit; t += 32)
                 d.items[ib + t] = make_int4(i, (int)rb + t * ITEM_PAIRS, min(ITEM_PAIRS, n - t * ITEM_PAIRS) | (n << 8), (int)rb);
+            for (int u = lane; u < nun; u += 32)
+                d.units[ub + u] = (int32_t)((unsigned)(ib + u / nseg) | ((unsigned)(u % nseg) << 24));
             __syncwarp();
             if (n <= DETECT_HB) {
                 // up to 8 pairs per lane; their gathers are issued together
@@ -743,9 +744,10 @@ __global__ void __launch_bounds__(256, 3) k_detect(Dev<T> d, int kind, int a, in
                         init = M::mn(init, M::mn(M::add(wn_x, M::mn(ys[j], M::inf())),
                                                  M::add(wn_x2, TWO ? M::mn(y2s[j], M::inf()) : M::inf())));
                     d.pairs[rb + lane + 32 * q] = j;
+                    d.pmin[rb + lane + 32 * q] = M::key(init);
+                    d.pstamp[rb + lane + 32 * q] = 0;
                     d.D[(int64_t)i * d.ld + j] = init;
                     if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
-                    atomicAdd(&d.col_count[j], 1);
                 }
                 __syncwarp();  // the buffer is reused by the next row
                 break;
@@ -779,13 +781,26 @@ __global__ void k_tombstone(Dev<T> d, int k) {
 // device and then either re-relaxes the affected pairs to a fixed point or
 // recomputes D by blocked Floyd-Warshall.
 //
-// Warm (restricted re-relaxation, replacing Algorithm 5's per-row Dijkstra):
-// every listed pair starts at an achievable upper bound; each pass sets
-//     D[i][j] = min(D[i][j], min_x D[i][x] + D[x][j])
-// for the listed pairs only (row i staged in shared memory, column j read as
-// row j of DT).  Unlisted pairs are exact and values only decrease, so a pass
-// that changes nothing leaves the exact APSP matrix; path doubling bounds the
-// passes by about log2(hops) + 2.
+// Warm (restricted re-relaxation, replacing Algorithm 5's per-row Dijkstra).
+// Every listed pair (i, j) starts at an achievable upper bound (its direct
+// edge, or a path through the new edge weight); unlisted pairs are exact.
+//
+// Pass 1 sets every listed pair to min over all x of D[i][x] + D[x][j],
+// reading only the starting values (results go to `pmin`, D is untouched), so
+// the pass is one read-only sweep taken in chunks of x that keep the touched
+// rows and columns in L2.  After it, a pair is exact unless the predecessor
+// of j on its new shortest path from i is itself a listed target of row i:
+// otherwise that predecessor y has D[i][y] exact and D[y][j] <= W[y][j].
+//
+// Passes >= 2 therefore only relax each row through its own listed targets,
+//     D[i][j] = min(D[i][j], min over listed y of D[i][y] + D[y][j]),
+// a Bellman-Ford over the row's list with any achievable D[y][j] <= W[y][j]
+// as the arc length.  Semi-naive: after pass 2 (which takes every y) a pair
+// is re-examined only through y lowered in the previous pass, and only y
+// with D[i][y] < D[i][j] can help (weights are non-negative).  A pass that
+// lowers nothing leaves every row at its fixed point, which is exact.
+// Rows never wait for each other: concurrent readers see either value of a
+// pair being lowered, and both are achievable upper bounds.
 // --------------------------------------------------------------------------
 
 struct RepairCfg {
@@ -798,47 +813,23 @@ struct RepairCfg {
     float feat_dw;       // relative weight change
 };
 
-// Exclusive prefix sum of in[0..n) into out[0..n] by one CTA.
-__device__ inline void cta_exclusive_scan(const int32_t *in, int32_t *out, int n) {
-    __shared__ int32_t part[256];
-    const int t = threadIdx.x;
-    const int per = (n + 255) / 256;
-    const int b = min(n, t * per), e = min(n, b + per);
-    int s = 0;
-    for (int k = b; k < e; ++k) s += __ldcg(in + k);
-    part[t] = s;
-    __syncthreads();
-    for (int off = 1; off < 256; off <<= 1) {
-        int v = t >= off ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int run = t ? part[t - 1] : 0;
-    for (int k = b; k < e; ++k) {
-        out[k] = run;
-        run += __ldcg(in + k);
-    }
-    if (t == 255) out[n] = part[255];
-    __syncthreads();
-}
-
-// Lowers D[i][j] (and DT[j][i]) to v if v is smaller and records the change
-// for pass `pass`; returns whether it lowered it.  An atomic min on the
-// ordered key: in pass 1 different warps handle different x-chunks of the
-// same pair at the same time, and a plain compare-then-store could let a
-// worse chunk result overwrite a better one.
-template <typename T>
-__device__ __forceinline__ bool relax_write(Dev<T> &d, int i, int j, T v, int pass) {
+// Minimum of four per-lane values over the warp with 6 shuffles: returns, in
+// every lane of each group of 8 lanes g = lane / 8, the minimum of value g.
+template <typename T> __device__ __forceinline__ T warp_min4(T a0, T a1, T a2, T a3, int lane) {
     using M = MinPlus<T>;
-    const int32_t key = M::key(v);
-    const int32_t old = atomicMin(reinterpret_cast<int32_t *>(d.D + (int64_t)i * d.ld + j), key);
-    if (key >= old) return false;
-    if (d.DT) atomicMin(reinterpret_cast<int32_t *>(d.DT + (int64_t)j * d.ld + i), key);
-    const int buf = pass % 3;
-    d.rowchg[buf * d.ld + i] = 1;
-    d.colchg[buf * d.ld + j] = 1;
-    return true;
+    const bool hi = lane & 16;
+    const T s0 = hi ? a0 : a2, s1 = hi ? a1 : a3;
+    T k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
+    k0 = M::mn(k0, __shfl_xor_sync(0xffffffffu, s0, 16));
+    k1 = M::mn(k1, __shfl_xor_sync(0xffffffffu, s1, 16));
+    const bool b3 = lane & 8;
+    const T s = b3 ? k0 : k1;
+    T k = b3 ? k1 : k0;
+    k = M::mn(k, __shfl_xor_sync(0xffffffffu, s, 8));
+    k = M::mn(k, __shfl_xor_sync(0xffffffffu, k, 4));
+    k = M::mn(k, __shfl_xor_sync(0xffffffffu, k, 2));
+    k = M::mn(k, __shfl_xor_sync(0xffffffffu, k, 1));
+    return k;
 }
 
 template <typename T>
@@ -848,88 +839,93 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
     Ctl *ctl = d.ctl;
     const int lane = threadIdx.x & 31;
     const int span = d.span;
+    const int64_t ld = d.ld;
     const T *cols = d.DT ? d.DT : d.D;   // row j of `cols` is column j of D
     const int nchunk = (span + PASS1_CHUNK - 1) / PASS1_CHUNK;
     constexpr int CV = PASS1_CHUNK / 128;  // 16-byte vectors per lane per chunk
+    const long long n_units = *(volatile const int32_t *)&ctl->unit_alloc;
 
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer_ns();
-    // Column lists (which rows are affected in each column) for the
-    // semi-naive passes: prefix sums now, filled during pass 1.
-    if (blockIdx.x == 0) cta_exclusive_scan(d.col_count, d.col_start, span);
-    if (!grid_barrier(ctl, NoLeader{})) return;
 
-    // Pass 1: every pair against every intermediate x, x taken in chunks so
-    // the rows and columns touched by all warps at once stay in L2.  One warp
-    // per work item (a row and up to ITEM_PAIRS of its pairs); the row chunk
-    // stays in registers and two pairs' column chunks are loaded at a time.
-    bool changed = false;
-    for (int c = 0; c < nchunk; ++c) {
-        const int x0 = c * PASS1_CHUNK;
-        const int nv = (min(span, x0 + PASS1_CHUNK) - x0) / 4;
+    const int wq = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % QUEUES) * 32;
+
+    // Pass 1: one warp per unit = (work item, group of PASS1_GROUP chunks of
+    // x), units ordered group-major so all warps sweep the same window of
+    // columns.  Per chunk the row's slice stays in registers and four pairs'
+    // column slices are loaded at a time; lane t keeps pair t's running
+    // minimum, stored once per unit with a fire-and-forget atomic min.
+    {
+        const int ngroups = (nchunk + PASS1_GROUP - 1) / PASS1_GROUP;
+        const int n1 = n_items * ngroups;   // items < 2^19 and groups <= 18 at the largest capacity
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&ctl->q1[wq], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
         while (true) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(&ctl->chunk_next[c], 1);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= n_items) break;
-            const int4 item = d.items[it];
-            const int i = item.x;
+            const int u = (wq >> 5) + QUEUES * t;
+            if (u >= n1 || u < 0) break;
+            const int g = u / n_items, it = u - g * n_items;
+            if (lane == 0) t = atomicAdd(&ctl->q1[wq], 1);   // next unit, in flight meanwhile
+            const int4 item = __ldcg(d.items + it);
             const int cnt = item.z & 0xff;
-            T *Dr = d.D + (int64_t)i * d.ld;
-            V4 rv[CV];
+            const int jl = lane < cnt ? __ldcg(d.pairs + item.y + lane) : 0;
+            const T *Dr = d.D + (int64_t)item.x * ld;
+            T pacc = M::inf();
+            for (int sc = 0; sc < PASS1_GROUP; ++sc) {
+                const int x0 = (g * PASS1_GROUP + sc) * PASS1_CHUNK;
+                if (x0 >= span) break;
+                const int nv = (min(span, x0 + PASS1_CHUNK) - x0) / 4;
+                const V4 *r4 = reinterpret_cast<const V4 *>(Dr + x0);
+                V4 rv[CV];
 #pragma unroll
-            for (int k = 0; k < CV; ++k)
-                if (lane + 32 * k < nv) rv[k] = __ldcg(reinterpret_cast<const V4 *>(Dr + x0) + lane + 32 * k);
-            for (int q = 0; q < cnt; q += 2) {
-                const bool second = q + 1 < cnt;
-                const int j0 = d.pairs[item.y + q];
-                const int j1 = second ? d.pairs[item.y + q + 1] : j0;
-                const V4 *c0 = reinterpret_cast<const V4 *>(cols + (int64_t)j0 * d.ld + x0);
-                const V4 *c1 = reinterpret_cast<const V4 *>(cols + (int64_t)j1 * d.ld + x0);
-                V4 a[CV], b[CV];
+                for (int k = 0; k < CV; ++k)
+                    if (lane + 32 * k < nv) rv[k] = __ldcg(r4 + lane + 32 * k);
+                for (int q = 0; q < cnt; q += 4) {
+                    int jq[4];
+                    jq[0] = __shfl_sync(0xffffffffu, jl, q);
 #pragma unroll
-                for (int k = 0; k < CV; ++k) {
-                    if (lane + 32 * k < nv) {
-                        a[k] = __ldcg(c0 + lane + 32 * k);
-                        if (second) b[k] = __ldcg(c1 + lane + 32 * k);
+                    for (int u4 = 1; u4 < 4; ++u4) {
+                        const int jj = __shfl_sync(0xffffffffu, jl, (q + u4) & 31);
+                        jq[u4] = q + u4 < cnt ? jj : jq[0];
                     }
-                }
-                T acc0 = M::inf(), acc1 = M::inf();
+                    V4 a[4][CV];
 #pragma unroll
-                for (int k = 0; k < CV; ++k) {
-                    if (lane + 32 * k < nv) {
-                        acc0 = M::add_min(rv[k].x, a[k].x, acc0);
-                        acc0 = M::add_min(rv[k].y, a[k].y, acc0);
-                        acc0 = M::add_min(rv[k].z, a[k].z, acc0);
-                        acc0 = M::add_min(rv[k].w, a[k].w, acc0);
-                        if (second) {
-                            acc1 = M::add_min(rv[k].x, b[k].x, acc1);
-                            acc1 = M::add_min(rv[k].y, b[k].y, acc1);
-                            acc1 = M::add_min(rv[k].z, b[k].z, acc1);
-                            acc1 = M::add_min(rv[k].w, b[k].w, acc1);
+                    for (int u4 = 0; u4 < 4; ++u4) {
+                        const V4 *c4 = reinterpret_cast<const V4 *>(cols + (int64_t)jq[u4] * ld + x0);
+#pragma unroll
+                        for (int k = 0; k < CV; ++k)
+                            if (lane + 32 * k < nv) a[u4][k] = __ldcg(c4 + lane + 32 * k);
+                    }
+                    T acc[4];
+#pragma unroll
+                    for (int u4 = 0; u4 < 4; ++u4) {
+                        acc[u4] = M::inf();
+#pragma unroll
+                        for (int k = 0; k < CV; ++k) {
+                            if (lane + 32 * k < nv) {
+                                acc[u4] = M::add_min(rv[k].x, a[u4][k].x, acc[u4]);
+                                acc[u4] = M::add_min(rv[k].y, a[u4][k].y, acc[u4]);
+                                acc[u4] = M::add_min(rv[k].z, a[u4][k].z, acc[u4]);
+                                acc[u4] = M::add_min(rv[k].w, a[u4][k].w, acc[u4]);
+                            }
                         }
                     }
-                }
-                acc0 = warp_min(acc0);
-                acc1 = warp_min(acc1);
-                if (lane == 0) {
-                    if (acc0 < __ldcg(Dr + j0) && relax_write(d, i, j0, acc0, 1)) changed = true;
-                    if (c == 0) d.colrows[__ldcg(d.col_start + j0) + atomicAdd(&d.col_fill[j0], 1)] = i;
-                    if (second) {
-                        if (acc1 < __ldcg(Dr + j1) && relax_write(d, i, j1, acc1, 1)) changed = true;
-                        if (c == 0) d.colrows[__ldcg(d.col_start + j1) + atomicAdd(&d.col_fill[j1], 1)] = i;
-                    }
+                    const T r = warp_min4(acc[0], acc[1], acc[2], acc[3], lane);
+                    // pair q + g' sits in lanes 8g'..8g'+7; hand it to lane q + g'
+                    const T got = __shfl_sync(0xffffffffu, r, ((lane - q) * 8) & 31);
+                    if (lane >= q && lane < q + 4) pacc = M::mn(pacc, got);
                 }
             }
+            if (lane < cnt) atomicMin(d.pmin + item.y + lane, M::key(pacc));
+            t = __shfl_sync(0xffffffffu, t, 0);
         }
     }
-    if (changed) *(volatile int32_t *)&ctl->changed[1] = 1;
     int pass = 1;
     auto leader = [&]() {
         volatile Ctl *cv = ctl;
         const int par = pass & 1;
-        cv->stop = cv->changed[par] == 0;
+        cv->stop = pass >= 2 && cv->changed[par] == 0;
         cv->changed[par ^ 1] = 0;
-        cv->item_next[par ^ 1] = 0;
+        for (int q = 0; q < QUEUES; ++q) cv->qn[par ^ 1][32 * q] = 0;
         cv->passes = pass;
         const unsigned long long now = globaltimer_ns();
         if (pass == 1) cv->t_pass1 = now;
@@ -937,91 +933,87 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
     };
     if (!grid_barrier(ctl, leader)) return;
 
-    // Passes >= 2 (semi-naive): only affected entries change, so a pair can
-    // improve only through x in its row's or its column's affected list, and
-    // only if that row or column changed in the previous pass.
-    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    const int full_limit = max(64, span / 4);
+    // Passes >= 2: one warp per unit = (work item, segment of YSEG of the
+    // row's listed targets y); lane t owns pair t of the item and gathers
+    // D[y][j_t] for up to 8 y at a time.  Pass 2 reads D[i][.] of listed
+    // pairs from pmin and stores every pair; later passes store only pairs
+    // they lower.  Stores are atomic minima (several units share a pair).
     for (pass = 2; pass <= MAX_PASSES && !*(volatile int32_t *)&ctl->stop; ++pass) {
-        const uint8_t *rprev = d.rowchg + ((pass - 1) % 3) * d.ld;
-        const uint8_t *cprev = d.colchg + ((pass - 1) % 3) * d.ld;
-        uint8_t *rclr = d.rowchg + ((pass + 1) % 3) * d.ld;
-        uint8_t *cclr = d.colchg + ((pass + 1) % 3) * d.ld;
-        for (int64_t t = gtid; t < span; t += gsz) { rclr[t] = 0; cclr[t] = 0; }
         const int par = pass & 1;
-        changed = false;
+        bool changed = false;
         unsigned long long evals = 0;
-        const int n_units = n_items * UNITS_PER_ITEM;
         while (true) {
-            int un = 0;
-            if (lane == 0) un = atomicAdd(&ctl->item_next[par], 1);
-            un = __shfl_sync(0xffffffffu, un, 0);
+            int tq = 0;
+            if (lane == 0) tq = atomicAdd(&ctl->qn[par][wq], 1);
+            tq = __shfl_sync(0xffffffffu, tq, 0);
+            const long long un = (long long)(wq >> 5) + (long long)QUEUES * tq;
             if (un >= n_units) break;
-            const int4 item = d.items[un / UNITS_PER_ITEM];
-            const int q0 = (un % UNITS_PER_ITEM) * UNIT_PAIRS;
+            const int code = __ldcg(d.units + un);
+            const int4 item = __ldcg(d.items + (code & 0xFFFFFF));
+            const int seg = (int)((unsigned)code >> 24);
             const int i = item.x;
-            const int cnt = item.z & 0xff;
-            if (q0 >= cnt) continue;
-            const int row_cnt = item.z >> 8;
-            const bool rch = __ldcg(rprev + i) != 0;
-            const T *Dr = d.D + (int64_t)i * d.ld;
-            const int32_t *Ai = d.pairs + item.w;
-            for (int q = q0; q < min(cnt, q0 + UNIT_PAIRS); ++q) {
-                const int j = d.pairs[item.y + q];
-                if (!rch && __ldcg(cprev + j) == 0) continue;
-                const int cb = __ldcg(d.col_start + j), ce = __ldcg(d.col_start + j + 1);
-                const T *cj = cols + (int64_t)j * d.ld;
-                T acc = M::inf();
-                if (row_cnt + (ce - cb) <= full_limit) {
-                    // x over the row's affected columns (sorted) and the
-                    // column's affected rows, 4 independent gathers per lane
-                    T a1 = M::inf(), a2 = M::inf(), a3 = M::inf();
-                    int t = lane;
-                    for (; t + 96 < row_cnt; t += 128) {
-                        const int x0 = __ldcg(Ai + t), x1 = __ldcg(Ai + t + 32), x2 = __ldcg(Ai + t + 64),
-                                  x3 = __ldcg(Ai + t + 96);
-                        acc = M::add_min(__ldcg(Dr + x0), __ldcg(cj + x0), acc);
-                        a1 = M::add_min(__ldcg(Dr + x1), __ldcg(cj + x1), a1);
-                        a2 = M::add_min(__ldcg(Dr + x2), __ldcg(cj + x2), a2);
-                        a3 = M::add_min(__ldcg(Dr + x3), __ldcg(cj + x3), a3);
-                    }
-                    for (; t < row_cnt; t += 32) {
-                        const int x = __ldcg(Ai + t);
-                        acc = M::add_min(__ldcg(Dr + x), __ldcg(cj + x), acc);
-                    }
-                    t = cb + lane;
-                    for (; t + 96 < ce; t += 128) {
-                        const int x0 = __ldcg(d.colrows + t), x1 = __ldcg(d.colrows + t + 32),
-                                  x2 = __ldcg(d.colrows + t + 64), x3 = __ldcg(d.colrows + t + 96);
-                        acc = M::add_min(__ldcg(Dr + x0), __ldcg(cj + x0), acc);
-                        a1 = M::add_min(__ldcg(Dr + x1), __ldcg(cj + x1), a1);
-                        a2 = M::add_min(__ldcg(Dr + x2), __ldcg(cj + x2), a2);
-                        a3 = M::add_min(__ldcg(Dr + x3), __ldcg(cj + x3), a3);
-                    }
-                    for (; t < ce; t += 32) {
-                        const int x = __ldcg(d.colrows + t);
-                        acc = M::add_min(__ldcg(Dr + x), __ldcg(cj + x), acc);
-                    }
-                    acc = M::mn(M::mn(acc, a1), M::mn(a2, a3));
-                } else {
-                    const V4 *r4 = reinterpret_cast<const V4 *>(Dr);
-                    const V4 *c4 = reinterpret_cast<const V4 *>(cj);
-#pragma unroll 8
-                    for (int v = lane; v < span / 4; v += 32) {
-                        V4 av = __ldcg(r4 + v), bv = __ldcg(c4 + v);
-                        acc = M::add_min(av.x, bv.x, acc);
-                        acc = M::add_min(av.y, bv.y, acc);
-                        acc = M::add_min(av.z, bv.z, acc);
-                        acc = M::add_min(av.w, bv.w, acc);
+            // a row is revisited only if it was lowered in the previous pass
+            // (a stamp of this pass means the same: its units run only then)
+            if (pass > 2 && (int)__ldcg(d.rstamp + i) < pass - 1) continue;
+            const int cnt = item.z & 0xff, nrow = item.z >> 8;
+            const bool mine = lane < cnt;
+            const T *Di = d.D + (int64_t)i * ld;
+            int j = 0;
+            T cur = M::inf();
+            if (mine) {
+                j = __ldcg(d.pairs + item.y + lane);
+                cur = pass == 2 ? M::unkey(__ldcg(d.pmin + item.y + lane)) : __ldcg(Di + j);
+            }
+            const int y1 = min(nrow, (seg + 1) * YSEG);
+            T acc = M::inf();
+            for (int s = seg * YSEG; s < y1; s += 32) {
+                const int yi = s + lane;
+                int y = 0;
+                T dy = M::inf();
+                bool ok = false;
+                if (yi < y1) {
+                    y = __ldcg(d.pairs + item.w + yi);
+                    if (pass == 2) {
+                        dy = M::unkey(__ldcg(d.pmin + item.w + yi));
+                        ok = true;
+                    } else if ((int)__ldcg(d.pstamp + item.w + yi) >= pass - 1) {
+                        dy = __ldcg(Di + y);
+                        ok = true;
                     }
                 }
-                acc = warp_min(acc);
-                if (lane == 0) {
-                    ++evals;
-                    if (acc < __ldcg(Dr + j) && relax_write(d, i, j, acc, pass)) changed = true;
+                unsigned m = __ballot_sync(0xffffffffu, ok);
+                while (m) {
+                    int ys[8];
+                    T dys[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int src = m ? __ffs(m) - 1 : 0;
+                        const bool has = m != 0;
+                        m &= m - 1;
+                        ys[e] = __shfl_sync(0xffffffffu, y, src);
+                        const T dd = __shfl_sync(0xffffffffu, dy, src);
+                        dys[e] = has ? dd : M::inf();
+                    }
+                    T v[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        v[e] = (mine && dys[e] < cur) ? __ldcg(d.D + (int64_t)ys[e] * ld + j) : M::inf();
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc = M::add_min(dys[e], v[e], acc);
                 }
             }
+            if (seg == 0 && lane == 0) evals += cnt;
+            const bool lower = mine && acc < cur;
+            if (mine && (pass == 2 || lower)) {
+                const int32_t key = M::key(M::mn(acc, cur));
+                atomicMin(reinterpret_cast<int32_t *>(d.D + (int64_t)i * ld + j), key);
+                if (d.DT) atomicMin(reinterpret_cast<int32_t *>(d.DT + (int64_t)j * ld + i), key);
+            }
+            if (lower) {
+                d.pstamp[item.y + lane] = (uint8_t)pass;
+                changed = true;
+            }
+            if (__any_sync(0xffffffffu, lower) && lane == 0) d.rstamp[i] = (uint8_t)pass;
         }
         if (changed) *(volatile int32_t *)&ctl->changed[par] = 1;
         if (evals) atomicAdd(&ctl->pairs_evaluated, evals);
@@ -1117,7 +1109,7 @@ __device__ inline void repair_record(Ctl *ctl, int reason, float cost, float pw,
 
 // Warm repair (cooperative launch): restricted re-relaxation.
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_repair_warm(Dev<T> d, RepairCfg cfg) {
+__global__ void __launch_bounds__(256, 3) k_repair_warm(Dev<T> d, RepairCfg cfg) {
     float cost, pw, pc;
     int n_items;
     const int reason = repair_decide(d.ctl, cfg, &cost, &pw, &pc, &n_items);

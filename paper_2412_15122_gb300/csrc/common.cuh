@@ -37,6 +37,10 @@ template <> struct MinPlus<int32_t> {
     // via - d for the batch screen (>= 0 for an exact APSP matrix; 0 = tight)
     __device__ static int32_t slack(int32_t via, int32_t d) { return via - d; }
     __device__ static bool slack_tight(int32_t s) { return s <= 0; }
+    // batch screen: some entry is tight iff s <= max over entries of
+    // screen_bound(d, y) (exact for int32: s + y <= d  <=>  s <= d - y)
+    __device__ static int32_t screen_bound(int32_t d, int32_t y) { return d - y; }
+    __device__ static int32_t screen_floor() { return -INF_I32 - 2; }
     // staged path-leg values: an unreachable leg becomes INF + 1 so that no
     // sum through it can equal a stored distance
     __device__ static int32_t leg(int32_t y) { return y >= INF_I32 ? INF_I32 + 1 : y; }
@@ -56,6 +60,11 @@ template <> struct MinPlus<float> {
     // <= 0 when tight within the relative slack (NaN, from inf - inf, is not)
     __device__ static float slack(float via, float d) { return via - fmaf(d, F32_TIGHT_REL, d); }
     __device__ static bool slack_tight(float s) { return s <= 0.f; }
+    // batch screen with twice the slack, so rounding in the rearranged test
+    // can only let extra batches through to the exact test (inf - inf gives
+    // NaN, which fmaxf ignores)
+    __device__ static float screen_bound(float d, float y) { return fmaf(d, 2.f * F32_TIGHT_REL, d) - y; }
+    __device__ static float screen_floor() { return -inf(); }
     __device__ static float leg(float y) { return y; }
     // non-negative floats (and +inf) order like their bit patterns as int32
     __device__ static int32_t key(float a) { return __float_as_int(a); }
@@ -107,6 +116,9 @@ struct Ctl {
     // and for passes >= 2 by parity
     int32_t q1[QUEUES * 32];
     int32_t qn[2][QUEUES * 32];
+    int32_t qd[QUEUES * 32];  // detection's row queues
+    int32_t hit_rows;         // rows flagged by the detection scan
+    int32_t hit_units;        // (row, batch) units flagged by the detection scan
     unsigned long long alloc; // detection reservations: (pairs << 24) | work items
     unsigned long long pairs_evaluated;  // semi-naive pair evaluations (passes >= 2)
     unsigned long long t_start, t_pass1, t_end;  // device timestamps (ns) of the warm repair
@@ -114,11 +126,18 @@ struct Ctl {
 };
 
 constexpr int ITEM_PAIRS = 32;          // affected pairs per re-relaxation work item
-constexpr int PASS1_CHUNK = 256;        // columns of x per pass-1 step (one 16-byte vector pair per lane)
-constexpr int PASS1_GROUP = 4;          // chunks per pass-1 work unit (1024 columns: the window stays in L2)
+constexpr int PASS1_COLS = 1024;        // columns of x per pass-1 work unit (the swept window stays in L2)
 constexpr int YSEG = 128;               // intermediates per work unit in passes >= 2
 constexpr int MAX_PASSES = 48;          // path doubling needs <= log2(hops) + 1 passes
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
+
+// 16-byte asynchronous global -> shared copy (no registers held while in
+// flight) and the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;

@@ -51,6 +51,10 @@ struct apsp_graph {
     void *w_in = nullptr, *w_out = nullptr, *x = nullptr, *x2 = nullptr, *y = nullptr, *y2 = nullptr;
     int32_t *vin_k = nullptr, *vout_k = nullptr, *rlist = nullptr, *pairs = nullptr;
     int32_t *pmin = nullptr, *units = nullptr;
+    int4 *hrows = nullptr;
+    int4 *hunits = nullptr, *hralloc = nullptr;
+    int32_t *rowcnt = nullptr;
+    long long *hbase = nullptr;
     uint8_t *pstamp = nullptr, *rstamp = nullptr;
     int4 *items = nullptr;
     Ctl *ctl = nullptr;
@@ -221,6 +225,11 @@ template <typename T> Dev<T> dev_of(apsp_graph *g) {
     d.y = (T *)g->y;
     d.y2 = (T *)g->y2;
     d.rlist = g->rlist;
+    d.hrows = g->hrows;
+    d.hunits = g->hunits;
+    d.hralloc = g->hralloc;
+    d.rowcnt = g->rowcnt;
+    d.hbase = g->hbase;
     d.items = g->items;
     d.pairs = g->pairs;
     d.pmin = g->pmin;
@@ -319,6 +328,12 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->vin_k = (int32_t *)dalloc(g, ld * 4);
     g->vout_k = (int32_t *)dalloc(g, ld * 4);
     g->rlist = (int32_t *)dalloc(g, ld * 4);
+    const int64_t hunit_cap = ld * ((ld + 1023) / 1024);   // every batch of every row
+    g->hrows = (int4 *)dalloc(g, ld * sizeof(int4));
+    g->hunits = (int4 *)dalloc(g, hunit_cap * sizeof(int4));
+    g->hralloc = (int4 *)dalloc(g, ld * sizeof(int4));
+    g->rowcnt = (int32_t *)dalloc(g, ld * apsp::DET_MAXB * sizeof(int32_t));
+    g->hbase = (long long *)dalloc(g, hunit_cap * sizeof(long long));
     g->pair_cap = std::min<int64_t>((int64_t)ld * 512, (int64_t)1 << 30);
     g->item_cap = (int32_t)(g->pair_cap / apsp::ITEM_PAIRS + ld);
     g->pairs = (int32_t *)dalloc(g, g->pair_cap * 4);
@@ -332,7 +347,8 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->model = (float *)dalloc(g, apsp::MLP_NPARAM * sizeof(float));
     if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
         !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->ctl || !g->model ||
-        !g->pmin || !g->pstamp || !g->rstamp || !g->units)
+        !g->pmin || !g->pstamp || !g->rstamp || !g->units || !g->hrows || !g->hunits || !g->hralloc || !g->rowcnt ||
+        !g->hbase)
         return APSP_E_NOMEM;
     if (cudaMallocHost(&g->pin, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
     if (cudaMallocHost(&g->pin_fetch, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;

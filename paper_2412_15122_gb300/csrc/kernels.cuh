@@ -39,6 +39,11 @@ template <typename T> struct Dev {
     int32_t *vin_k, *vout_k;  // Corollary 2 / Corollary 1 vectors as ordered keys
     T *x, *x2, *y, *y2;       // staged rows / columns of the current update
     int32_t *rlist;           // prepass row list
+    int4 *hrows;              // detection: flagged rows (row, first unit, units, batch mask)
+    int4 *hunits;             // detection: flagged units (row, batch, row entry, position in the row)
+    int4 *hralloc;            // detection: per flagged row (first item, first unit, pairs)
+    int32_t *rowcnt;          // detection: listed pairs per (row, batch), DET_MAXB a row
+    long long *hbase;         // detection: first pair slot per unit (-1: none)
     int4 *items;              // (row, first pair, pair count | row's pair count << 8, row's first pair)
     int32_t *pairs;           // affected column per pair, grouped by row (columns ascending)
     int32_t *pmin;            // per pair: first-pass minimum as an ordered key
@@ -522,106 +527,254 @@ __global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
     warp_append(in_r, i, d.rlist, &d.ctl->r_count);
 }
 
-constexpr int DETECT_HB = 256;  // per-warp buffer of a row's affected columns
+constexpr int DET_MAXB = 32;    // 1024-column batches a row may have (rows <= 32768 columns)
 
-// Second scan of a row with more affected pairs than the warp buffer holds:
-// the same test, writing each pair at the row's reserved offsets with the
-// direct-edge weights of the batch fetched together.  Out of line so the hot
-// scan keeps its registers.
-template <typename T, bool TWO>
-__device__ __noinline__ void det_wide_write(const Dev<T> &d, int kind, int i, int a, long long base, T s1, T s2,
-                                            bool use1, bool use2, T wn_x, T wn_x2, const T *ys, const T *y2s) {
-    using M = MinPlus<T>;
-    using V4 = typename M::V4;
-    const int lane = threadIdx.x & 31;
-    const int nv4 = d.span / 4;
-    const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
-    const V4 *Wr4 = reinterpret_cast<const V4 *>(d.W + (int64_t)i * d.ld);
-    const V4 *ys4 = reinterpret_cast<const V4 *>(ys);
-    const V4 *y2s4 = reinterpret_cast<const V4 *>(y2s);
-    const int ci = i >> 2, cia = i & 3;
-    const int ca = kind == 0 ? (a >> 2) : -1, caa = a & 3;
-    constexpr int B = 4;
-    int n = 0;
-    for (int c0 = 0; c0 < nv4; c0 += 32 * B) {
-        V4 v[B], wv[B];
-#pragma unroll
-        for (int bb = 0; bb < B; ++bb) {
-            const int c4 = c0 + bb * 32 + lane;
-            if (c4 < nv4) {
-                v[bb] = Dr4[c4];
-                wv[bb] = __ldg(Wr4 + c4);
-            }
-        }
-        unsigned mask = 0;
-#pragma unroll
-        for (int bb = 0; bb < B; ++bb) {
-            const int c4 = c0 + bb * 32 + lane;
-            if (c4 < nv4) {
-                unsigned m = 0;
-                if (use1) {
-                    const V4 y = ys4[c4];
-                    m |= (unsigned)M::slack_tight(M::slack(s1 + y.x, v[bb].x)) |
-                         (unsigned)M::slack_tight(M::slack(s1 + y.y, v[bb].y)) << 1 |
-                         (unsigned)M::slack_tight(M::slack(s1 + y.z, v[bb].z)) << 2 |
-                         (unsigned)M::slack_tight(M::slack(s1 + y.w, v[bb].w)) << 3;
-                }
-                if (TWO && use2) {
-                    const V4 y = y2s4[c4];
-                    m |= (unsigned)M::slack_tight(M::slack(s2 + y.x, v[bb].x)) |
-                         (unsigned)M::slack_tight(M::slack(s2 + y.y, v[bb].y)) << 1 |
-                         (unsigned)M::slack_tight(M::slack(s2 + y.z, v[bb].z)) << 2 |
-                         (unsigned)M::slack_tight(M::slack(s2 + y.w, v[bb].w)) << 3;
-                }
-                if (c4 == ci) m &= ~(1u << cia);
-                if (c4 == ca) m &= ~(1u << caa);
-                mask |= m << (4 * bb);
-            }
-        }
-        int tot;
-        int off = n + warp_exclusive_scan(__popc(mask), &tot);
-#pragma unroll
-        for (int bb = 0; bb < B; ++bb) {
-            const T wv4[4] = {wv[bb].x, wv[bb].y, wv[bb].z, wv[bb].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (!(mask >> (4 * bb + e) & 1u)) continue;
-                const int j = 4 * (c0 + bb * 32 + lane) + e;
-                T init = wv4[e];
-                if (kind == 1)
-                    init = M::mn(init, M::mn(M::add(wn_x, M::mn(ys[j], M::inf())),
-                                             M::add(wn_x2, TWO ? M::mn(y2s[j], M::inf()) : M::inf())));
-                d.pairs[base + off] = j;
-                d.pmin[base + off] = M::key(init);
-                d.pstamp[base + off] = 0;
-                d.D[(int64_t)i * d.ld + j] = init;
-                if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
-                ++off;
-            }
-        }
-        n += tot;
-    }
-}
+template <typename T> __device__ __forceinline__ T unreachable_leg();
+template <> __device__ __forceinline__ int32_t unreachable_leg<int32_t>() { return INF_I32 + 1; }
+template <> __device__ __forceinline__ float unreachable_leg<float>() { return __int_as_float(0x7f800000); }
+__device__ __forceinline__ int32_t max_of(int32_t a, int32_t b) { return max(a, b); }
+__device__ __forceinline__ float max_of(float a, float b) { return fmaxf(a, b); }
 
+// Affected-pair detection.
 // kind 0: removal of node a (rows: every live row != a).  Affected pairs are
 //   exactly the need_update_list of Section 3.2: (i, j), i != j, both != a,
 //   listed unless D[i][j] < D[i][a] + D[a][j] (Corollary 3).
 // kind 1: increase of edge a -> b from w_old to w_new (rows: prepass list):
 //   the same test with the path through the old edge.
-// One warp per row, 8 vectors per lane in flight.  Each lane turns its 8
-// vectors into a 32-bit mask of tight entries (for an exact APSP matrix a
-// path through the removed node / old edge is never shorter than the stored
-// distance, so tight means equal, or equal within the fp32 slack); batches
-// where some lane has a bit set append those columns, in order, to a
-// per-warp buffer (one prefix sum).  One packed atomic reserves the row's
-// slots; a row with more than DETECT_HB pairs is scanned a second time the
-// same way, writing at the reserved offsets.
+// For an exact APSP matrix a path through the removed node / old edge is
+// never shorter than the stored distance, so "listed" means equal (within
+// the fp32 slack).  The staged legs are y = D[a][.] (removal) or D[b][.]
+// (increase; y2 = D[a][.] for the reverse direction of an undirected edge).
+//
+// k_det_scan streams every row once with nothing but a cheap screen per
+// entry and records, per row, the 1024-column batches where an entry may be
+// tight; three short kernels then apply the exact test to those batches only
+// and commit each row's pairs (in column order) with their starting upper
+// bounds.
+
+// Exact mask of batch c0 (vectors [c0, c0 + 256) of row i): bit 4 bb + e of
+// lane l is entry 4 (c0 + 32 bb + l) + e.
 template <typename T, bool TWO>
-__global__ void __launch_bounds__(256, 3) k_detect(Dev<T> d, int kind, int a, int b, T w_old, T w_new) {
+__device__ __forceinline__ unsigned det_exact_mask(const Dev<T> &d, const typename MinPlus<T>::V4 (&v)[SWEEP_B],
+                                                   int c0, T s1, T s2, bool use1, bool use2, int i, int a, int kind) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    const int lane = threadIdx.x & 31;
+    const int nv4 = d.span / 4;
+    const V4 *y4 = reinterpret_cast<const V4 *>(d.y);
+    const V4 *y24 = reinterpret_cast<const V4 *>(d.y2);
+    const int ci = i >> 2, cia = i & 3;
+    const int ca = kind == 0 ? (a >> 2) : -1, caa = a & 3;
+    unsigned mask = 0;
+#pragma unroll
+    for (int bb = 0; bb < SWEEP_B; ++bb) {
+        const int c4 = c0 + bb * 32 + lane;
+        if (c4 < nv4) {
+            unsigned m = 0;
+            if (use1) {
+                const V4 y = __ldcg(y4 + c4);
+                m |= (unsigned)M::slack_tight(M::slack(s1 + M::leg(y.x), v[bb].x)) |
+                     (unsigned)M::slack_tight(M::slack(s1 + M::leg(y.y), v[bb].y)) << 1 |
+                     (unsigned)M::slack_tight(M::slack(s1 + M::leg(y.z), v[bb].z)) << 2 |
+                     (unsigned)M::slack_tight(M::slack(s1 + M::leg(y.w), v[bb].w)) << 3;
+            }
+            if (TWO && use2) {
+                const V4 y = __ldcg(y24 + c4);
+                m |= (unsigned)M::slack_tight(M::slack(s2 + M::leg(y.x), v[bb].x)) |
+                     (unsigned)M::slack_tight(M::slack(s2 + M::leg(y.y), v[bb].y)) << 1 |
+                     (unsigned)M::slack_tight(M::slack(s2 + M::leg(y.z), v[bb].z)) << 2 |
+                     (unsigned)M::slack_tight(M::slack(s2 + M::leg(y.w), v[bb].w)) << 3;
+            }
+            if (c4 == ci) m &= ~(1u << cia);
+            if (c4 == ca) m &= ~(1u << caa);
+            mask |= m << (4 * bb);
+        }
+    }
+    return mask;
+}
+
+// Starting upper bound of listed pair (i, j): the direct edge, and for an
+// increase also the path through the edge at its new weight.
+template <typename T, bool TWO>
+__device__ __forceinline__ T det_init(const Dev<T> &d, int kind, T w_ij, int j, T wn_x, T wn_x2) {
+    using M = MinPlus<T>;
+    if (kind != 1) return w_ij;
+    return M::mn(w_ij, M::mn(M::add(wn_x, M::mn(d.y[j], M::inf())),
+                             M::add(wn_x2, TWO ? M::mn(d.y2[j], M::inf()) : M::inf())));
+}
+
+template <typename T>
+__device__ __forceinline__ void det_write_pair(const Dev<T> &d, int i, int j, long long slot, T init) {
+    d.pairs[slot] = j;
+    d.pmin[slot] = MinPlus<T>::key(init);
+    d.pstamp[slot] = 0;
+    d.D[(int64_t)i * d.ld + j] = init;
+    if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
+}
+
+// The rows the scan flagged are committed by two kernels so that a row with
+// many flagged batches is spread over as many warps:
+//   k_det_alloc  one lane per flagged row (32 rows a warp, one reservation
+//                per warp): the row's pairs, work items and re-relaxation
+//                units, and each flagged batch's first pair slot (column order);
+//   k_det_write  one warp per (row, flagged batch): its pairs, written at the
+//                batch's slots with their starting upper bounds.
+template <typename T>
+__global__ void __launch_bounds__(256) k_det_alloc(Dev<T> d) {
+    const int lane = threadIdx.x & 31;
+    const int n_rows = *(volatile const int32_t *)&d.ctl->hit_rows;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    int rows_hit = 0;
+    for (int r0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n_rows; r0 += nwarps * 32) {
+        const int r = r0 + lane;
+        int4 re = make_int4(0, 0, 0, 0);   // (row, first unit, units, batch mask)
+        int cnt[DET_MAXB];                  // the row's per-batch counts (flagged batches only)
+        int n = 0;
+        if (r < n_rows) re = __ldcg(d.hrows + r);
+        {
+            const int4 *rc4 = reinterpret_cast<const int4 *>(d.rowcnt + (int64_t)re.x * DET_MAXB);
+#pragma unroll
+            for (int q = 0; q < DET_MAXB / 4; ++q) {
+                int4 c4 = make_int4(0, 0, 0, 0);
+                if (r < n_rows && (((unsigned)re.w >> (4 * q)) & 15u)) c4 = __ldcg(rc4 + q);
+                cnt[4 * q] = ((unsigned)re.w >> (4 * q)) & 1u ? c4.x : 0;
+                cnt[4 * q + 1] = ((unsigned)re.w >> (4 * q + 1)) & 1u ? c4.y : 0;
+                cnt[4 * q + 2] = ((unsigned)re.w >> (4 * q + 2)) & 1u ? c4.z : 0;
+                cnt[4 * q + 3] = ((unsigned)re.w >> (4 * q + 3)) & 1u ? c4.w : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < DET_MAXB; ++q) n += cnt[q];
+        }
+        const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
+        const int nseg = (n + YSEG - 1) / YSEG;
+        const int nun = nit * nseg;
+        int tn, tit, tun;
+        const int on = warp_exclusive_scan(n, &tn);
+        const int oit = warp_exclusive_scan(nit, &tit);
+        const int oun = warp_exclusive_scan(nun, &tun);
+        unsigned long long old = 0;
+        int ub = 0;
+        if (lane == 0 && tn > 0) {
+            old = atomicAdd(&d.ctl->alloc, ((unsigned long long)tn << 24) | (unsigned long long)tit);
+            ub = atomicAdd(&d.ctl->unit_alloc, tun);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        ub = __shfl_sync(0xffffffffu, ub, 0);
+        if (tn == 0) continue;
+        const long long pbw = (long long)(old >> 24);
+        const int ibw = (int)(old & 0xFFFFFFull);
+        if (pbw + tn > d.pair_cap || ibw + tit > d.item_cap || (long long)ub + tun > d.unit_cap) {
+            if (lane == 0) atomicOr(&d.ctl->overflow, 1);
+            continue;   // these rows' units write nothing (their slots stay -1)
+        }
+        const long long pb = pbw + on;
+        if (n > 0) {
+            ++rows_hit;
+            long long q = pb;
+            int u = re.y;
+#pragma unroll
+            for (int b = 0; b < DET_MAXB; ++b) {
+                if (((unsigned)re.w >> b) & 1u) d.hbase[u++] = q;
+                q += cnt[b];
+            }
+        }
+        // the row's items and unit range; its units are written by the
+        // warps of k_det_write, each a share
+        if (r < n_rows) d.hralloc[r] = make_int4(ibw + oit, ub + oun, n, 0);
+        for (int t = 0; t < 32; ++t) {
+            const int nt = __shfl_sync(0xffffffffu, n, t);
+            if (nt == 0) continue;
+            const int it = __shfl_sync(0xffffffffu, re.x, t);
+            const long long pbt = __shfl_sync(0xffffffffu, pb, t);
+            const int ibt = ibw + __shfl_sync(0xffffffffu, oit, t);
+            const int nitt = (nt + ITEM_PAIRS - 1) / ITEM_PAIRS;
+            for (int k = lane; k < nitt; k += 32)
+                d.items[ibt + k] = make_int4(it, (int)pbt + k * ITEM_PAIRS, min(ITEM_PAIRS, nt - k * ITEM_PAIRS) | (nt << 8), (int)pbt);
+        }
+    }
+    if (rows_hit) atomicAdd(&d.ctl->n_rows, rows_hit);
+}
+
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(256, 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    __shared__ int32_t hbuf[8][32 * SWEEP_B * 4];
+    const int lane = threadIdx.x & 31;
+    int32_t *hb = hbuf[threadIdx.x >> 5];
+    const int n_units = *(volatile const int32_t *)&d.ctl->hit_units;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int nv4 = d.span / 4;
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n_units; u += nwarps) {
+        const int4 ue = __ldcg(d.hunits + u);   // (row, batch, row entry, position among the row's units)
+        const long long base = __ldcg(d.hbase + u);
+        const int i = ue.x;
+        const int c0 = ue.y * 32 * SWEEP_B;
+        if (base >= 0) {
+            // this unit's share of the row's re-relaxation units
+            const int4 ra = __ldcg(d.hralloc + ue.z);   // (first item, first unit, pairs)
+            const int k = __ldcg(&d.hrows[ue.z].z);
+            const int nit = (ra.z + ITEM_PAIRS - 1) / ITEM_PAIRS, nseg = (ra.z + YSEG - 1) / YSEG;
+            const int nun = nit * nseg;
+            const int lo = (int)((long long)nun * ue.w / k), hi = (int)((long long)nun * (ue.w + 1) / k);
+            for (int t = lo + lane; t < hi; t += 32)
+                d.units[ra.y + t] = (int32_t)((unsigned)(ra.x + t / nseg) | ((unsigned)(t % nseg) << 24));
+        }
+        const T xi = __ldcg(d.x + i);
+        const T x2i = TWO ? __ldcg(d.x2 + i) : M::inf();
+        const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+        V4 v[SWEEP_B];
+#pragma unroll
+        for (int bb = 0; bb < SWEEP_B; ++bb) {
+            const int c4 = c0 + bb * 32 + lane;
+            if (c4 < nv4) v[bb] = __ldcg(Dr4 + c4);
+        }
+        if (base < 0) continue;   // a row that did not fit
+        const T s1 = kind == 0 ? xi : M::add(xi, w_old);
+        const T s2 = M::add(x2i, w_old);
+        const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
+        const unsigned mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
+        int tot;
+        int off = warp_exclusive_scan(__popc(mask), &tot);
+        __syncwarp();   // the previous unit's buffer reads are done
+        for (unsigned m = mask; m; m &= m - 1) {
+            const int bit = __ffs(m) - 1;
+            hb[off++] = 4 * (c0 + (bit >> 2) * 32 + lane) + (bit & 3);
+        }
+        __syncwarp();
+        const T wn_x = kind == 1 ? M::add(xi, w_new) : M::inf();
+        const T wn_x2 = kind == 1 ? M::add(x2i, w_new) : M::inf();
+        const T *Wr = d.W + (int64_t)i * d.ld;
+        for (int h = 0; h < tot; h += 256) {
+            int jj[8];
+            T ww[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int t = h + lane + 32 * q;
+                jj[q] = t < tot ? hb[t] : -1;
+                if (jj[q] >= 0) ww[q] = __ldg(Wr + jj[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (jj[q] >= 0)
+                    det_write_pair<T>(d, i, jj[q], base + h + lane + 32 * q, det_init<T, TWO>(d, kind, ww[q], jj[q], wn_x, wn_x2));
+        }
+    }
+}
+
+// One warp per row, rows assigned round-robin; the legs are staged once per
+// CTA in shared memory (the removed node's own column as unreachable, so its
+// D[a][a] = 0 never makes a row look tight).  A lane streams 8 vectors at a
+// time and keeps only the maximum of d - y (int32: a batch holds a tight
+// entry iff that maximum reaches s; fp32: with twice the slack, so rounding
+// can only flag extra batches).  A warp keeps the rows it flags in lane
+// registers (lane t: its t-th flagged row and batch mask) and appends them
+// to the hit list with one atomic when it is done or holds 32.
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, T w_old) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int32_t hbuf[8][DETECT_HB];
     const int span = d.span;
     T *ys = reinterpret_cast<T *>(smem_raw);
     T *y2s = ys + span;
@@ -629,133 +782,131 @@ __global__ void __launch_bounds__(256, 3) k_detect(Dev<T> d, int kind, int a, in
     if (TWO) stage_vec<T>(y2s, d.y2, span);
     __syncthreads();
     for (int c = threadIdx.x; c < span; c += blockDim.x) {
-        ys[c] = M::leg(ys[c]);
+        ys[c] = kind == 0 && c == a ? unreachable_leg<T>() : M::leg(ys[c]);
         if (TWO) y2s[c] = M::leg(y2s[c]);
     }
     __syncthreads();
     const V4 *ys4 = reinterpret_cast<const V4 *>(ys);
     const V4 *y2s4 = reinterpret_cast<const V4 *>(y2s);
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int32_t *hb = hbuf[wib];
+    const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const int nrows = kind == 0 ? span : *(volatile int32_t *)&d.ctl->r_count;
     const int nv4 = span / 4;
-    int rows_hit = 0;
-    for (int r = blockIdx.x * (blockDim.x >> 5) + wib; r < nrows; r += nwarps) {
-        const int i = kind == 0 ? r : d.rlist[r];
+    int nh = 0, hrow = 0;
+    unsigned hmask = 0;
+    auto flush = [&]() {
+        // lane t < nh holds a flagged row: one row entry and one unit per
+        // flagged batch, the row's units contiguous and in column order
+        const int k = lane < nh ? __popc(hmask) : 0;
+        int nu;
+        const int uoff = warp_exclusive_scan(k, &nu);
+        int rbase = 0, ubase = 0;
+        if (lane == 0) {
+            rbase = atomicAdd(&d.ctl->hit_rows, nh);
+            ubase = atomicAdd(&d.ctl->hit_units, nu);
+        }
+        rbase = __shfl_sync(0xffffffffu, rbase, 0);
+        ubase = __shfl_sync(0xffffffffu, ubase, 0);
+        if (lane < nh) {
+            d.hrows[rbase + lane] = make_int4(hrow, ubase + uoff, k, (int)hmask);
+            int q = ubase + uoff, pos = 0;
+            for (unsigned m = hmask; m; m &= m - 1) {
+                d.hunits[q] = make_int4(hrow, __ffs(m) - 1, rbase + lane, pos++);
+                d.hbase[q] = -1;
+                ++q;
+            }
+        }
+        nh = 0;
+    };
+    const int r0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int i_next = r0 < nrows ? (kind == 0 ? r0 : d.rlist[r0]) : 0;
+    T x_next = r0 < nrows ? d.x[i_next] : M::inf();
+    T x2_next = TWO && r0 < nrows ? d.x2[i_next] : M::inf();
+    for (int r = r0; r < nrows; r += nwarps) {
+        const int i = i_next;
+        const T xi = x_next;  // missing for a dead row, so it is skipped below
+        const T x2i = x2_next;
+        if (r + nwarps < nrows) {
+            i_next = kind == 0 ? r + nwarps : d.rlist[r + nwarps];
+            x_next = d.x[i_next];
+            if (TWO) x2_next = d.x2[i_next];
+        }
         if (kind == 0 && i == a) continue;
-        const T xi = d.x[i];  // missing for a dead row, so it is skipped below
-        const T x2i = TWO ? d.x2[i] : M::inf();
         const T s1 = kind == 0 ? xi : M::add(xi, w_old);
         const T s2 = M::add(x2i, w_old);
         const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
         if (!use1 && !use2) continue;
         const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
-        const int ci = i >> 2, cia = i & 3;
-        const int ca = kind == 0 ? (a >> 2) : -1, caa = a & 3;
-        const T wn_x = kind == 1 ? M::add(xi, w_new) : M::inf();
-        const T wn_x2 = kind == 1 ? M::add(x2i, w_new) : M::inf();
-        int n = 0;
-        for (int pass = 0; pass < 1; ++pass) {
-            for (int c0 = 0; c0 < nv4; c0 += 32 * SWEEP_B) {
-                V4 v[SWEEP_B];
+        unsigned bmask = 0;
+        for (int c0 = 0, bi = 0; c0 < nv4; c0 += 32 * SWEEP_B, ++bi) {
+            V4 v[SWEEP_B];
 #pragma unroll
-                for (int bb = 0; bb < SWEEP_B; ++bb) {
-                    const int c4 = c0 + bb * 32 + lane;
-                    if (c4 < nv4) v[bb] = Dr4[c4];
+            for (int bb = 0; bb < SWEEP_B; ++bb) {
+                const int c4 = c0 + bb * 32 + lane;
+                if (c4 < nv4) v[bb] = __ldcs(Dr4 + c4);
+            }
+            T b1 = M::screen_floor(), b2 = M::screen_floor();
+#pragma unroll
+            for (int bb = 0; bb < SWEEP_B; ++bb) {
+                const int c4 = c0 + bb * 32 + lane;
+                if (c4 < nv4) {
+                    const V4 y = ys4[c4];
+                    b1 = max_of(b1, max_of(max_of(M::screen_bound(v[bb].x, y.x), M::screen_bound(v[bb].y, y.y)),
+                                           max_of(M::screen_bound(v[bb].z, y.z), M::screen_bound(v[bb].w, y.w))));
+                    if (TWO && use2) {
+                        const V4 z = y2s4[c4];
+                        b2 = max_of(b2, max_of(max_of(M::screen_bound(v[bb].x, z.x), M::screen_bound(v[bb].y, z.y)),
+                                               max_of(M::screen_bound(v[bb].z, z.z), M::screen_bound(v[bb].w, z.w))));
+                    }
                 }
-                unsigned mask = 0;
+            }
+            const bool maybe = (use1 && s1 <= b1) || (TWO && use2 && s2 <= b2);
+            if (__ballot_sync(0xffffffffu, maybe)) {
+                // exact count of the batch's listed pairs (the same test as
+                // det_exact_mask; column a is staged unreachable, column i
+                // is taken out below)
+                int c = 0;
 #pragma unroll
                 for (int bb = 0; bb < SWEEP_B; ++bb) {
                     const int c4 = c0 + bb * 32 + lane;
                     if (c4 < nv4) {
-                        unsigned m = 0;
                         if (use1) {
                             const V4 y = ys4[c4];
-                            m |= (unsigned)M::slack_tight(M::slack(s1 + y.x, v[bb].x)) |
-                                 (unsigned)M::slack_tight(M::slack(s1 + y.y, v[bb].y)) << 1 |
-                                 (unsigned)M::slack_tight(M::slack(s1 + y.z, v[bb].z)) << 2 |
-                                 (unsigned)M::slack_tight(M::slack(s1 + y.w, v[bb].w)) << 3;
+                            c += M::slack_tight(M::slack(s1 + y.x, v[bb].x)) + M::slack_tight(M::slack(s1 + y.y, v[bb].y)) +
+                                 M::slack_tight(M::slack(s1 + y.z, v[bb].z)) + M::slack_tight(M::slack(s1 + y.w, v[bb].w));
                         }
                         if (TWO && use2) {
                             const V4 y = y2s4[c4];
-                            m |= (unsigned)M::slack_tight(M::slack(s2 + y.x, v[bb].x)) |
-                                 (unsigned)M::slack_tight(M::slack(s2 + y.y, v[bb].y)) << 1 |
-                                 (unsigned)M::slack_tight(M::slack(s2 + y.z, v[bb].z)) << 2 |
-                                 (unsigned)M::slack_tight(M::slack(s2 + y.w, v[bb].w)) << 3;
+                            c += (M::slack_tight(M::slack(s2 + y.x, v[bb].x)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4], v[bb].x)))) +
+                                 (M::slack_tight(M::slack(s2 + y.y, v[bb].y)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4 + 1], v[bb].y)))) +
+                                 (M::slack_tight(M::slack(s2 + y.z, v[bb].z)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4 + 2], v[bb].z)))) +
+                                 (M::slack_tight(M::slack(s2 + y.w, v[bb].w)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4 + 3], v[bb].w))));
                         }
-                        if (c4 == ci) m &= ~(1u << cia);
-                        if (c4 == ca) m &= ~(1u << caa);
-                        mask |= m << (4 * bb);
+                        if (c4 == (i >> 2)) {
+                            // the diagonal is never a pair (tight only on a zero-length cycle)
+                            const int e = i & 3;
+                            const T ve = e == 0 ? v[bb].x : e == 1 ? v[bb].y : e == 2 ? v[bb].z : v[bb].w;
+                            c -= (use1 && M::slack_tight(M::slack(s1 + ys[i], ve))) ||
+                                 (TWO && use2 && M::slack_tight(M::slack(s2 + y2s[i], ve)));
+                        }
                     }
                 }
-                if (__ballot_sync(0xffffffffu, mask != 0) == 0) continue;
-                int tot;
-                int off = n + warp_exclusive_scan(__popc(mask), &tot);
-                for (unsigned m = mask; m; m &= m - 1) {
-                    const int bit = __ffs(m) - 1;
-                    if (off < DETECT_HB) hb[off] = 4 * (c0 + (bit >> 2) * 32 + lane) + (bit & 3);
-                    ++off;
+                c = warp_sum(c);
+                if (c > 0) {
+                    bmask |= 1u << bi;
+                    if (lane == 0) d.rowcnt[(int64_t)i * DET_MAXB + bi] = c;
                 }
-                n += tot;
             }
-            if (n == 0) break;
-            // reserve the row's slots
-            const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
-            const int nseg = (n + YSEG - 1) / YSEG;
-            const int nun = nit * nseg;
-            unsigned long long old = 0;
-            int ub = 0;
-            if (lane == 0) {
-                old = atomicAdd(&d.ctl->alloc, ((unsigned long long)n << 24) | (unsigned long long)nit);
-                ub = atomicAdd(&d.ctl->unit_alloc, nun);
+        }
+        if (bmask) {
+            if (lane == nh) {
+                hrow = i;
+                hmask = bmask;
             }
-            old = __shfl_sync(0xffffffffu, old, 0);
-            ub = __shfl_sync(0xffffffffu, ub, 0);
-            const long long rb = (long long)(old >> 24);
-            const int ib = (int)(old & 0xFFFFFFull);
-            if (rb + n > d.pair_cap || ib + nit > d.item_cap || (long long)ub + nun > d.unit_cap) {
-                if (lane == 0) atomicOr(&d.ctl->overflow, 1);
-                n = 0;
-                break;
-            }
-            ++rows_hit;
-            for (int t = lane; t < nit; t += 32)
-                d.items[ib + t] = make_int4(i, (int)rb + t * ITEM_PAIRS, min(ITEM_PAIRS, n - t * ITEM_PAIRS) | (n << 8), (int)rb);
-            for (int u = lane; u < nun; u += 32)
-                d.units[ub + u] = (int32_t)((unsigned)(ib + u / nseg) | ((unsigned)(u % nseg) << 24));
-            __syncwarp();
-            if (n <= DETECT_HB) {
-                // up to 8 pairs per lane; their gathers are issued together
-                int jj[DETECT_HB / 32];
-                T ww[DETECT_HB / 32];
-#pragma unroll
-                for (int q = 0; q < DETECT_HB / 32; ++q) {
-                    const int t = lane + 32 * q;
-                    jj[q] = t < n ? hb[t] : -1;
-                    if (jj[q] >= 0) ww[q] = __ldg(d.W + (int64_t)i * d.ld + jj[q]);
-                }
-#pragma unroll
-                for (int q = 0; q < DETECT_HB / 32; ++q) {
-                    if (jj[q] < 0) continue;
-                    const int j = jj[q];
-                    T init = ww[q];
-                    if (kind == 1)
-                        init = M::mn(init, M::mn(M::add(wn_x, M::mn(ys[j], M::inf())),
-                                                 M::add(wn_x2, TWO ? M::mn(y2s[j], M::inf()) : M::inf())));
-                    d.pairs[rb + lane + 32 * q] = j;
-                    d.pmin[rb + lane + 32 * q] = M::key(init);
-                    d.pstamp[rb + lane + 32 * q] = 0;
-                    d.D[(int64_t)i * d.ld + j] = init;
-                    if (d.DT) d.DT[(int64_t)j * d.ld + i] = init;
-                }
-                __syncwarp();  // the buffer is reused by the next row
-                break;
-            }
-            det_wide_write<T, TWO>(d, kind, i, a, rb, s1, s2, use1, use2, wn_x, wn_x2, ys, y2s);
+            if (++nh == 32) flush();
         }
     }
-    if (lane == 0 && rows_hit) atomicAdd(&d.ctl->n_rows, rows_hit);
+    if (nh) flush();
 }
 
 // Removal: node k's row and column become missing, slot k dead.
@@ -813,25 +964,6 @@ struct RepairCfg {
     float feat_dw;       // relative weight change
 };
 
-// Minimum of four per-lane values over the warp with 6 shuffles: returns, in
-// every lane of each group of 8 lanes g = lane / 8, the minimum of value g.
-template <typename T> __device__ __forceinline__ T warp_min4(T a0, T a1, T a2, T a3, int lane) {
-    using M = MinPlus<T>;
-    const bool hi = lane & 16;
-    const T s0 = hi ? a0 : a2, s1 = hi ? a1 : a3;
-    T k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
-    k0 = M::mn(k0, __shfl_xor_sync(0xffffffffu, s0, 16));
-    k1 = M::mn(k1, __shfl_xor_sync(0xffffffffu, s1, 16));
-    const bool b3 = lane & 8;
-    const T s = b3 ? k0 : k1;
-    T k = b3 ? k1 : k0;
-    k = M::mn(k, __shfl_xor_sync(0xffffffffu, s, 8));
-    k = M::mn(k, __shfl_xor_sync(0xffffffffu, k, 4));
-    k = M::mn(k, __shfl_xor_sync(0xffffffffu, k, 2));
-    k = M::mn(k, __shfl_xor_sync(0xffffffffu, k, 1));
-    return k;
-}
-
 template <typename T>
 __device__ void repair_warm(Dev<T> &d, int n_items) {
     using M = MinPlus<T>;
@@ -841,22 +973,24 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
     const int span = d.span;
     const int64_t ld = d.ld;
     const T *cols = d.DT ? d.DT : d.D;   // row j of `cols` is column j of D
-    const int nchunk = (span + PASS1_CHUNK - 1) / PASS1_CHUNK;
-    constexpr int CV = PASS1_CHUNK / 128;  // 16-byte vectors per lane per chunk
     const long long n_units = *(volatile const int32_t *)&ctl->unit_alloc;
 
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer_ns();
 
     const int wq = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % QUEUES) * 32;
 
-    // Pass 1: one warp per unit = (work item, group of PASS1_GROUP chunks of
-    // x), units ordered group-major so all warps sweep the same window of
-    // columns.  Per chunk the row's slice stays in registers and four pairs'
-    // column slices are loaded at a time; lane t keeps pair t's running
-    // minimum, stored once per unit with a fire-and-forget atomic min.
+    // Pass 1: one warp per unit = (work item, window of PASS1_COLS columns
+    // of x), units ordered window-major so all warps sweep the same window.
+    // The row's slice of the window is staged in the warp's shared buffer;
+    // per pair the whole column slice is loaded at once (8 vectors a lane),
+    // reduced over the warp, and kept by lane t for pair t; one
+    // fire-and-forget atomic min per pair and unit stores it.
     {
-        const int ngroups = (nchunk + PASS1_GROUP - 1) / PASS1_GROUP;
-        const int n1 = n_items * ngroups;   // items < 2^19 and groups <= 18 at the largest capacity
+        constexpr int CW = PASS1_COLS / 128;   // 16-byte vectors per lane per window
+        __shared__ V4 rowbuf[8][PASS1_COLS / 4];
+        V4 *rb = rowbuf[threadIdx.x >> 5];
+        const int nwin = (span + PASS1_COLS - 1) / PASS1_COLS;
+        const int n1 = n_items * nwin;   // items < 2^19 and windows <= 18 at the largest capacity
         int t = 0;
         if (lane == 0) t = atomicAdd(&ctl->q1[wq], 1);
         t = __shfl_sync(0xffffffffu, t, 0);
@@ -868,52 +1002,36 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
             const int4 item = __ldcg(d.items + it);
             const int cnt = item.z & 0xff;
             const int jl = lane < cnt ? __ldcg(d.pairs + item.y + lane) : 0;
-            const T *Dr = d.D + (int64_t)item.x * ld;
+            const int x0 = g * PASS1_COLS;
+            const int nv = (min(span, x0 + PASS1_COLS) - x0) / 4;
+            const V4 *r4 = reinterpret_cast<const V4 *>(d.D + (int64_t)item.x * ld + x0);
+            __syncwarp();   // the previous unit's reads of the buffer are done
+#pragma unroll
+            for (int k = 0; k < CW; ++k)
+                if (lane + 32 * k < nv) cp_async16(rb + lane + 32 * k, r4 + lane + 32 * k);
             T pacc = M::inf();
-            for (int sc = 0; sc < PASS1_GROUP; ++sc) {
-                const int x0 = (g * PASS1_GROUP + sc) * PASS1_CHUNK;
-                if (x0 >= span) break;
-                const int nv = (min(span, x0 + PASS1_CHUNK) - x0) / 4;
-                const V4 *r4 = reinterpret_cast<const V4 *>(Dr + x0);
-                V4 rv[CV];
+            for (int q = 0; q < cnt; ++q) {
+                const int jq = __shfl_sync(0xffffffffu, jl, q);
+                const V4 *c4 = reinterpret_cast<const V4 *>(cols + (int64_t)jq * ld + x0);
+                V4 a[CW];
 #pragma unroll
-                for (int k = 0; k < CV; ++k)
-                    if (lane + 32 * k < nv) rv[k] = __ldcg(r4 + lane + 32 * k);
-                for (int q = 0; q < cnt; q += 4) {
-                    int jq[4];
-                    jq[0] = __shfl_sync(0xffffffffu, jl, q);
+                for (int k = 0; k < CW; ++k)
+                    if (lane + 32 * k < nv) a[k] = __ldcg(c4 + lane + 32 * k);
+                cp_async_wait_all();   // the row slice (in flight with the first column)
+                __syncwarp();
+                T acc = M::inf();
 #pragma unroll
-                    for (int u4 = 1; u4 < 4; ++u4) {
-                        const int jj = __shfl_sync(0xffffffffu, jl, (q + u4) & 31);
-                        jq[u4] = q + u4 < cnt ? jj : jq[0];
+                for (int k = 0; k < CW; ++k) {
+                    if (lane + 32 * k < nv) {
+                        const V4 r = rb[lane + 32 * k];
+                        acc = M::add_min(r.x, a[k].x, acc);
+                        acc = M::add_min(r.y, a[k].y, acc);
+                        acc = M::add_min(r.z, a[k].z, acc);
+                        acc = M::add_min(r.w, a[k].w, acc);
                     }
-                    V4 a[4][CV];
-#pragma unroll
-                    for (int u4 = 0; u4 < 4; ++u4) {
-                        const V4 *c4 = reinterpret_cast<const V4 *>(cols + (int64_t)jq[u4] * ld + x0);
-#pragma unroll
-                        for (int k = 0; k < CV; ++k)
-                            if (lane + 32 * k < nv) a[u4][k] = __ldcg(c4 + lane + 32 * k);
-                    }
-                    T acc[4];
-#pragma unroll
-                    for (int u4 = 0; u4 < 4; ++u4) {
-                        acc[u4] = M::inf();
-#pragma unroll
-                        for (int k = 0; k < CV; ++k) {
-                            if (lane + 32 * k < nv) {
-                                acc[u4] = M::add_min(rv[k].x, a[u4][k].x, acc[u4]);
-                                acc[u4] = M::add_min(rv[k].y, a[u4][k].y, acc[u4]);
-                                acc[u4] = M::add_min(rv[k].z, a[u4][k].z, acc[u4]);
-                                acc[u4] = M::add_min(rv[k].w, a[u4][k].w, acc[u4]);
-                            }
-                        }
-                    }
-                    const T r = warp_min4(acc[0], acc[1], acc[2], acc[3], lane);
-                    // pair q + g' sits in lanes 8g'..8g'+7; hand it to lane q + g'
-                    const T got = __shfl_sync(0xffffffffu, r, ((lane - q) * 8) & 31);
-                    if (lane >= q && lane < q + 4) pacc = M::mn(pacc, got);
                 }
+                acc = warp_min(acc);
+                if (lane == q) pacc = acc;
             }
             if (lane < cnt) atomicMin(d.pmin + item.y + lane, M::key(pacc));
             t = __shfl_sync(0xffffffffu, t, 0);
@@ -934,10 +1052,14 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
     if (!grid_barrier(ctl, leader)) return;
 
     // Passes >= 2: one warp per unit = (work item, segment of YSEG of the
-    // row's listed targets y); lane t owns pair t of the item and gathers
-    // D[y][j_t] for up to 8 y at a time.  Pass 2 reads D[i][.] of listed
-    // pairs from pmin and stores every pair; later passes store only pairs
-    // they lower.  Stores are atomic minima (several units share a pair).
+    // row's listed targets y).  Lane u holds intermediates y = segment[u +
+    // 32b] with D[i][y]; pairs are taken four at a time, every lane gathering
+    // D[y][j] = cols[j][y] for its y (16 gathers in flight), and a transpose
+    // reduction leaves pair t's minimum in lane t.  Pass 2 reads D[i][.] of
+    // listed pairs from pmin and stores every pair; later passes take only
+    // y lowered in the previous pass and store only pairs they lower.
+    // Stores are atomic minima (the segments of one item share its pairs).
+    constexpr int YB = YSEG / 32;
     for (pass = 2; pass <= MAX_PASSES && !*(volatile int32_t *)&ctl->stop; ++pass) {
         const int par = pass & 1;
         bool changed = false;
@@ -959,53 +1081,73 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
             const bool mine = lane < cnt;
             const T *Di = d.D + (int64_t)i * ld;
             int j = 0;
-            T cur = M::inf();
+            T cur = (T)0;   // pairs past cnt: no y passes dy < 0, so they load nothing
             if (mine) {
                 j = __ldcg(d.pairs + item.y + lane);
                 cur = pass == 2 ? M::unkey(__ldcg(d.pmin + item.y + lane)) : __ldcg(Di + j);
             }
-            const int y1 = min(nrow, (seg + 1) * YSEG);
-            T acc = M::inf();
-            for (int s = seg * YSEG; s < y1; s += 32) {
-                const int yi = s + lane;
-                int y = 0;
-                T dy = M::inf();
-                bool ok = false;
-                if (yi < y1) {
-                    y = __ldcg(d.pairs + item.w + yi);
-                    if (pass == 2) {
-                        dy = M::unkey(__ldcg(d.pmin + item.w + yi));
-                        ok = true;
-                    } else if ((int)__ldcg(d.pstamp + item.w + yi) >= pass - 1) {
-                        dy = __ldcg(Di + y);
-                        ok = true;
-                    }
-                }
-                unsigned m = __ballot_sync(0xffffffffu, ok);
-                while (m) {
-                    int ys[8];
-                    T dys[8];
+            const int ybeg = seg * YSEG, yend = min(nrow, ybeg + YSEG);
+            int yv[YB];
+            T dyv[YB];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int src = m ? __ffs(m) - 1 : 0;
-                        const bool has = m != 0;
-                        m &= m - 1;
-                        ys[e] = __shfl_sync(0xffffffffu, y, src);
-                        const T dd = __shfl_sync(0xffffffffu, dy, src);
-                        dys[e] = has ? dd : M::inf();
-                    }
-                    T v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        v[e] = (mine && dys[e] < cur) ? __ldcg(d.D + (int64_t)ys[e] * ld + j) : M::inf();
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) acc = M::add_min(dys[e], v[e], acc);
+            for (int b = 0; b < YB; ++b) {
+                const int yi = ybeg + 32 * b + lane;
+                yv[b] = 0;
+                dyv[b] = M::inf();
+                if (yi < yend) {
+                    yv[b] = __ldcg(d.pairs + item.w + yi);
+                    if (pass == 2) dyv[b] = M::unkey(__ldcg(d.pmin + item.w + yi));
+                    else if ((int)__ldcg(d.pstamp + item.w + yi) >= pass - 1) dyv[b] = __ldcg(Di + yv[b]);
                 }
             }
+            bool any_y = false;
+#pragma unroll
+            for (int b = 0; b < YB; ++b) any_y |= dyv[b] < M::inf();
             if (seg == 0 && lane == 0) evals += cnt;
-            const bool lower = mine && acc < cur;
+            if (pass > 2 && !__any_sync(0xffffffffu, any_y)) continue;   // pass 2 stores every pair
+            const int nb = (yend - ybeg + 31) >> 5;   // y blocks holding data (warp-uniform)
+            T acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = M::inf();
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) {
+                if (q < cnt) {
+                    const T *cr[4];
+                    T cq[4];
+#pragma unroll
+                    for (int u4 = 0; u4 < 4; ++u4) {
+                        const int jj = __shfl_sync(0xffffffffu, j, q + u4);
+                        cq[u4] = __shfl_sync(0xffffffffu, cur, q + u4);
+                        cr[u4] = cols + (int64_t)jj * ld;
+                    }
+                    T v[4][YB];
+#pragma unroll
+                    for (int u4 = 0; u4 < 4; ++u4)
+#pragma unroll
+                        for (int b = 0; b < YB; ++b)
+                            v[u4][b] = (b < nb && dyv[b] < cq[u4]) ? __ldcg(cr[u4] + yv[b]) : M::inf();
+#pragma unroll
+                    for (int u4 = 0; u4 < 4; ++u4)
+#pragma unroll
+                        for (int b = 0; b < YB; ++b) acc[q + u4] = M::add_min(dyv[b], v[u4][b], acc[q + u4]);
+                }
+            }
+            // transpose reduction: after the step over lane bit s, acc[k]
+            // (k < s) holds the partial minimum of pair (lane's high bits) + k
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const bool hi = lane & s;
+#pragma unroll
+                for (int k = 0; k < s; ++k) {
+                    const T send = hi ? acc[k] : acc[k + s];
+                    const T keep = hi ? acc[k + s] : acc[k];
+                    acc[k] = M::mn(keep, __shfl_xor_sync(0xffffffffu, send, s));
+                }
+            }
+            const T best = acc[0];
+            const bool lower = mine && best < cur;
             if (mine && (pass == 2 || lower)) {
-                const int32_t key = M::key(M::mn(acc, cur));
+                const int32_t key = M::key(M::mn(best, cur));
                 atomicMin(reinterpret_cast<int32_t *>(d.D + (int64_t)i * ld + j), key);
                 if (d.DT) atomicMin(reinterpret_cast<int32_t *>(d.DT + (int64_t)j * ld + i), key);
             }

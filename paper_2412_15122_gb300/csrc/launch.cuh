@@ -75,6 +75,23 @@ template <typename T> static size_t detect_smem(const Dev<T> &d, bool two) {
     return (size_t)d.span * sizeof(T) * (two ? 2 : 1);
 }
 
+// Detection: the streaming scan over the candidate rows (with exact counts of
+// the batches it flags), then the reservation and the writes of those units.
+template <typename T, bool TWO>
+static cudaError_t run_detect_t(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, const char *name) {
+    cudaError_t e;
+    const int scan_grid = TWO ? c.detect2_grid : c.detect_grid;
+    if ((e = launch(c, name, [&] { k_det_scan<T, TWO><<<scan_grid, 256, detect_smem(d, TWO), c.stream>>>(d, kind, a, w_old); })) != cudaSuccess) return e;
+    if ((e = launch(c, "detect_alloc", [&] { k_det_alloc<T><<<c.detalloc_grid, 256, 0, c.stream>>>(d); })) != cudaSuccess) return e;
+    return launch(c, "detect_write", [&] { k_det_write<T, TWO><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new); });
+}
+
+template <typename T>
+static cudaError_t run_detect(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, const char *name) {
+    if (d.undirected && kind == 1) return run_detect_t<T, true>(c, d, kind, a, w_old, w_new, name);
+    return run_detect_t<T, false>(c, d, kind, a, w_old, w_new, name);
+}
+
 // Both repair kernels are launched; the one whose path the device-side
 // decision did not choose returns at once.
 template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d, const RepairCfg &cfg) {
@@ -96,7 +113,7 @@ template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d
 template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
-    if ((e = launch(c, "detect_remove", [&] { k_detect<T, false><<<c.detect_grid, 256, detect_smem(d, false), c.stream>>>(d, 0, k, -1, (T)0, (T)0); })) != cudaSuccess) return e;
+    if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, "detect_remove")) != cudaSuccess) return e;
     if ((e = launch(c, "tombstone", [&] { k_tombstone<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
     return run_repair<T>(c, d, cfg);
 }
@@ -105,11 +122,7 @@ template <typename T>
 cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_old, T w_new, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "increase_prepass", [&] { k_inc_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w_old, w_new); })) != cudaSuccess) return e;
-    if (d.undirected) {
-        if ((e = launch(c, "detect_increase", [&] { k_detect<T, true><<<c.detect2_grid, 256, detect_smem(d, true), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
-    } else {
-        if ((e = launch(c, "detect_increase", [&] { k_detect<T, false><<<c.detect_grid, 256, detect_smem(d, false), c.stream>>>(d, 1, u, v, w_old, w_new); })) != cudaSuccess) return e;
-    }
+    if ((e = run_detect<T>(c, d, 1, u, w_old, w_new, "detect_increase")) != cudaSuccess) return e;
     return run_repair<T>(c, d, cfg);
 }
 
@@ -128,14 +141,16 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&warm_sm, k_repair_warm<T>, 256, 0)) != cudaSuccess) return e;
     if (warm_sm < 1) return cudaErrorInvalidConfiguration;
     c.warm_grid = warm_sm * c.num_sms;
-    if ((e = cudaFuncSetAttribute(k_detect<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_det_scan<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row)) != cudaSuccess) return e;
     int det_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_detect<T, false>, 256, row)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_det_scan<T, false>, 256, row)) != cudaSuccess) return e;
     c.detect_grid = std::max(1, det_sm) * c.num_sms;
-    if ((e = cudaFuncSetAttribute(k_detect<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * row))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_det_scan<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * row))) != cudaSuccess) return e;
     int det2_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det2_sm, k_detect<T, true>, 256, 2 * row)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det2_sm, k_det_scan<T, true>, 256, 2 * row)) != cudaSuccess) return e;
     c.detect2_grid = std::max(1, det2_sm) * c.num_sms;
+    c.detunit_grid = 4 * c.num_sms;
+    c.detalloc_grid = (int)((ld + 255) / 256);   // a lane per row: 256 rows a CTA
     size_t rel = (size_t)ld * sizeof(int32_t);
     if ((e = cudaFuncSetAttribute(k_insert_relax<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rel)) != cudaSuccess) return e;
     int rel_sm = 0;

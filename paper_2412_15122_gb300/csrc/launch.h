@@ -19,6 +19,8 @@ struct LaunchCtx {
     int relax_grid = 1;
     int warm_grid = 1;
     int detect2_grid = 1;
+    int detunit_grid = 1;
+    int detalloc_grid = 1;
 };
 
 template <typename T> cudaError_t run_fill(const LaunchCtx &, T *, T, int64_t);

@@ -39,6 +39,9 @@ METRIC = "warm-start APSP updates/s at n=8192 vs GPU cold FW; sweep HBM GB/s vs 
 UNIT = "updates/s"
 WORKLOAD = "n=8192 directed complete graph, int32 weights U[1,1e6], mixed updates 25% add / 25% remove / 25% decrease (w/2) / 25% increase (4w), uniform targets, one call per update"
 SWEEP_KERNELS = ("insert_reduce", "insert_relax", "detect_remove")
+# DRAM bytes (read + write) per launch of each sweep, from the ncu captures
+# summarised in profiles/traffic_sweeps_n8192.md (mean of two launches)
+SWEEP_TRAFFIC = {"insert_reduce": 271.32e6, "insert_relax": 274.83e6, "detect_remove": 274.49e6}
 
 
 def peaks():
@@ -180,6 +183,33 @@ def run_reference(args):
     }))
 
 
+def run_case(case: str):
+    """The workload's graph plus a few fixed updates, for profiler captures:
+    "removals" removes nodes 7115 (about 5k affected pairs) and 5533 (about
+    284k), "inserts" adds two nodes with the workload's weight distribution."""
+    import torch
+    from paper_2412_15122_gb300 import Graph, build
+    build.build()
+    W = synth.complete_digraph_i32(N, W_LO, W_HI, SEED)
+    g = Graph(W, CAP)
+    if case == "removals":
+        for k in (7115, 5533):
+            g.remove_node(k)
+            g.sync()
+            st = g.stats()
+            print(json.dumps({"op": "remove", "node": k, "pairs": st["affected_pairs"], "rows": st["affected_rows"],
+                              "passes": st["passes"], "warm_us": st["warm_total_us"]}))
+    else:
+        for t in range(2):
+            iw = synth.uniform_int(SEED, 60 + t, CAP, W_LO, W_HI).astype(np.int32)
+            ow = synth.uniform_int(SEED, 70 + t, CAP, W_LO, W_HI).astype(np.int32)
+            p = g.add_node(iw, ow)
+            g.sync()
+            print(json.dumps({"op": "add", "slot": p}))
+    g.close()
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,9 +220,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--no-stats", action="store_true")
+    ap.add_argument("--case", choices=["removals", "inserts"],
+                    help="run a small fixed case of the workload (for profiler captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args.case)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -358,7 +392,8 @@ def main():
         achieved = bytes_per_launch / (tot_ms / nl / 1000.0) / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
-                    "traffic": None, "bytes_per_launch": bytes_per_launch, "launches": nl,
+                    "traffic": SWEEP_TRAFFIC.get(name), "traffic_source": "profiles/traffic_sweeps_n8192.md",
+                    "bytes_per_launch": bytes_per_launch, "launches": nl,
                     "avg_launch_us": 1000 * tot_ms / nl}
 
     cpu = None

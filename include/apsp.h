@@ -208,6 +208,51 @@ apsp_status apsp_sync(apsp_graph *g);
  * overflows the scratch capacity). */
 apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta);
 
+/* ----- learned warm/cold cost model ---------------------------------------
+ * Algorithm 5 chooses between re-running the affected rows and recomputing
+ * everything with a threshold delta on Cost (Definition of Cost, Section
+ * 3.2).  APSP_DISPATCH_MODEL replaces the threshold with a small regression
+ * model evaluated on the device at the decision point: a multilayer
+ * perceptron 6 -> 64 -> 64 -> 2 with ReLU hidden layers (fp32) that predicts
+ * log2(microseconds) of the warm and of the cold path; the smaller wins.
+ *
+ * Features of an update (computed on the device from detection counters):
+ *   0 update type (0 add, 1/3 removal, 2/3 decrease, 1 increase)
+ *   1 log2(N), N = live nodes before the update
+ *   2 relative weight change (w_new - w_old) / w_old (0 for node updates)
+ *   3 affected pairs / N^2
+ *   4 Cost = rows with an affected pair / (N - 1)
+ *   5 rows with an affected pair / N
+ * Parameter block (APSP_MODEL_NPARAM floats, this order): mu[6], sd[6]
+ * (features are standardised as (f - mu) / sd), W1[64][6], b1[64],
+ * W2[64][64], b2[64], W3[2][64], b3[2]; output o = W3 relu(W2 relu(W1 x +
+ * b1) + b2) + b3.  The trainable part starts at W1 (APSP_MODEL_NTRAIN floats).
+ *
+ * The training entry points are stateless and run on the current CUDA
+ * device; all buffers are host memory owned by the caller.  Labels Y are
+ * n x 2 (warm, cold) log2 microseconds; a NaN label is missing and
+ * contributes nothing.  Loss = (1/n) sum over samples and outputs of
+ * (o - y)^2 over present labels. */
+#define APSP_MODEL_NPARAM 4750
+#define APSP_MODEL_NTRAIN 4738
+
+/* Install model parameters (host, APSP_MODEL_NPARAM floats) on the handle;
+ * used by APSP_DISPATCH_MODEL.  params == NULL removes the model. */
+apsp_status apsp_set_model(apsp_graph *g, const float *params);
+/* Loss and its gradient with respect to the trainable parameters over all n
+ * samples (X: n x 6 raw features, row-major; grad: APSP_MODEL_NTRAIN floats
+ * in parameter order).  Hand-written forward / backward kernels. */
+apsp_status apsp_model_loss_grad(const float *params, const float *X, const float *Y, int32_t n, float *loss,
+                                 float *grad);
+/* Outputs (n x 2) of the model for n raw feature rows. */
+apsp_status apsp_model_predict(const float *params, const float *X, int32_t n, float *out);
+/* Trains a model from scratch: standardisation from X, He-initialised
+ * weights from `seed` (SplitMix64), mini-batch Adam (beta 0.9 / 0.999) with
+ * learning rate lr for `epochs` passes over a per-epoch shuffle.  Writes
+ * APSP_MODEL_NPARAM floats to params_out and the final full-data loss. */
+apsp_status apsp_model_train(const float *X, const float *Y, int32_t n, int32_t epochs, int32_t batch, float lr,
+                             uint64_t seed, float *params_out, float *final_loss);
+
 /* ----- instrumentation ---------------------------------------------------- */
 
 /* Number of kernels this handle has launched so far. */

@@ -98,6 +98,10 @@ def _load():
         "apsp_profile_read": [P, ctypes.POINTER(apsp_profile_entry), I32, ctypes.POINTER(I32)],
         "apsp_profile_reset": [P],
         "apsp_add_node_noalloc": [P, I64, I32, P, I32, P, P, I32, P],
+        "apsp_set_model": [P, P],
+        "apsp_model_loss_grad": [P, P, P, I32, P, P],
+        "apsp_model_predict": [P, P, I32, P],
+        "apsp_model_train": [P, P, I32, I32, I32, ctypes.c_float, ctypes.c_uint64, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -245,6 +249,54 @@ def apsp_sync(g: int):
 def apsp_set_dispatch(g: int, mode, delta: float = 1.0):
     m = DISPATCH[mode] if isinstance(mode, str) else int(mode)
     _check(_load().apsp_set_dispatch(g, m, float(delta)), "apsp_set_dispatch")
+
+
+MODEL_NPARAM = 4750      # APSP_MODEL_NPARAM
+MODEL_NTRAIN = 4738      # APSP_MODEL_NTRAIN
+
+
+def _f32(a, shape_tail=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a
+
+
+def apsp_set_model(g: int, params):
+    """Install cost-model parameters (MODEL_NPARAM floats) on the handle; None removes it."""
+    if params is None:
+        _check(_load().apsp_set_model(g, None), "apsp_set_model")
+        return
+    p = _f32(params)
+    if p.size != MODEL_NPARAM:
+        raise ValueError(f"expected {MODEL_NPARAM} parameters, got {p.size}")
+    _check(_load().apsp_set_model(g, p.ctypes.data), "apsp_set_model")
+
+
+def apsp_model_loss_grad(params, X, Y):
+    """(loss, grad[MODEL_NTRAIN]) of the model over samples X (n x 6), Y (n x 2)."""
+    p, x, y = _f32(params), _f32(X), _f32(Y)
+    n = x.shape[0]
+    loss = np.zeros(1, np.float32)
+    grad = np.zeros(MODEL_NTRAIN, np.float32)
+    _check(_load().apsp_model_loss_grad(p.ctypes.data, x.ctypes.data, y.ctypes.data, n, loss.ctypes.data,
+                                        grad.ctypes.data), "apsp_model_loss_grad")
+    return float(loss[0]), grad
+
+
+def apsp_model_predict(params, X):
+    p, x = _f32(params), _f32(X)
+    out = np.zeros((x.shape[0], 2), np.float32)
+    _check(_load().apsp_model_predict(p.ctypes.data, x.ctypes.data, x.shape[0], out.ctypes.data), "apsp_model_predict")
+    return out
+
+
+def apsp_model_train(X, Y, epochs: int = 100, batch: int = 256, lr: float = 1e-3, seed: int = 1):
+    """Train a cost model from scratch; returns (params[MODEL_NPARAM], final full-data loss)."""
+    x, y = _f32(X), _f32(Y)
+    out = np.zeros(MODEL_NPARAM, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(_load().apsp_model_train(x.ctypes.data, y.ctypes.data, x.shape[0], epochs, batch, float(lr), int(seed),
+                                    out.ctypes.data, loss.ctypes.data), "apsp_model_train")
+    return out, float(loss[0])
 
 
 def apsp_launch_count(g: int) -> int:
@@ -395,6 +447,9 @@ class Graph:
 
     def set_dispatch(self, mode, delta: float = 1.0):
         apsp_set_dispatch(self.h, mode, delta)
+
+    def set_model(self, params):
+        apsp_set_model(self.h, params)
 
     def launches(self) -> int:
         return apsp_launch_count(self.h)

@@ -761,6 +761,21 @@ apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta) {
     return APSP_OK;
 }
 
+apsp_status apsp_set_model(apsp_graph *g, const float *params) {
+    if (!g) return APSP_E_ARG;
+    if (!params) {
+        g->has_model = false;
+        return APSP_OK;
+    }
+    for (int i = 0; i < apsp::MLP_IN; ++i)   // standardisation divides by sd
+        if (!(params[apsp::MLP_OFF_SD + i] > 0.f)) return APSP_E_ARG;
+    // the copy is staged before the call returns (pageable source)
+    cudaError_t e = cudaMemcpyAsync(g->model, params, apsp::MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->has_model = true;
+    return APSP_OK;
+}
+
 int64_t apsp_launch_count(apsp_graph *g) { return g ? g->launches : -1; }
 
 apsp_status apsp_profile_enable(apsp_graph *g, int32_t on) {

@@ -210,6 +210,196 @@ def run_case(case: str):
     torch.cuda.synchronize()
 
 
+TYPE_FEATURE = {"remove": 1.0 / 3.0, "increase": 1.0}
+
+
+def _euclid_stream(n0, count, seed, fractions, capacity):
+    """Update stream for an undirected Euclidean graph: rank-based node
+    references from synth.mixed_updates; a new node is a new uniform point
+    (its weights are drawn when it is applied)."""
+    return synth.mixed_updates(n0, count, seed, fractions=fractions, tight=True, capacity=capacity, stream=90)
+
+
+class _Tracked:
+    """A graph plus the host mirror of its weights (and, for Euclidean
+    graphs, its points) that the update streams of the dispatch study need."""
+
+    def __init__(self, Graph, W, cap, euclid, pts=None):
+        self.g = Graph(W, cap, undirected=euclid)
+        n = W.shape[0]
+        self.W = np.full((cap, cap), synth.INF_I32, np.int32)
+        self.W[:n, :n] = W
+        self.alive = np.zeros(cap, bool)
+        self.alive[:n] = True
+        self.euclid = euclid
+        self.pts = np.zeros((cap, 2))
+        if pts is not None:
+            self.pts[:n] = pts
+
+    def apply(self, up, seed, t):
+        """Issues one update; returns (kind, relative weight change)."""
+        g, live = self.g, np.flatnonzero(self.alive)
+        if up.kind == synth.ADD:
+            cap = len(self.alive)
+            iw = np.full(cap, synth.INF_I32, np.int32)
+            ow = iw.copy()
+            if self.euclid:
+                w, pnt = synth.new_point_weights_i32(self.pts[live], seed, 5000 + t)
+                iw[live] = w
+                ow[live] = w
+            else:
+                iw[live] = up.in_w[:len(live)]
+                ow[live] = up.out_w[:len(live)]
+            slot = g.add_node(iw, ow)
+            if self.euclid:
+                self.pts[slot] = pnt
+            self.W[:, slot] = np.where(self.alive, iw, synth.INF_I32)
+            self.W[slot, :] = np.where(self.alive, ow, synth.INF_I32)
+            self.W[slot, slot] = 0
+            self.alive[slot] = True
+            return "add", 0.0
+        if up.kind == synth.REMOVE:
+            k = int(live[up.a])
+            g.remove_node(k)
+            self.alive[k] = False
+            self.W[k, :] = synth.INF_I32
+            self.W[:, k] = synth.INF_I32
+            return "remove", 0.0
+        u, v = int(live[up.a]), int(live[up.b])
+        if up.tight:   # the lightest out-edge of u is always a shortest path
+            row = np.where(self.alive, self.W[u].astype(np.int64), synth.INF_I32)
+            row[u] = synth.INF_I32
+            v = int(np.argmin(row))
+        w0 = int(self.W[u, v])
+        w = w0 // 2 if up.kind == synth.DECREASE else min(max(1, w0) * 4, 1 << 26)
+        g.update_edge(u, v, w)
+        self.W[u, v] = w
+        if self.euclid:
+            self.W[v, u] = w
+        return up.kind, ((w - w0) / max(1, w0) if up.kind == synth.INCREASE else 0.0)
+
+
+def run_dispatch_study(args):
+    """Cost-model study (warm/cold dispatch): samples from real warm updates
+    at n in {1024, ..., 8192} on directed uniform and undirected Euclidean
+    graphs (features as the device computes them, labels = measured log2
+    microseconds of the warm repair and of the cold Floyd-Warshall at that
+    size), training on 80 %, held-out loss and decision accuracy on 20 %, then
+    total device time of the update stream on an n=16384 undirected Euclidean
+    graph under the delta rule, the model, always-warm and always-cold."""
+    import torch
+    from paper_2412_15122_gb300 import Graph, build
+    from paper_2412_15122_gb300 import apsp as A
+    build.build()
+    t_start = time.perf_counter()
+    sizes = (1024, 2048, 4096, 8192)
+    per = max(50, args.study_samples // (2 * len(sizes)))
+    X, Y = [], []
+    for euclid in (False, True):
+        for n in sizes:
+            seed = 300 + n + (1 if euclid else 0)
+            if euclid:
+                W, pts0 = synth.euclidean_undirected_i32(n, seed)
+                cap = n + 64
+                pts = np.zeros((cap, 2))
+                pts[:n] = pts0
+            else:
+                W = synth.complete_digraph_i32(n, 1, 10**6, seed)
+                cap, pts = n + 64, None
+            tg = _Tracked(Graph, W, cap, euclid, pts[:n] if euclid else None)
+            g = tg.g
+            # cold label: the blocked FW at this size
+            g.recompute()
+            g.sync()
+            t0 = time.perf_counter()
+            g.recompute()
+            g.sync()
+            cold_us = (time.perf_counter() - t0) * 1e6
+            g.set_dispatch("warm")
+            # adds balance removals so the graph keeps its size
+            mix = (0.35, 0.35, 0.0, 0.3)
+            ups = _euclid_stream(n, per * 3, seed, mix, cap) if euclid else \
+                synth.mixed_updates(n, per * 3, seed, fractions=mix, w_lo=1, w_hi=10**6,
+                                    tight=True, capacity=cap, stream=91)
+            got = 0
+            for t, up in enumerate(ups):
+                kind, dw = tg.apply(up, seed, t)
+                if kind not in TYPE_FEATURE:
+                    continue
+                st = g.stats()
+                if st["path"] != "warm":
+                    continue
+                nb = st["n_live"] + (1 if kind == "remove" else 0)
+                nb = max(2, nb)
+                X.append([TYPE_FEATURE[kind], np.log2(nb), dw, st["affected_pairs"] / (nb * nb),
+                          st["affected_rows"] / max(1, nb - 1), st["affected_rows"] / nb])
+                Y.append([np.log2(max(1.0, st["warm_total_us"])), np.log2(cold_us)])
+                got += 1
+                if got >= per:
+                    break
+            g.close()
+    X = np.asarray(X, np.float32)
+    Y = np.asarray(Y, np.float32)
+    order = np.argsort(synth.u64(7, 7, len(X)))
+    cut = int(0.8 * len(X))
+    tr, te = order[:cut], order[cut:]
+    t_train = time.perf_counter()
+    P, train_loss = A.apsp_model_train(X[tr], Y[tr], epochs=80, batch=256, lr=2e-3, seed=5)
+    train_s = time.perf_counter() - t_train
+    held_loss, _ = A.apsp_model_loss_grad(P, X[te], Y[te])
+    pred = A.apsp_model_predict(P, X[te])
+    acc = float(np.mean((pred[:, 0] <= pred[:, 1]) == (Y[te, 0] <= Y[te, 1])))
+
+    # ---- the four arms on n = 16384 undirected Euclidean updates -------------
+    n = 16384
+    W, pts0 = synth.euclidean_undirected_i32(n, 3)
+    cap = n + 64
+    ups = _euclid_stream(n, args.study_updates, 3, (0.1, 0.4, 0.1, 0.4), cap)
+    arms = {}
+    finals = {}
+    for arm in ("delta", "model", "warm", "cold"):
+        tg = _Tracked(Graph, W, cap, True, pts0)
+        g = tg.g
+        if arm == "delta":
+            g.set_dispatch("delta", 0.5)
+        elif arm == "model":
+            g.set_model(P)
+            g.set_dispatch("model")
+        else:
+            g.set_dispatch(arm)
+        g.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        paths = {}
+        for t, up in enumerate(ups):
+            tg.apply(up, 3, t)
+            st = g.stats()
+            paths[st["path"]] = paths.get(st["path"], 0) + 1
+        g.sync()
+        arms[arm] = {"seconds": time.perf_counter() - t0, "paths": paths}
+        finals[arm] = torch.from_numpy(g.D()).cuda()
+        alive, Wf = tg.alive.copy(), tg.W
+        g.close()
+    same = all(torch.equal(finals["warm"], finals[a]) for a in finals)
+    # 64 sampled rows of the final matrix against the oracle's Dijkstra
+    from oracle import apsp as O
+    Dw = finals["warm"].cpu().numpy()
+    m = Dw.shape[0]
+    live = np.flatnonzero(alive[:m])
+    rows = live[synth.uniform_int(3, 77, 64, 0, len(live) - 1)]
+    ref = O.dijkstra_rows(Wf[:m, :m], rows, alive=alive[:m])
+    ok_rows = bool(np.array_equal(O.to_i32(ref)[:, live], Dw[rows][:, live]))
+    print(json.dumps({
+        "study": "warm/cold dispatch", "samples": int(len(X)), "train": int(len(tr)), "held_out": int(len(te)),
+        "sizes": list(sizes), "graphs": ["directed complete U[1,1e6]", "undirected Euclidean round(1e4 d)"],
+        "model_train_seconds": train_s, "train_loss": train_loss, "held_out_loss": held_loss,
+        "held_out_decision_accuracy": acc,
+        "eval": {"workload": f"n={n} undirected Euclidean, {len(ups)} updates (10% add, 40% remove, "
+                             "10% decrease, 40% increase on lightest out-edges)", "arms": arms,
+                 "identical_final_D": bool(same), "sampled_rows_match_oracle": ok_rows},
+        "wall_seconds": time.perf_counter() - t_start}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,11 +412,18 @@ def main():
     ap.add_argument("--no-stats", action="store_true")
     ap.add_argument("--case", choices=["removals", "inserts"],
                     help="run a small fixed case of the workload (for profiler captures) and exit")
+    ap.add_argument("--study", choices=["dispatch"],
+                    help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
+                         "always-warm and always-cold on n=16384 undirected Euclidean updates")
+    ap.add_argument("--study-updates", type=int, default=100)
+    ap.add_argument("--study-samples", type=int, default=20000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
         return run_case(args.case)
+    if args.study == "dispatch":
+        return run_dispatch_study(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -253,6 +253,37 @@ apsp_status apsp_model_predict(const float *params, const float *X, int32_t n, f
 apsp_status apsp_model_train(const float *X, const float *Y, int32_t n, int32_t epochs, int32_t batch, float lr,
                              uint64_t seed, float *params_out, float *final_loss);
 
+/* ----- batched execution: many graphs, one persistent launch --------------
+ * A batch applies ordered update sequences to several independent graphs
+ * with ONE persistent kernel: CTAs take graphs from a device queue and each
+ * applies its graph's updates in order (add: Corollaries 1-2 and Theorem 3;
+ * removal and edge increase: Corollary 3's test, starting upper bounds and
+ * re-relaxation to the fixed point; edge decrease: the exact closed form).
+ * Results are the same exact matrices as the one-call-per-update path.
+ * Graphs must be directed, of one dtype, with capacity <= APSP_BATCH_MAX_SLOTS.
+ * Items of one graph are applied in their order in `items`; items of
+ * different graphs are independent.  The call validates every item first
+ * (nothing changes on an error), waits for each graph's pending work, and
+ * returns when the batch is done.  new_ids (count entries, may be NULL)
+ * receives the slot of each ADD and -1 for the other items. */
+#define APSP_BATCH_MAX_SLOTS 8192
+typedef enum { APSP_BATCH_ADD = 0, APSP_BATCH_REMOVE = 1, APSP_BATCH_EDGE = 2 } apsp_batch_op;
+typedef struct {
+    int32_t graph;            /* index into the graphs array of the call */
+    int32_t op;               /* apsp_batch_op */
+    int32_t u, v;             /* REMOVE: node u; EDGE: edge (u, v) */
+    const void *in_w;         /* ADD: host, `capacity` weights w(t -> new) (see apsp_add_node) */
+    const void *out_w;        /* ADD: host, `capacity` weights w(new -> t) */
+    double w;                 /* EDGE: new weight; missing (INF_I32 / +inf or larger) deletes the edge */
+} apsp_batch_item;
+typedef struct apsp_batch apsp_batch;
+/* An executor with its own stream (cuda_stream, or a new one when NULL) and
+ * device buffers that grow as needed. */
+apsp_status apsp_batch_create(apsp_batch **b, void *cuda_stream);
+apsp_status apsp_batch_run(apsp_batch *b, apsp_graph *const *graphs, int32_t n_graphs, const apsp_batch_item *items,
+                           int32_t count, int32_t *new_ids);
+apsp_status apsp_batch_destroy(apsp_batch *b);
+
 /* ----- instrumentation ---------------------------------------------------- */
 
 /* Number of kernels this handle has launched so far. */

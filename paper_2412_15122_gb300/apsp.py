@@ -52,6 +52,14 @@ class apsp_stats(ctypes.Structure):
         return d
 
 
+class apsp_batch_item(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("op", ctypes.c_int32), ("u", ctypes.c_int32), ("v", ctypes.c_int32),
+                ("in_w", ctypes.c_void_p), ("out_w", ctypes.c_void_p), ("w", ctypes.c_double)]
+
+
+BATCH_OPS = {"add": 0, "remove": 1, "edge": 2}
+
+
 class apsp_info(ctypes.Structure):
     _fields_ = [("n_live", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("capacity", ctypes.c_int32),
                 ("ld", ctypes.c_int32), ("dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
@@ -98,6 +106,9 @@ def _load():
         "apsp_profile_read": [P, ctypes.POINTER(apsp_profile_entry), I32, ctypes.POINTER(I32)],
         "apsp_profile_reset": [P],
         "apsp_add_node_noalloc": [P, I64, I32, P, I32, P, P, I32, P],
+        "apsp_batch_create": [ctypes.POINTER(P), P],
+        "apsp_batch_run": [P, ctypes.POINTER(P), I32, ctypes.POINTER(apsp_batch_item), I32, ctypes.POINTER(I32)],
+        "apsp_batch_destroy": [P],
         "apsp_set_model": [P, P],
         "apsp_model_loss_grad": [P, P, P, I32, P, P],
         "apsp_model_predict": [P, P, I32, P],
@@ -297,6 +308,63 @@ def apsp_model_train(X, Y, epochs: int = 100, batch: int = 256, lr: float = 1e-3
     _check(_load().apsp_model_train(x.ctypes.data, y.ctypes.data, x.shape[0], epochs, batch, float(lr), int(seed),
                                     out.ctypes.data, loss.ctypes.data), "apsp_model_train")
     return out, float(loss[0])
+
+
+def apsp_batch_create(stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(_load().apsp_batch_create(ctypes.byref(h), _stream_ptr(stream)), "apsp_batch_create")
+    return h.value
+
+
+def apsp_batch_destroy(b: int):
+    _check(_load().apsp_batch_destroy(b), "apsp_batch_destroy")
+
+
+def apsp_batch_run(b: int, graphs: Sequence[int], items) -> np.ndarray:
+    """items: sequence of (graph index, op, ...): ("add", in_w, out_w), ("remove", u)
+    or ("edge", u, v, w).  Returns the new slot of every add (-1 elsewhere)."""
+    n = len(items)
+    arr = (apsp_batch_item * max(1, n))()
+    keep = []
+    for q, it in enumerate(items):
+        gi, op = it[0], it[1]
+        e = arr[q]
+        e.graph = gi
+        e.op = BATCH_OPS[op]
+        if op == "add":
+            a = np.ascontiguousarray(it[2])
+            c = np.ascontiguousarray(it[3])
+            keep += [a, c]
+            e.in_w, e.out_w = a.ctypes.data, c.ctypes.data
+        elif op == "remove":
+            e.u = int(it[2])
+        else:
+            e.u, e.v, e.w = int(it[2]), int(it[3]), float(it[4])
+    hs = (ctypes.c_void_p * len(graphs))(*graphs)
+    ids = (ctypes.c_int32 * max(1, n))()
+    _check(_load().apsp_batch_run(b, hs, len(graphs), arr, n, ids), "apsp_batch_run")
+    return np.array(ids[:n], dtype=np.int32)
+
+
+class Batch:
+    """Executor that applies ordered updates to many graphs in one persistent launch."""
+
+    def __init__(self, stream=None):
+        self.h = apsp_batch_create(stream)
+
+    def run(self, graphs, items) -> np.ndarray:
+        return apsp_batch_run(self.h, [g.h for g in graphs], items)
+
+    def close(self):
+        if self.h:
+            apsp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def apsp_launch_count(g: int) -> int:

@@ -1,0 +1,341 @@
+// Batched execution: one persistent kernel applies a batch of updates to many
+// independent graphs.  CTAs take graphs from a device queue; a CTA applies its
+// graph's updates in order (each graph's sequence is causal, different graphs
+// are independent), with the same steps as the single-graph path:
+//   add       Corollary 1 / Corollary 2 as row reductions over D and D^T,
+//             then the Theorem 3 sweep, then row / column p;
+//   decrease  D = min(D, D[:,u] + w + D[v,:]) on rows with D[i][u] + w < D[i][v];
+//   increase  tightness of the old edge, Corollary 3's test through it, and
+//   removal   Corollary 3's test through the removed node (the
+//             need_update_list of Section 3.2): listed pairs restart from an
+//             achievable upper bound and are re-relaxed,
+//                 D[i][j] = min over x of D[i][x] + D[x][j],
+//             in full passes until a pass lowers nothing (the fixed point of
+//             D = min(D, D (x) D) over the listed pairs is exact).
+// Graphs are directed (D and D^T kept, row-major, ld = the graph's leading
+// dimension); the host has already chosen new nodes' slots, read old edge
+// weights from its mirror and masked new-node weight vectors.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace apsp {
+
+enum : int32_t { BOP_ADD = 0, BOP_REMOVE = 1, BOP_DECREASE = 2, BOP_INCREASE = 3 };
+
+struct BatchGraph {
+    void *D, *DT, *W;         // T* (device)
+    int32_t *alive;
+    int64_t ld;
+    uint32_t *mask;           // listed-pair bitmask scratch: mask_words words per row
+    int32_t mask_words;
+    int32_t first, count;     // this graph's updates in the batch's op array
+    int32_t status;           // written by the kernel: 0, or ERR_* bits
+};
+
+struct BatchOp {
+    int32_t op;
+    int32_t a, b;             // add: slot p; remove: k; edges: (u, v)
+    int32_t span;             // slots covered by the graph's sweeps during this update
+    int64_t vec;              // add: element offset of in_w then out_w (span each) in the vector arena
+    int32_t w_bits, w_old_bits;   // edges: new and old weight (bit patterns of T)
+};
+
+struct BatchHeader {
+    BatchGraph *graphs;
+    const BatchOp *ops;
+    const void *vecs;
+    int32_t n_graphs;
+    int32_t max_span;         // largest span of any update (sizes the shared arrays)
+    int32_t queue;            // next graph to take
+    int32_t pad_;
+};
+
+template <typename T> __device__ __forceinline__ T bits_as(int32_t b) {
+    if constexpr (std::is_same<T, float>::value) return __int_as_float(b);
+    else return (T)b;
+}
+
+template <typename T> struct BG {
+    T *D, *DT, *W;
+    int32_t *alive;
+    int64_t ld;
+    __device__ T &d(int i, int j) const { return D[(int64_t)i * ld + j]; }
+    __device__ T &dt(int i, int j) const { return DT[(int64_t)i * ld + j]; }
+    __device__ T &w(int i, int j) const { return W[(int64_t)i * ld + j]; }
+    __device__ void set(int i, int j, T v) const {
+        D[(int64_t)i * ld + j] = v;
+        DT[(int64_t)j * ld + i] = v;
+    }
+};
+
+// Warp-wide min over x < span of D[i][x] + D[x][j] (D[x][j] read as D^T row j).
+template <typename T> __device__ __forceinline__ T b_dot_min(const BG<T> &g, int i, int j, int span) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    const int lane = threadIdx.x & 31;
+    const V4 *r4 = reinterpret_cast<const V4 *>(g.D + (int64_t)i * g.ld);
+    const V4 *c4 = reinterpret_cast<const V4 *>(g.DT + (int64_t)j * g.ld);
+    T acc = M::inf();
+    for (int v = lane; v < span / 4; v += 32) {
+        const V4 a = __ldcg(r4 + v), b = __ldcg(c4 + v);
+        acc = M::add_min(a.x, b.x, acc);
+        acc = M::add_min(a.y, b.y, acc);
+        acc = M::add_min(a.z, b.z, acc);
+        acc = M::add_min(a.w, b.w, acc);
+    }
+    return warp_min(acc);
+}
+
+// Re-relaxes the listed pairs (bitmask rows of `words` words; the rows
+// holding any are rows[0, nrows)) in full passes until a pass lowers
+// nothing; returns false when the pass cap is reached.
+template <typename T>
+__device__ bool b_relax(const BG<T> &g, const uint32_t *mask, int words, int span, const int32_t *rows, int nrows) {
+    __shared__ int changed_s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int pass = 0; pass < MAX_PASSES; ++pass) {
+        if (threadIdx.x == 0) changed_s = 0;
+        __syncthreads();
+        bool changed = false;
+        for (int r = wid; r < nrows; r += nw) {
+            const int i = rows[r];
+            for (int w0 = 0; w0 < words; w0 += 32) {
+                const uint32_t my = w0 + lane < words ? __ldcg(mask + (int64_t)i * words + w0 + lane) : 0u;
+                for (unsigned nz = __ballot_sync(0xffffffffu, my != 0u); nz; nz &= nz - 1) {
+                    const int src = __ffs(nz) - 1;
+                    uint32_t m = __shfl_sync(0xffffffffu, my, src);
+                    while (m) {
+                        const int j = (w0 + src) * 32 + __ffs(m) - 1;
+                        m &= m - 1;
+                        const T cand = b_dot_min(g, i, j, span);
+                        if (lane == 0 && cand < __ldcg(&g.d(i, j))) {
+                            g.set(i, j, cand);
+                            changed = true;
+                        }
+                    }
+                }
+            }
+        }
+        if (changed) changed_s = 1;
+        __syncthreads();
+        const int any = changed_s;
+        __syncthreads();
+        if (!any) return true;
+    }
+    return false;
+}
+
+// Clears rows [0, span) of the bitmask and the listed-row count.
+__device__ __forceinline__ void b_clear_mask(uint32_t *mask, int words, int span, int *nrows_s) {
+    for (int64_t t = threadIdx.x; t < (int64_t)span * words; t += blockDim.x) mask[t] = 0u;
+    if (threadIdx.x == 0) *nrows_s = 0;
+    __syncthreads();
+}
+
+// Node insertion at slot p with masked weights wi (t -> p) and wo (p -> t).
+template <typename T>
+__device__ void b_add(const BG<T> &g, int p, int span, const T *wi, const T *wo, T *s_in, T *s_out) {
+    using M = MinPlus<T>;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // Corollary 2: D[i][p] = min_t D[i][t] + w(t -> p); Corollary 1:
+    // D[p][j] = min_t w(p -> t) + D[t][j], a row reduction over D^T row j
+    for (int r = wid; r < span; r += nw) {
+        T a = M::inf(), b = M::inf();
+        if (g.alive[r] && r != p) {
+            for (int t = lane; t < span; t += 32) {
+                a = M::mn(a, M::add(__ldcg(&g.d(r, t)), wi[t]));
+                b = M::mn(b, M::add(wo[t], __ldcg(&g.dt(r, t))));
+            }
+        }
+        a = warp_min(a);
+        b = warp_min(b);
+        if (lane == 0) {
+            s_in[r] = a;
+            s_out[r] = b;
+        }
+    }
+    __syncthreads();
+    // Theorem 3: D[i][j] = min(D[i][j], D[i][p] + D[p][j])
+    for (int i = wid; i < span; i += nw) {
+        const T vi = s_in[i];
+        if (i == p || !M::finite(vi)) continue;
+        for (int j = lane; j < span; j += 32) {
+            const T c = vi + s_out[j];
+            if (j != p && M::finite(s_out[j]) && c < __ldcg(&g.d(i, j))) g.set(i, j, c);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        const T out_t = t == p ? (T)0 : s_out[t];
+        const T in_t = t == p ? (T)0 : s_in[t];
+        g.set(p, t, out_t);
+        g.set(t, p, in_t);
+        g.w(p, t) = t == p ? (T)0 : wo[t];
+        g.w(t, p) = t == p ? (T)0 : wi[t];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) g.alive[p] = 1;
+    __syncthreads();
+}
+
+// Edge decrease (u, v) -> w.
+template <typename T> __device__ void b_decrease(const BG<T> &g, int u, int v, T w, int span, T *sx, T *sy) {
+    using M = MinPlus<T>;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        sx[t] = __ldcg(&g.dt(u, t));   // D[t][u]
+        sy[t] = __ldcg(&g.d(v, t));    // D[v][t]
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) g.w(u, v) = w;
+    for (int i = wid; i < span; i += nw) {
+        const T xi = sx[i];
+        if (!M::finite(xi) || !(M::add(xi, w) < __ldcg(&g.dt(v, i)))) continue;   // row filter
+        const T s = xi + w;
+        for (int j = lane; j < span; j += 32) {
+            const T c = s + sy[j];
+            if (M::finite(sy[j]) && c < __ldcg(&g.d(i, j))) g.set(i, j, c);
+        }
+    }
+    __syncthreads();
+}
+
+// Edge increase (u, v): w_old -> w (w may be missing: a deletion).  Returns
+// false on the pass cap.
+template <typename T>
+__device__ bool b_increase(const BG<T> &g, int u, int v, T w_old, T w, int span, uint32_t *mask, int words, T *sx,
+                           T *sy, int32_t *rows, int *nrows_s) {
+    using M = MinPlus<T>;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool tight_edge = M::tight(w_old, __ldcg(&g.d(u, v)));
+    __syncthreads();
+    if (threadIdx.x == 0) g.w(u, v) = w;
+    if (!tight_edge) {
+        __syncthreads();
+        return true;
+    }
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        sx[t] = __ldcg(&g.dt(u, t));   // D[t][u]
+        sy[t] = M::leg(__ldcg(&g.d(v, t)));
+    }
+    b_clear_mask(mask, words, span, nrows_s);
+    // pairs whose distance is a path through the old edge (Corollary 3 for an edge)
+    for (int i = wid; i < span; i += nw) {
+        const T xi = sx[i];
+        if (!M::finite(xi) || !g.alive[i]) continue;
+        const T s = M::add(xi, w_old);
+        if (!M::tight(s, __ldcg(&g.dt(v, i)))) continue;
+        bool any = false;
+        for (int j = lane; j < span; j += 32) {
+            const bool hit = j != i && M::slack_tight(M::slack(s + sy[j], __ldcg(&g.d(i, j))));
+            const unsigned b = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0 && b) mask[(int64_t)i * words + (j >> 5)] = b;
+            any |= b != 0u;
+        }
+        if (lane == 0 && any) rows[atomicAdd(nrows_s, 1)] = i;
+    }
+    __syncthreads();
+    // starting upper bounds: the direct edge, or the path through the edge at its new weight
+    const int nrows = *nrows_s;
+    for (int r = wid; r < nrows; r += nw) {
+        const int i = rows[r];
+        for (int wd = 0; wd < words; ++wd) {
+            const uint32_t m = mask[(int64_t)i * words + wd];
+            const int j = wd * 32 + lane;
+            if ((m >> lane) & 1u) {
+                const T via = M::add(M::add(sx[i], w), M::mn(sy[j], M::inf()));
+                g.set(i, j, M::mn(__ldcg(&g.w(i, j)), via));
+            }
+        }
+    }
+    __syncthreads();
+    return b_relax(g, mask, words, span, rows, nrows);
+}
+
+// Removal of node k.  Returns false on the pass cap.
+template <typename T>
+__device__ bool b_remove(const BG<T> &g, int k, int span, uint32_t *mask, int words, T *sx, T *sy, int32_t *rows,
+                         int *nrows_s) {
+    using M = MinPlus<T>;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        sx[t] = __ldcg(&g.dt(k, t));                         // D[t][k]
+        sy[t] = t == k ? unreachable_leg<T>() : M::leg(__ldcg(&g.d(k, t)));   // D[k][t]
+    }
+    b_clear_mask(mask, words, span, nrows_s);
+    // need_update_list: D[i][k] + D[k][j] == D[i][j], i != j, both != k
+    for (int i = wid; i < span; i += nw) {
+        const T xi = sx[i];
+        if (i == k || !M::finite(xi) || !g.alive[i]) continue;
+        bool any = false;
+        for (int j = lane; j < span; j += 32) {
+            const bool hit = j != i && M::slack_tight(M::slack(xi + sy[j], __ldcg(&g.d(i, j))));
+            const unsigned b = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0 && b) mask[(int64_t)i * words + (j >> 5)] = b;
+            any |= b != 0u;
+        }
+        if (lane == 0 && any) rows[atomicAdd(nrows_s, 1)] = i;
+    }
+    __syncthreads();
+    // tombstone k (Section 3.2: its distances become infinite), then the
+    // listed pairs restart from their direct edges
+    const T inf = M::inf();
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        g.set(k, t, inf);
+        g.set(t, k, inf);
+        g.w(k, t) = inf;
+        g.w(t, k) = inf;
+    }
+    if (threadIdx.x == 0) g.alive[k] = 0;
+    __syncthreads();
+    const int nrows = *nrows_s;
+    for (int r = wid; r < nrows; r += nw) {
+        const int i = rows[r];
+        for (int wd = 0; wd < words; ++wd) {
+            const uint32_t m = mask[(int64_t)i * words + wd];
+            const int j = wd * 32 + lane;
+            if ((m >> lane) & 1u) g.set(i, j, __ldcg(&g.w(i, j)));
+        }
+    }
+    __syncthreads();
+    return b_relax(g, mask, words, span, rows, nrows);
+}
+
+template <typename T> __global__ void __launch_bounds__(256) k_batch(BatchHeader *hdr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int gi_s, nrows_s;
+    const T *vecs = reinterpret_cast<const T *>(hdr->vecs);
+    while (true) {
+        if (threadIdx.x == 0) gi_s = atomicAdd(&hdr->queue, 1);
+        __syncthreads();
+        const int gi = gi_s;
+        __syncthreads();
+        if (gi >= hdr->n_graphs) break;
+        BatchGraph &bg = hdr->graphs[gi];
+        BG<T> g{reinterpret_cast<T *>(bg.D), reinterpret_cast<T *>(bg.DT), reinterpret_cast<T *>(bg.W), bg.alive, bg.ld};
+        T *s0 = reinterpret_cast<T *>(smem_raw);
+        T *s1 = s0 + hdr->max_span;
+        int32_t *srows = reinterpret_cast<int32_t *>(s1 + hdr->max_span);
+        int err = 0;
+        for (int q = bg.first; q < bg.first + bg.count; ++q) {
+            const BatchOp op = hdr->ops[q];
+            bool ok = true;
+            if (op.op == BOP_ADD) {
+                b_add<T>(g, op.a, op.span, vecs + op.vec, vecs + op.vec + op.span, s0, s1);
+            } else if (op.op == BOP_DECREASE) {
+                b_decrease<T>(g, op.a, op.b, bits_as<T>(op.w_bits), op.span, s0, s1);
+            } else if (op.op == BOP_INCREASE) {
+                ok = b_increase<T>(g, op.a, op.b, bits_as<T>(op.w_old_bits), bits_as<T>(op.w_bits), op.span, bg.mask,
+                                   bg.mask_words, s0, s1, srows, &nrows_s);
+            } else {
+                ok = b_remove<T>(g, op.a, op.span, bg.mask, bg.mask_words, s0, s1, srows, &nrows_s);
+            }
+            if (!ok) err |= ERR_PASSES;
+        }
+        if (threadIdx.x == 0) bg.status = err;
+        __syncthreads();
+    }
+}
+
+}  // namespace apsp

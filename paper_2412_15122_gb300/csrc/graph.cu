@@ -10,6 +10,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
+#include <new>
 #include <map>
 #include <string>
 #include <vector>
@@ -806,6 +808,301 @@ apsp_status apsp_profile_reset(apsp_graph *g) {
     flush_profile(g);
     g->prof_acc.clear();
     return APSP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched execution (apsp_batch_*): the host validates every item, resolves
+// slots / old weights / spans in order on each graph's mirrors, packs one
+// upload (header, graph table, updates, masked new-node vectors) and launches
+// one persistent kernel (k_batch) over all graphs.
+// ---------------------------------------------------------------------------
+
+struct apsp_batch {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char *h_blob = nullptr;   // pinned staging of the upload
+    size_t h_cap = 0;
+    char *d_blob = nullptr;
+    size_t d_cap = 0;
+    uint32_t *d_mask = nullptr;   // listed-pair bitmasks
+    size_t mask_cap = 0;          // words
+};
+
+namespace {
+
+size_t align256(size_t a) { return (a + 255) & ~size_t(255); }
+
+template <typename T> apsp_status batch_weight(double w, T *out) {
+    if (std::isnan(w)) return APSP_E_ARG;
+    if (w < 0) return APSP_E_NEGATIVE;
+    if constexpr (std::is_same<T, float>::value) {
+        *out = w >= (double)std::numeric_limits<float>::max() ? inf_of<float>() : (float)w;
+        if (*out == 0.f) *out = 0.f;
+    } else {
+        if (w >= (double)apsp::INF_I32) {
+            *out = apsp::INF_I32;
+        } else {
+            if (w != std::floor(w)) return APSP_E_ARG;
+            *out = (int32_t)w;
+        }
+    }
+    return APSP_OK;
+}
+
+template <typename T> int32_t bits_of(T v) {
+    int32_t b;
+    std::memcpy(&b, &v, sizeof(b));
+    return b;
+}
+
+template <typename T>
+apsp_status batch_impl(apsp_batch *b, apsp_graph *const *graphs, int n_graphs, const apsp_batch_item *items, int count,
+                       int32_t *new_ids) {
+    using apsp::BatchGraph;
+    using apsp::BatchHeader;
+    using apsp::BatchOp;
+    std::vector<std::vector<int>> per(n_graphs);
+    for (int q = 0; q < count; ++q) per[items[q].graph].push_back(q);
+    // ---- validation on simulated liveness (nothing changes on an error)
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        apsp_graph *g = graphs[gi];
+        std::vector<uint8_t> alive = g->alive_h;
+        int hwm = g->hwm;
+        for (int q : per[gi]) {
+            const apsp_batch_item &it = items[q];
+            if (it.op == APSP_BATCH_ADD) {
+                int p = -1;
+                for (int s = 0; s < hwm && p < 0; ++s)
+                    if (!alive[s]) p = s;
+                if (p < 0) p = hwm < g->cap ? hwm : -1;
+                if (p < 0) return APSP_E_CAPACITY;
+                if (!it.in_w || !it.out_w) return APSP_E_ARG;
+                const T *hi = (const T *)it.in_w, *ho = (const T *)it.out_w;
+                for (int t = 0; t < g->cap; ++t) {
+                    if (t == p || !alive[t]) continue;
+                    T a = hi[t], c = ho[t];
+                    apsp_status s1 = check_weight<T>(a), s2 = check_weight<T>(c);
+                    if (s1 != APSP_OK) return s1;
+                    if (s2 != APSP_OK) return s2;
+                }
+                alive[p] = 1;
+                hwm = std::max(hwm, p + 1);
+            } else if (it.op == APSP_BATCH_REMOVE) {
+                if (it.u < 0 || it.u >= g->cap || !alive[it.u]) return APSP_E_NODE;
+                alive[it.u] = 0;
+            } else if (it.op == APSP_BATCH_EDGE) {
+                if (it.u < 0 || it.v < 0 || it.u >= g->cap || it.v >= g->cap || !alive[it.u] || !alive[it.v])
+                    return APSP_E_NODE;
+                if (it.u == it.v) return APSP_E_ARG;
+                T w;
+                apsp_status s = batch_weight<T>(it.w, &w);
+                if (s != APSP_OK) return s;
+            } else {
+                return APSP_E_ARG;
+            }
+        }
+    }
+    // ---- wait for each graph's own pending work
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        settle_fetch<T>(graphs[gi]);
+        if (cudaStreamSynchronize(graphs[gi]->stream) != cudaSuccess) return APSP_E_CUDA;
+    }
+    // ---- resolve the updates in order on the mirrors
+    std::vector<BatchGraph> table;
+    std::vector<BatchOp> ops;
+    std::vector<T> vecs;
+    std::vector<int> spans;
+    int max_span = 32;
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        apsp_graph *g = graphs[gi];
+        BatchGraph bg{};
+        bg.D = g->D;
+        bg.DT = g->DT;
+        bg.W = g->W;
+        bg.alive = g->alive;
+        bg.ld = g->ld;
+        bg.first = (int)ops.size();
+        int gspan = span_of(g);
+        for (int q : per[gi]) {
+            const apsp_batch_item &it = items[q];
+            if (new_ids) new_ids[q] = -1;
+            BatchOp op{};
+            if (it.op == APSP_BATCH_ADD) {
+                const int p = pick_slot(g);
+                g->hwm = std::max(g->hwm, p + 1);
+                const int span = span_of(g);
+                const T *hi = (const T *)it.in_w, *ho = (const T *)it.out_w;
+                op.op = apsp::BOP_ADD;
+                op.a = p;
+                op.span = span;
+                op.vec = (int64_t)vecs.size();
+                vecs.resize(vecs.size() + 2 * (size_t)span, inf_of<T>());
+                T *wi = vecs.data() + op.vec, *wo = wi + span;
+                for (int t = 0; t < g->cap; ++t) {
+                    T a = inf_of<T>(), c = inf_of<T>();
+                    if (t != p && g->alive_h[t]) {
+                        a = hi[t];
+                        c = ho[t];
+                        check_weight<T>(a);
+                        check_weight<T>(c);
+                    }
+                    if (t < span) {
+                        wi[t] = a;
+                        wo[t] = c;
+                    }
+                    mirror<T>(g, t, p) = a;
+                    mirror<T>(g, p, t) = c;
+                }
+                mirror<T>(g, p, p) = (T)0;
+                g->alive_h[p] = 1;
+                g->n_live++;
+                if (new_ids) new_ids[q] = p;
+            } else if (it.op == APSP_BATCH_REMOVE) {
+                op.op = apsp::BOP_REMOVE;
+                op.a = it.u;
+                op.span = span_of(g);
+                g->alive_h[it.u] = 0;
+                for (int t = 0; t < g->cap; ++t) {
+                    mirror<T>(g, t, it.u) = inf_of<T>();
+                    mirror<T>(g, it.u, t) = inf_of<T>();
+                }
+                g->n_live--;
+            } else {
+                T w;
+                batch_weight<T>(it.w, &w);
+                const T w_old = mirror<T>(g, it.u, it.v);
+                if (w == w_old) continue;
+                op.op = w < w_old ? apsp::BOP_DECREASE : apsp::BOP_INCREASE;
+                op.a = it.u;
+                op.b = it.v;
+                op.span = span_of(g);
+                op.w_bits = bits_of<T>(w);
+                op.w_old_bits = bits_of<T>(w_old);
+                mirror<T>(g, it.u, it.v) = w;
+            }
+            gspan = std::max(gspan, op.span);
+            ops.push_back(op);
+        }
+        bg.count = (int)ops.size() - bg.first;
+        bg.mask_words = (gspan + 31) / 32;
+        spans.push_back(gspan);
+        max_span = std::max(max_span, gspan);
+        table.push_back(bg);
+    }
+    // ---- device buffers
+    size_t mask_words = 0;
+    for (int gi = 0; gi < n_graphs; ++gi) mask_words += (size_t)spans[gi] * table[gi].mask_words;
+    if (mask_words > b->mask_cap) {
+        if (b->d_mask) cudaFree(b->d_mask);
+        b->d_mask = nullptr;
+        b->mask_cap = 0;
+        if (cudaMalloc(&b->d_mask, mask_words * 4) != cudaSuccess) return APSP_E_NOMEM;
+        b->mask_cap = mask_words;
+    }
+    size_t off = 0;
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        table[gi].mask = b->d_mask + off;
+        off += (size_t)spans[gi] * table[gi].mask_words;
+    }
+    const size_t o_hdr = 0, o_tab = align256(sizeof(BatchHeader));
+    const size_t o_ops = o_tab + align256(table.size() * sizeof(BatchGraph));
+    const size_t o_vec = o_ops + align256(std::max<size_t>(1, ops.size()) * sizeof(BatchOp));
+    const size_t total = o_vec + align256(std::max<size_t>(1, vecs.size()) * sizeof(T));
+    if (total > b->h_cap) {
+        if (b->h_blob) cudaFreeHost(b->h_blob);
+        b->h_blob = nullptr;
+        b->h_cap = 0;
+        if (cudaMallocHost(&b->h_blob, total) != cudaSuccess) return APSP_E_NOMEM;
+        b->h_cap = total;
+    }
+    if (total > b->d_cap) {
+        if (b->d_blob) cudaFree(b->d_blob);
+        b->d_blob = nullptr;
+        b->d_cap = 0;
+        if (cudaMalloc(&b->d_blob, total) != cudaSuccess) return APSP_E_NOMEM;
+        b->d_cap = total;
+    }
+    BatchHeader hdr{};
+    hdr.graphs = reinterpret_cast<BatchGraph *>(b->d_blob + o_tab);
+    hdr.ops = reinterpret_cast<const BatchOp *>(b->d_blob + o_ops);
+    hdr.vecs = b->d_blob + o_vec;
+    hdr.n_graphs = n_graphs;
+    hdr.max_span = max_span;
+    hdr.queue = 0;
+    std::memcpy(b->h_blob + o_hdr, &hdr, sizeof(hdr));
+    std::memcpy(b->h_blob + o_tab, table.data(), table.size() * sizeof(BatchGraph));
+    if (!ops.empty()) std::memcpy(b->h_blob + o_ops, ops.data(), ops.size() * sizeof(BatchOp));
+    if (!vecs.empty()) std::memcpy(b->h_blob + o_vec, vecs.data(), vecs.size() * sizeof(T));
+    cudaError_t e = cudaMemcpyAsync(b->d_blob, b->h_blob, total, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const size_t smem = (size_t)max_span * (2 * sizeof(T) + sizeof(int32_t));
+    int per_sm = 0, dev = 0, sms = 1;
+    if ((e = apsp::batch_occupancy<T>(smem, &per_sm)) != cudaSuccess) return cuda_status(e);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(n_graphs, std::max(1, per_sm) * sms));
+    if ((e = apsp::run_batch<T>(b->stream, reinterpret_cast<BatchHeader *>(b->d_blob), grid, smem)) != cudaSuccess)
+        return cuda_status(e);
+    // statuses back (the graph table is re-read after the kernel)
+    e = cudaMemcpyAsync(b->h_blob + o_tab, b->d_blob + o_tab, table.size() * sizeof(BatchGraph), cudaMemcpyDeviceToHost,
+                        b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const BatchGraph *done = reinterpret_cast<const BatchGraph *>(b->h_blob + o_tab);
+    for (int gi = 0; gi < n_graphs; ++gi)
+        if (done[gi].status) return APSP_E_TIMEOUT;
+    return APSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+apsp_status apsp_batch_create(apsp_batch **out, void *cuda_stream) {
+    if (!out) return APSP_E_ARG;
+    apsp_batch *b = new (std::nothrow) apsp_batch();
+    if (!b) return APSP_E_NOMEM;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return APSP_E_CUDA;
+        }
+        b->own_stream = true;
+    }
+    *out = b;
+    return APSP_OK;
+}
+
+apsp_status apsp_batch_destroy(apsp_batch *b) {
+    if (!b) return APSP_E_ARG;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->h_blob) cudaFreeHost(b->h_blob);
+    if (b->d_blob) cudaFree(b->d_blob);
+    if (b->d_mask) cudaFree(b->d_mask);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return APSP_OK;
+}
+
+apsp_status apsp_batch_run(apsp_batch *b, apsp_graph *const *graphs, int32_t n_graphs, const apsp_batch_item *items,
+                           int32_t count, int32_t *new_ids) {
+    if (!b || !graphs || n_graphs <= 0 || count < 0 || (count > 0 && !items)) return APSP_E_ARG;
+    const int dtype = graphs[0] ? graphs[0]->dtype : -1;
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        apsp_graph *g = graphs[gi];
+        if (!g || g->dtype != dtype) return APSP_E_ARG;
+        if (g->undirected || !g->DT || g->cap > APSP_BATCH_MAX_SLOTS) return APSP_E_UNSUPPORTED;
+        for (int gj = 0; gj < gi; ++gj)
+            if (graphs[gj] == g) return APSP_E_ARG;
+    }
+    for (int q = 0; q < count; ++q)
+        if (items[q].graph < 0 || items[q].graph >= n_graphs) return APSP_E_ARG;
+    if (dtype == APSP_F32) return batch_impl<float>(b, graphs, n_graphs, items, count, new_ids);
+    return batch_impl<int32_t>(b, graphs, n_graphs, items, count, new_ids);
 }
 
 }  // extern "C"

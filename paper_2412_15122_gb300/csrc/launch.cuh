@@ -159,6 +159,18 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     return cudaSuccess;
 }
 
+// One persistent launch for a whole batch of graphs (batch.cuh).
+template <typename T> cudaError_t run_batch(cudaStream_t s, BatchHeader *hdr, int grid, size_t smem) {
+    k_batch<T><<<grid, 256, smem, s>>>(hdr);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t batch_occupancy(size_t smem, int *per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T>, 256, smem);
+}
+
 #define APSP_INSTANTIATE(T)                                                                                   \
     template cudaError_t run_fill<T>(const LaunchCtx &, T *, T, int64_t);                                     \
     template cudaError_t run_sanitize<T>(const LaunchCtx &, T *, int64_t, int, int, Ctl *);                   \
@@ -169,6 +181,8 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     template cudaError_t run_remove<T>(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);            \
     template cudaError_t run_increase<T>(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &); \
     template cudaError_t run_repair<T>(const LaunchCtx &, const Dev<T> &, const RepairCfg &);                 \
-    template cudaError_t setup_shapes<T>(LaunchCtx &, int64_t, int);
+    template cudaError_t setup_shapes<T>(LaunchCtx &, int64_t, int);                                          \
+    template cudaError_t run_batch<T>(cudaStream_t, BatchHeader *, int, size_t);                              \
+    template cudaError_t batch_occupancy<T>(size_t, int *);
 
 }  // namespace apsp

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cuda_runtime.h>
 
+#include "batch.cuh"
 #include "kernels.cuh"
 
 namespace apsp {
@@ -33,5 +34,7 @@ template <typename T> cudaError_t run_remove(const LaunchCtx &, const Dev<T> &, 
 template <typename T> cudaError_t run_increase(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &);
 template <typename T> cudaError_t run_repair(const LaunchCtx &, const Dev<T> &, const RepairCfg &);
 template <typename T> cudaError_t setup_shapes(LaunchCtx &, int64_t, int);
+template <typename T> cudaError_t run_batch(cudaStream_t, BatchHeader *, int, size_t);
+template <typename T> cudaError_t batch_occupancy(size_t, int *);
 
 }  // namespace apsp

@@ -1,0 +1,165 @@
+"""Batched execution (one persistent launch for many graphs) against the
+oracle and against the one-call-per-update path."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import apsp as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_15122_gb300 import apsp, build
+    build.build()
+    return apsp
+
+
+def _graph_and_updates(n, cap, seed, count, dtype, tight):
+    if dtype == "f32":
+        W = synth.lognormal_digraph_f32(n, seed)
+        ups = synth.mixed_updates(n, count, seed, capacity=cap, weights="lognormal", tight=tight, stream=11)
+    else:
+        W = synth.complete_digraph_i32(n, 1, 1000, seed)
+        ups = synth.mixed_updates(n, count, seed, capacity=cap, w_lo=1, w_hi=1000, tight=tight, stream=11)
+    return W, ups
+
+
+def _items_for(gi, ups, Wm, alive, cap, dtype):
+    """Concrete items with slot ids, tracking the weight mirror and liveness
+    the way the library assigns slots (lowest free slot)."""
+    items = []
+    inf = np.float32(np.inf) if dtype == "f32" else synth.INF_I32
+    npdt = np.float32 if dtype == "f32" else np.int32
+    for up in ups:
+        live = np.flatnonzero(alive)
+        if up.kind == synth.ADD:
+            iw = np.full(cap, inf, npdt)
+            ow = np.full(cap, inf, npdt)
+            iw[live] = up.in_w[:len(live)]
+            ow[live] = up.out_w[:len(live)]
+            p = int(np.flatnonzero(~alive)[0])
+            Wm[:, p] = np.where(alive, iw, inf)
+            Wm[p, :] = np.where(alive, ow, inf)
+            Wm[p, p] = 0
+            alive[p] = True
+            items.append((gi, "add", iw, ow))
+        elif up.kind == synth.REMOVE:
+            k = int(live[up.a])
+            alive[k] = False
+            Wm[k, :] = inf
+            Wm[:, k] = inf
+            items.append((gi, "remove", k))
+        else:
+            u, v = int(live[up.a]), int(live[up.b])
+            if up.tight:
+                row = np.where(alive, Wm[u], inf).astype(np.float64)
+                row[u] = np.inf
+                v = int(np.argmin(row))
+            w0 = Wm[u, v]
+            w = (w0 // 2 if dtype == "i32" else np.float32(w0 / 2)) if up.kind == synth.DECREASE else \
+                (min(int(w0) * 4, 1 << 26) if dtype == "i32" else np.float32(w0 * 4))
+            Wm[u, v] = w
+            items.append((gi, "edge", u, v, float(w)))
+    return items
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+@pytest.mark.parametrize("tight", [False, True])
+def test_batch_matches_oracle_and_single_calls(lib, dtype, tight):
+    from paper_2412_15122_gb300 import Batch, Graph
+    sizes = [40, 97, 130, 257]
+    graphs, singles, items, mirrors = [], [], [], []
+    for gi, n in enumerate(sizes):
+        cap = n + 24
+        W, ups = _graph_and_updates(n, cap, 100 + gi + (50 if tight else 0), 16, dtype, tight)
+        g = Graph(W, cap)
+        s = Graph(W, cap)
+        inf = np.float32(np.inf) if dtype == "f32" else synth.INF_I32
+        Wm = np.full((cap, cap), inf, W.dtype)
+        Wm[:n, :n] = W
+        alive = np.zeros(cap, bool)
+        alive[:n] = True
+        its = _items_for(gi, ups, Wm, alive, cap, dtype)
+        graphs.append(g)
+        singles.append(s)
+        items += its
+        mirrors.append((Wm, alive))
+    # interleave the graphs' items (per-graph order is what counts)
+    order = sorted(range(len(items)), key=lambda q: (q % 7, q))
+    per_graph = {}
+    for q in range(len(items)):
+        per_graph.setdefault(items[q][0], []).append(q)
+    mixed = []
+    pos = {gi: 0 for gi in per_graph}
+    for q in order:
+        gi = items[q][0]
+        mixed.append(items[per_graph[gi][pos[gi]]])
+        pos[gi] += 1
+    b = Batch()
+    ids = b.run(graphs, mixed)
+    assert (ids[[m[1] == "add" for m in mixed]] >= 0).all()
+    for gi, (g, s) in enumerate(zip(graphs, singles)):
+        for it in items:
+            if it[0] != gi:
+                continue
+            if it[1] == "add":
+                s.add_node(it[2], it[3])
+            elif it[1] == "remove":
+                s.remove_node(it[2])
+            else:
+                s.update_edge(it[2], it[3], it[4])
+        Wm, alive = mirrors[gi]
+        m = g.info()["n_slots"]
+        Db, Ds = g.D(), s.D()
+        np.testing.assert_array_equal(g.W()[:m, :m], Wm[:m, :m])
+        np.testing.assert_array_equal(g.alive()[:m].astype(bool), alive[:m])
+        ref = O.fw(Wm[:m, :m], alive[:m])
+        live = np.flatnonzero(alive[:m])
+        if dtype == "i32":
+            np.testing.assert_array_equal(Db[np.ix_(live, live)], O.to_i32(ref)[np.ix_(live, live)])
+            np.testing.assert_array_equal(Db, Ds)
+        else:
+            r = ref[np.ix_(live, live)]
+            d = Db[np.ix_(live, live)].astype(np.float64)
+            fin = np.isfinite(r)
+            assert (np.isfinite(d) == fin).all()
+            assert (np.abs(d[fin] - r[fin]) <= 1e-5 * np.abs(r[fin]) + 1e-6).all()
+        g.close()
+        s.close()
+    b.close()
+
+
+def test_batch_rejects_invalid_item_without_changes(lib):
+    from paper_2412_15122_gb300 import ApspError, Batch, Graph
+    W = synth.complete_digraph_i32(50, 1, 100, 3)
+    g = Graph(W, 64)
+    D0 = g.D().copy()
+    b = Batch()
+    with pytest.raises(ApspError):
+        b.run([g], [(0, "remove", 5), (0, "remove", 5)])   # second removal of a dead node
+    np.testing.assert_array_equal(g.D(), D0)
+    assert g.alive()[5] == 1
+    with pytest.raises(ApspError):
+        b.run([g], [(0, "edge", 1, 2, -3.0)])
+    b.run([g], [])
+    b.close()
+    g.close()
+
+
+def test_batch_then_single_calls_continue(lib):
+    from paper_2412_15122_gb300 import Batch, Graph
+    W = synth.complete_digraph_i32(64, 1, 100, 9)
+    g = Graph(W, 80)
+    b = Batch()
+    b.run([g], [(0, "remove", 3), (0, "edge", 4, 5, 1.0)])
+    g.remove_node(10)   # the single-graph path sees the batch's state
+    Wm = g.W()
+    alive = g.alive().astype(bool)
+    m = g.info()["n_slots"]
+    live = np.flatnonzero(alive[:m])
+    ref = O.to_i32(O.fw(Wm[:m, :m], alive[:m]))
+    np.testing.assert_array_equal(g.D()[np.ix_(live, live)], ref[np.ix_(live, live)])
+    b.close()
+    g.close()

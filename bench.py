@@ -400,6 +400,133 @@ def run_dispatch_study(args):
         "wall_seconds": time.perf_counter() - t_start}))
 
 
+def _batch_workload(n_graphs, per, dtype, seed):
+    """Graphs with n ~ U[64, 2048] and `per` ordered mixed updates each
+    (25 % of each kind, uniform targets), as concrete per-graph items."""
+    sizes = synth.uniform_int(seed, 3, n_graphs, 64, 2048)
+    graphs, items = [], []
+    for gi, n in enumerate(sizes):
+        n = int(n)
+        cap = n + per
+        if dtype == "f32":
+            W = synth.lognormal_digraph_f32(n, seed + gi)
+            ups = synth.mixed_updates(n, per, seed + gi, capacity=cap, weights="lognormal", stream=11)
+            inf, npdt = np.float32(np.inf), np.float32
+        else:
+            W = synth.complete_digraph_i32(n, 1, 1000, seed + gi)
+            ups = synth.mixed_updates(n, per, seed + gi, capacity=cap, w_lo=1, w_hi=1000, stream=11)
+            inf, npdt = synth.INF_I32, np.int32
+        Wm = np.full((cap, cap), inf, W.dtype)
+        Wm[:n, :n] = W
+        alive = np.zeros(cap, bool)
+        alive[:n] = True
+        its = []
+        for up in ups:
+            live = np.flatnonzero(alive)
+            if up.kind == synth.ADD:
+                iw = np.full(cap, inf, npdt)
+                ow = np.full(cap, inf, npdt)
+                iw[live] = up.in_w[:len(live)]
+                ow[live] = up.out_w[:len(live)]
+                p = int(np.flatnonzero(~alive)[0])
+                Wm[:, p] = np.where(alive, iw, inf)
+                Wm[p, :] = np.where(alive, ow, inf)
+                Wm[p, p] = 0
+                alive[p] = True
+                its.append((gi, "add", iw, ow))
+            elif up.kind == synth.REMOVE:
+                k = int(live[up.a])
+                alive[k] = False
+                Wm[k, :] = inf
+                Wm[:, k] = inf
+                its.append((gi, "remove", k))
+            else:
+                u, v = int(live[up.a]), int(live[up.b])
+                w0 = Wm[u, v]
+                if dtype == "f32":
+                    w = np.float32(w0 / 2) if up.kind == synth.DECREASE else np.float32(w0 * 4)
+                else:
+                    w = int(w0) // 2 if up.kind == synth.DECREASE else min(int(w0) * 4, 1 << 26)
+                Wm[u, v] = w
+                its.append((gi, "edge", u, v, float(w)))
+        graphs.append((W, cap))
+        items.append(its)
+    return graphs, items
+
+
+def run_batch_study(args):
+    """Batched execution: 512 directed complete graphs, n ~ U[64, 2048],
+    16 ordered mixed updates each, applied (a) by one persistent batch
+    launch, (b) by one library call per update, (c) as a cold Floyd-Warshall
+    of every graph; int32 U[1, 1000] and fp32 lognormal(0, 1) weights."""
+    import torch
+    from paper_2412_15122_gb300 import Batch, Graph, build
+    build.build()
+    per = 16
+    out = {"study": "batched execution", "graphs": args.study_graphs, "updates_per_graph": per,
+           "workload": "directed complete graphs, n ~ U[64, 2048], mixed updates 25% each kind, uniform targets"}
+    for dtype in ("i32", "f32"):
+        specs, items = _batch_workload(args.study_graphs, per, dtype, 40 if dtype == "i32" else 41)
+        n_upd = sum(len(x) for x in items)
+        # (a) batched
+        G = [Graph(W, cap) for W, cap in specs]
+        for g in G:
+            g.sync()
+        b = Batch()
+        flat = [it for its in items for it in its]
+        # warm-up of the executor's buffers on a copy of the first graph
+        gw = Graph(specs[0][0], specs[0][1])
+        b.run([gw], items[0])
+        gw.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run(G, flat)
+        batch_s = time.perf_counter() - t0
+        # (b) one call per update
+        S = [Graph(W, cap) for W, cap in specs]
+        for g in S:
+            g.sync()
+        t0 = time.perf_counter()
+        for gi, its in enumerate(items):
+            g = S[gi]
+            for it in its:
+                if it[1] == "add":
+                    g.add_node(it[2], it[3])
+                elif it[1] == "remove":
+                    g.remove_node(it[2])
+                else:
+                    g.update_edge(it[2], it[3], it[4])
+        for g in S:
+            g.sync()
+        single_s = time.perf_counter() - t0
+        # identical results, graph by graph (int32 exact, fp32 within 1e-5)
+        worst = 0.0
+        for g, s in zip(G, S):
+            a, c = torch.from_numpy(g.D()).cuda(), torch.from_numpy(s.D()).cuda()
+            if dtype == "i32":
+                worst = max(worst, float((a != c).sum().item()))
+            else:
+                fin = torch.isfinite(c)
+                rel = ((a[fin] - c[fin]).abs() / c[fin].abs().clamp_min(1e-30)).max().item() if fin.any() else 0.0
+                worst = max(worst, rel)
+        # (c) cold FW of every graph (the state after the updates)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g in G:
+            g.recompute()
+        for g in G:
+            g.sync()
+        cold_s = time.perf_counter() - t0
+        for g in G + S:
+            g.close()
+        b.close()
+        out[dtype] = {"updates": n_upd, "batched_seconds": batch_s, "batched_updates_per_s": n_upd / batch_s,
+                      "single_call_seconds": single_s, "single_call_updates_per_s": n_upd / single_s,
+                      "cold_fw_all_graphs_seconds": cold_s,
+                      ("mismatched_entries" if dtype == "i32" else "max_rel_diff"): worst}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,7 +539,8 @@ def main():
     ap.add_argument("--no-stats", action="store_true")
     ap.add_argument("--case", choices=["removals", "inserts"],
                     help="run a small fixed case of the workload (for profiler captures) and exit")
-    ap.add_argument("--study", choices=["dispatch"],
+    ap.add_argument("--study-graphs", type=int, default=512)
+    ap.add_argument("--study", choices=["dispatch", "batch"],
                     help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
                          "always-warm and always-cold on n=16384 undirected Euclidean updates")
     ap.add_argument("--study-updates", type=int, default=100)
@@ -424,6 +552,8 @@ def main():
         return run_case(args.case)
     if args.study == "dispatch":
         return run_dispatch_study(args)
+    if args.study == "batch":
+        return run_batch_study(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

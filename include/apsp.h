@@ -284,6 +284,42 @@ apsp_status apsp_batch_run(apsp_batch *b, apsp_graph *const *graphs, int32_t n_g
                            int32_t count, int32_t *new_ids);
 apsp_status apsp_batch_destroy(apsp_batch *b);
 
+/* ----- serving loop ---------------------------------------------------------
+ * Replays a trace of timed requests against resident graphs in real time with
+ * continuous (wave-level) batching: arrived requests queue per graph; while
+ * the GPU is busy with one wave the next arrivals queue, and when it is free
+ * one wave admits every queued request whose graph fits the budget (a query
+ * ends its graph's share of a wave, so it sees exactly the updates that
+ * arrived before it).  In a wave, graphs with capacity <= small_max_slots are
+ * updated by one persistent batched launch (apsp_batch_*), which flags each
+ * graph's completion in mapped host memory as soon as its CTA finishes;
+ * larger graphs run the one-call-per-update path on their own streams,
+ * completion observed with events.  Per graph, requests take effect in
+ * arrival order, so every graph ends exactly as if its requests had been
+ * applied alone.  Requests must be sorted by arrival time. */
+#define APSP_BATCH_QUERY 3    /* request op besides apsp_batch_op: distance u -> v */
+typedef struct {
+    apsp_batch_item item;     /* ADD / REMOVE / EDGE, or APSP_BATCH_QUERY with (u, v) */
+    double arrival_s;         /* seconds after the start of apsp_serve */
+} apsp_request;
+typedef struct {
+    double admit_s;           /* seconds after the start: taken into a wave */
+    double done_s;            /* seconds after the start: result visible on the host */
+    double dist;              /* QUERY: the distance (missing: INF_I32 or +inf) */
+    int32_t status;           /* apsp_status of the request */
+    int32_t wave;             /* wave that served it */
+    int32_t new_id;           /* ADD: the new node's slot, else -1 */
+    int32_t pad_;
+} apsp_request_result;
+typedef struct {
+    double hbm_budget_bytes;  /* bytes of graph state (W, D, D^T) one wave may touch; 0 = unlimited
+                                 (a single graph larger than the budget still runs alone) */
+    int32_t small_max_slots;  /* graphs of capacity <= this use the batched kernel (0: none) */
+    int32_t max_wave_requests;/* 0 = unlimited */
+} apsp_serve_config;
+apsp_status apsp_serve(apsp_graph *const *graphs, int32_t n_graphs, const apsp_request *reqs, int32_t count,
+                       const apsp_serve_config *cfg, apsp_request_result *results);
+
 /* ----- instrumentation ---------------------------------------------------- */
 
 /* Number of kernels this handle has launched so far. */
@@ -329,6 +365,9 @@ apsp_status apsp_add_node_noalloc(void *D, int64_t ld, int32_t n_slots, const in
                                   int32_t p, void *cuda_stream);
 
 const char *apsp_status_string(apsp_status s);
+/* The CUDA runtime error code behind this thread's last APSP_E_CUDA or
+ * APSP_E_NOMEM (0 if none); *name (may be NULL) receives its name. */
+int32_t apsp_last_cuda_error(const char **name);
 /* Library version, e.g. "0.1.0". */
 const char *apsp_version(void);
 

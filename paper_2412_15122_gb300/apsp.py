@@ -57,7 +57,22 @@ class apsp_batch_item(ctypes.Structure):
                 ("in_w", ctypes.c_void_p), ("out_w", ctypes.c_void_p), ("w", ctypes.c_double)]
 
 
-BATCH_OPS = {"add": 0, "remove": 1, "edge": 2}
+BATCH_OPS = {"add": 0, "remove": 1, "edge": 2, "query": 3}
+
+
+class apsp_request(ctypes.Structure):
+    _fields_ = [("item", apsp_batch_item), ("arrival_s", ctypes.c_double)]
+
+
+class apsp_request_result(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("dist", ctypes.c_double),
+                ("status", ctypes.c_int32), ("wave", ctypes.c_int32), ("new_id", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+class apsp_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("small_max_slots", ctypes.c_int32),
+                ("max_wave_requests", ctypes.c_int32)]
 
 
 class apsp_info(ctypes.Structure):
@@ -109,6 +124,8 @@ def _load():
         "apsp_batch_create": [ctypes.POINTER(P), P],
         "apsp_batch_run": [P, ctypes.POINTER(P), I32, ctypes.POINTER(apsp_batch_item), I32, ctypes.POINTER(I32)],
         "apsp_batch_destroy": [P],
+        "apsp_serve": [ctypes.POINTER(P), I32, ctypes.POINTER(apsp_request), I32, ctypes.POINTER(apsp_serve_config),
+                       ctypes.POINTER(apsp_request_result)],
         "apsp_set_model": [P, P],
         "apsp_model_loss_grad": [P, P, P, I32, P, P],
         "apsp_model_predict": [P, P, I32, P],
@@ -123,6 +140,8 @@ def _load():
     lib.apsp_status_string.argtypes = [ctypes.c_int]
     lib.apsp_status_string.restype = ctypes.c_char_p
     lib.apsp_version.restype = ctypes.c_char_p
+    lib.apsp_last_cuda_error.argtypes = [ctypes.POINTER(ctypes.c_char_p)]
+    lib.apsp_last_cuda_error.restype = ctypes.c_int32
     _lib = lib
     return lib
 
@@ -138,8 +157,17 @@ def _status_string(s: int) -> str:
         return "?"
 
 
+def apsp_last_cuda_error():
+    name = ctypes.c_char_p()
+    code = int(_load().apsp_last_cuda_error(ctypes.byref(name)))
+    return code, (name.value.decode() if name.value else "")
+
+
 def _check(s: int, where: str):
     if s != 0:
+        if STATUS.get(s) in ("APSP_E_CUDA", "APSP_E_NOMEM"):
+            code, name = apsp_last_cuda_error()
+            raise ApspError(s, f"{where} [{name} {code}]")
         raise ApspError(s, where)
 
 
@@ -327,23 +355,47 @@ def apsp_batch_run(b: int, graphs: Sequence[int], items) -> np.ndarray:
     arr = (apsp_batch_item * max(1, n))()
     keep = []
     for q, it in enumerate(items):
-        gi, op = it[0], it[1]
-        e = arr[q]
-        e.graph = gi
-        e.op = BATCH_OPS[op]
-        if op == "add":
-            a = np.ascontiguousarray(it[2])
-            c = np.ascontiguousarray(it[3])
-            keep += [a, c]
-            e.in_w, e.out_w = a.ctypes.data, c.ctypes.data
-        elif op == "remove":
-            e.u = int(it[2])
-        else:
-            e.u, e.v, e.w = int(it[2]), int(it[3]), float(it[4])
+        _fill_item(arr[q], it, keep)
     hs = (ctypes.c_void_p * len(graphs))(*graphs)
     ids = (ctypes.c_int32 * max(1, n))()
     _check(_load().apsp_batch_run(b, hs, len(graphs), arr, n, ids), "apsp_batch_run")
     return np.array(ids[:n], dtype=np.int32)
+
+
+def _fill_item(e, it, keep):
+    gi, op = it[0], it[1]
+    e.graph = gi
+    e.op = BATCH_OPS[op]
+    if op == "add":
+        a = np.ascontiguousarray(it[2])
+        c = np.ascontiguousarray(it[3])
+        keep += [a, c]
+        e.in_w, e.out_w = a.ctypes.data, c.ctypes.data
+    elif op == "remove":
+        e.u = int(it[2])
+    elif op == "query":
+        e.u, e.v = int(it[2]), int(it[3])
+    else:
+        e.u, e.v, e.w = int(it[2]), int(it[3]), float(it[4])
+
+
+def apsp_serve(graphs: Sequence[int], requests, arrivals, hbm_budget_bytes: float = 0.0, small_max_slots: int = 0,
+               max_wave_requests: int = 0) -> dict:
+    """Replays requests (items as for apsp_batch_run, plus ("query", u, v)) that
+    arrive at `arrivals` (seconds, non-decreasing).  Returns numpy arrays:
+    admit_s, done_s, dist, status, wave, new_id."""
+    n = len(requests)
+    arr = (apsp_request * max(1, n))()
+    keep = []
+    for q, it in enumerate(requests):
+        _fill_item(arr[q].item, it, keep)
+        arr[q].arrival_s = float(arrivals[q])
+    cfg = apsp_serve_config(float(hbm_budget_bytes), int(small_max_slots), int(max_wave_requests))
+    out = (apsp_request_result * max(1, n))()
+    hs = (ctypes.c_void_p * len(graphs))(*graphs)
+    _check(_load().apsp_serve(hs, len(graphs), arr, n, ctypes.byref(cfg), out), "apsp_serve")
+    res = {k: np.array([getattr(out[q], k) for q in range(n)]) for k in ("admit_s", "done_s", "dist", "status", "wave", "new_id")}
+    return res
 
 
 class Batch:

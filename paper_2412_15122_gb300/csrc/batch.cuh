@@ -49,6 +49,7 @@ struct BatchHeader {
     int32_t max_span;         // largest span of any update (sizes the shared arrays)
     int32_t queue;            // next graph to take
     int32_t pad_;
+    volatile int32_t *done;   // optional (mapped host memory): 1 + status per graph when it is finished
 };
 
 template <typename T> __device__ __forceinline__ T bits_as(int32_t b) {
@@ -69,6 +70,21 @@ template <typename T> struct BG {
     }
 };
 
+// A warp walks vectors [0, span/4) of a row, 4 vectors per lane in flight,
+// calling f(c4, v) for each.
+template <typename V4, typename F> __device__ __forceinline__ void b_row(const V4 *row, int nv4, F &&f) {
+    const int lane = threadIdx.x & 31;
+    for (int c0 = lane; c0 < nv4; c0 += 128) {
+        V4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (c0 + 32 * k < nv4) v[k] = __ldcg(row + c0 + 32 * k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (c0 + 32 * k < nv4) f(c0 + 32 * k, v[k]);
+    }
+}
+
 // Warp-wide min over x < span of D[i][x] + D[x][j] (D[x][j] read as D^T row j).
 template <typename T> __device__ __forceinline__ T b_dot_min(const BG<T> &g, int i, int j, int span) {
     using M = MinPlus<T>;
@@ -76,13 +92,24 @@ template <typename T> __device__ __forceinline__ T b_dot_min(const BG<T> &g, int
     const int lane = threadIdx.x & 31;
     const V4 *r4 = reinterpret_cast<const V4 *>(g.D + (int64_t)i * g.ld);
     const V4 *c4 = reinterpret_cast<const V4 *>(g.DT + (int64_t)j * g.ld);
+    const int nv4 = span / 4;
     T acc = M::inf();
-    for (int v = lane; v < span / 4; v += 32) {
-        const V4 a = __ldcg(r4 + v), b = __ldcg(c4 + v);
-        acc = M::add_min(a.x, b.x, acc);
-        acc = M::add_min(a.y, b.y, acc);
-        acc = M::add_min(a.z, b.z, acc);
-        acc = M::add_min(a.w, b.w, acc);
+    for (int v0 = lane; v0 < nv4; v0 += 128) {
+        V4 a[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (v0 + 32 * k < nv4) {
+                a[k] = __ldcg(r4 + v0 + 32 * k);
+                b[k] = __ldcg(c4 + v0 + 32 * k);
+            }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (v0 + 32 * k < nv4) {
+                acc = M::add_min(a[k].x, b[k].x, acc);
+                acc = M::add_min(a[k].y, b[k].y, acc);
+                acc = M::add_min(a[k].z, b[k].z, acc);
+                acc = M::add_min(a[k].w, b[k].w, acc);
+            }
     }
     return warp_min(acc);
 }
@@ -135,18 +162,31 @@ __device__ __forceinline__ void b_clear_mask(uint32_t *mask, int words, int span
 
 // Node insertion at slot p with masked weights wi (t -> p) and wo (p -> t).
 template <typename T>
-__device__ void b_add(const BG<T> &g, int p, int span, const T *wi, const T *wo, T *s_in, T *s_out) {
+__device__ __noinline__ void b_add(const BG<T> &g, int p, int span, const T *wi, const T *wo, T *s_in, T *s_out, T *s_wi,
+                      T *s_wo) {
     using M = MinPlus<T>;
+    using V4 = typename M::V4;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nv4 = span / 4;
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        s_wi[t] = wi[t];
+        s_wo[t] = wo[t];
+    }
+    __syncthreads();
+    const V4 *wi4 = reinterpret_cast<const V4 *>(s_wi), *wo4 = reinterpret_cast<const V4 *>(s_wo);
     // Corollary 2: D[i][p] = min_t D[i][t] + w(t -> p); Corollary 1:
     // D[p][j] = min_t w(p -> t) + D[t][j], a row reduction over D^T row j
     for (int r = wid; r < span; r += nw) {
         T a = M::inf(), b = M::inf();
         if (g.alive[r] && r != p) {
-            for (int t = lane; t < span; t += 32) {
-                a = M::mn(a, M::add(__ldcg(&g.d(r, t)), wi[t]));
-                b = M::mn(b, M::add(wo[t], __ldcg(&g.dt(r, t))));
-            }
+            b_row(reinterpret_cast<const V4 *>(g.D + (int64_t)r * g.ld), nv4, [&](int c4, const V4 &v) {
+                const V4 w = wi4[c4];
+                a = M::mn(a, M::mn(M::mn(M::add(v.x, w.x), M::add(v.y, w.y)), M::mn(M::add(v.z, w.z), M::add(v.w, w.w))));
+            });
+            b_row(reinterpret_cast<const V4 *>(g.DT + (int64_t)r * g.ld), nv4, [&](int c4, const V4 &v) {
+                const V4 w = wo4[c4];
+                b = M::mn(b, M::mn(M::mn(M::add(v.x, w.x), M::add(v.y, w.y)), M::mn(M::add(v.z, w.z), M::add(v.w, w.w))));
+            });
         }
         a = warp_min(a);
         b = warp_min(b);
@@ -156,14 +196,22 @@ __device__ void b_add(const BG<T> &g, int p, int span, const T *wi, const T *wo,
         }
     }
     __syncthreads();
-    // Theorem 3: D[i][j] = min(D[i][j], D[i][p] + D[p][j])
+    // Theorem 3: D[i][j] = min(D[i][j], D[i][p] + D[p][j]) (s_out[p] and the
+    // dead columns are missing, so those entries never improve)
+    if (threadIdx.x == 0) s_out[p] = M::inf();
+    __syncthreads();
     for (int i = wid; i < span; i += nw) {
         const T vi = s_in[i];
         if (i == p || !M::finite(vi)) continue;
-        for (int j = lane; j < span; j += 32) {
-            const T c = vi + s_out[j];
-            if (j != p && M::finite(s_out[j]) && c < __ldcg(&g.d(i, j))) g.set(i, j, c);
-        }
+        T *Di = g.D + (int64_t)i * g.ld;
+        b_row(reinterpret_cast<const V4 *>(Di), nv4, [&](int c4, const V4 &v) {
+            const T dv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const T o = s_out[4 * c4 + e];
+                if (M::finite(o) && vi + o < dv[e]) g.set(i, 4 * c4 + e, vi + o);
+            }
+        });
     }
     __syncthreads();
     for (int t = threadIdx.x; t < span; t += blockDim.x) {
@@ -171,16 +219,49 @@ __device__ void b_add(const BG<T> &g, int p, int span, const T *wi, const T *wo,
         const T in_t = t == p ? (T)0 : s_in[t];
         g.set(p, t, out_t);
         g.set(t, p, in_t);
-        g.w(p, t) = t == p ? (T)0 : wo[t];
-        g.w(t, p) = t == p ? (T)0 : wi[t];
+        g.w(p, t) = t == p ? (T)0 : s_wo[t];
+        g.w(t, p) = t == p ? (T)0 : s_wi[t];
     }
     __syncthreads();
     if (threadIdx.x == 0) g.alive[p] = 1;
     __syncthreads();
 }
 
+// Marks the entries j != i of row i with s + y[j] tight against D[i][j] in
+// the row's bitmask words (bit j % 32 of word j / 32); returns whether any.
+// Lane l holds 4 consecutive entries of each 128-entry block, so the bits of
+// a 32-entry word come from 8 lanes and are combined with shuffles.
+template <typename T>
+__device__ __forceinline__ bool b_detect_row(const BG<T> &g, int i, T s, const T *sy, int span, uint32_t *mrow) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    const int lane = threadIdx.x & 31;
+    bool any = false;
+    b_row(reinterpret_cast<const V4 *>(g.D + (int64_t)i * g.ld), span / 4, [&](int c4, const V4 &v) {
+        const T dv[4] = {v.x, v.y, v.z, v.w};
+        uint32_t m = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = 4 * c4 + e;
+            if (j != i && M::slack_tight(M::slack(s + sy[j], dv[e]))) m |= 1u << e;
+        }
+        // entries 4 c4 .. 4 c4 + 3 sit at bits 4 (c4 % 8) .. of word c4 / 8;
+        // the row length is a multiple of 32 entries, so a word's 8 lanes
+        // are active together (the last batch of a row may leave whole
+        // groups out)
+        const unsigned am = __activemask();
+        m <<= 4 * (c4 & 7);
+        m |= __shfl_xor_sync(am, m, 1);
+        m |= __shfl_xor_sync(am, m, 2);
+        m |= __shfl_xor_sync(am, m, 4);
+        if ((lane & 7) == 0 && m) mrow[c4 >> 3] = m;
+        any |= m != 0u;
+    });
+    return __any_sync(0xffffffffu, any);
+}
+
 // Edge decrease (u, v) -> w.
-template <typename T> __device__ void b_decrease(const BG<T> &g, int u, int v, T w, int span, T *sx, T *sy) {
+template <typename T> __device__ __noinline__ void b_decrease(const BG<T> &g, int u, int v, T w, int span, T *sx, T *sy) {
     using M = MinPlus<T>;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int t = threadIdx.x; t < span; t += blockDim.x) {
@@ -193,10 +274,15 @@ template <typename T> __device__ void b_decrease(const BG<T> &g, int u, int v, T
         const T xi = sx[i];
         if (!M::finite(xi) || !(M::add(xi, w) < __ldcg(&g.dt(v, i)))) continue;   // row filter
         const T s = xi + w;
-        for (int j = lane; j < span; j += 32) {
-            const T c = s + sy[j];
-            if (M::finite(sy[j]) && c < __ldcg(&g.d(i, j))) g.set(i, j, c);
-        }
+        b_row(reinterpret_cast<const typename M::V4 *>(g.D + (int64_t)i * g.ld), span / 4,
+              [&](int c4, const typename M::V4 &dv4) {
+                  const T dv[4] = {dv4.x, dv4.y, dv4.z, dv4.w};
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                      const T y = sy[4 * c4 + e];
+                      if (M::finite(y) && s + y < dv[e]) g.set(i, 4 * c4 + e, s + y);
+                  }
+              });
     }
     __syncthreads();
 }
@@ -204,7 +290,7 @@ template <typename T> __device__ void b_decrease(const BG<T> &g, int u, int v, T
 // Edge increase (u, v): w_old -> w (w may be missing: a deletion).  Returns
 // false on the pass cap.
 template <typename T>
-__device__ bool b_increase(const BG<T> &g, int u, int v, T w_old, T w, int span, uint32_t *mask, int words, T *sx,
+__device__ __noinline__ bool b_increase(const BG<T> &g, int u, int v, T w_old, T w, int span, uint32_t *mask, int words, T *sx,
                            T *sy, int32_t *rows, int *nrows_s) {
     using M = MinPlus<T>;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -226,13 +312,7 @@ __device__ bool b_increase(const BG<T> &g, int u, int v, T w_old, T w, int span,
         if (!M::finite(xi) || !g.alive[i]) continue;
         const T s = M::add(xi, w_old);
         if (!M::tight(s, __ldcg(&g.dt(v, i)))) continue;
-        bool any = false;
-        for (int j = lane; j < span; j += 32) {
-            const bool hit = j != i && M::slack_tight(M::slack(s + sy[j], __ldcg(&g.d(i, j))));
-            const unsigned b = __ballot_sync(0xffffffffu, hit);
-            if (lane == 0 && b) mask[(int64_t)i * words + (j >> 5)] = b;
-            any |= b != 0u;
-        }
+        const bool any = b_detect_row(g, i, s, sy, span, mask + (int64_t)i * words);
         if (lane == 0 && any) rows[atomicAdd(nrows_s, 1)] = i;
     }
     __syncthreads();
@@ -255,7 +335,7 @@ __device__ bool b_increase(const BG<T> &g, int u, int v, T w_old, T w, int span,
 
 // Removal of node k.  Returns false on the pass cap.
 template <typename T>
-__device__ bool b_remove(const BG<T> &g, int k, int span, uint32_t *mask, int words, T *sx, T *sy, int32_t *rows,
+__device__ __noinline__ bool b_remove(const BG<T> &g, int k, int span, uint32_t *mask, int words, T *sx, T *sy, int32_t *rows,
                          int *nrows_s) {
     using M = MinPlus<T>;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -268,13 +348,7 @@ __device__ bool b_remove(const BG<T> &g, int k, int span, uint32_t *mask, int wo
     for (int i = wid; i < span; i += nw) {
         const T xi = sx[i];
         if (i == k || !M::finite(xi) || !g.alive[i]) continue;
-        bool any = false;
-        for (int j = lane; j < span; j += 32) {
-            const bool hit = j != i && M::slack_tight(M::slack(xi + sy[j], __ldcg(&g.d(i, j))));
-            const unsigned b = __ballot_sync(0xffffffffu, hit);
-            if (lane == 0 && b) mask[(int64_t)i * words + (j >> 5)] = b;
-            any |= b != 0u;
-        }
+        const bool any = b_detect_row(g, i, xi, sy, span, mask + (int64_t)i * words);
         if (lane == 0 && any) rows[atomicAdd(nrows_s, 1)] = i;
     }
     __syncthreads();
@@ -302,7 +376,7 @@ __device__ bool b_remove(const BG<T> &g, int k, int span, uint32_t *mask, int wo
     return b_relax(g, mask, words, span, rows, nrows);
 }
 
-template <typename T> __global__ void __launch_bounds__(256) k_batch(BatchHeader *hdr) {
+template <typename T> __global__ void __launch_bounds__(256, 3) k_batch(BatchHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int gi_s, nrows_s;
     const T *vecs = reinterpret_cast<const T *>(hdr->vecs);
@@ -316,13 +390,15 @@ template <typename T> __global__ void __launch_bounds__(256) k_batch(BatchHeader
         BG<T> g{reinterpret_cast<T *>(bg.D), reinterpret_cast<T *>(bg.DT), reinterpret_cast<T *>(bg.W), bg.alive, bg.ld};
         T *s0 = reinterpret_cast<T *>(smem_raw);
         T *s1 = s0 + hdr->max_span;
-        int32_t *srows = reinterpret_cast<int32_t *>(s1 + hdr->max_span);
+        T *s2 = s1 + hdr->max_span;
+        T *s3 = s2 + hdr->max_span;
+        int32_t *srows = reinterpret_cast<int32_t *>(s3 + hdr->max_span);
         int err = 0;
         for (int q = bg.first; q < bg.first + bg.count; ++q) {
             const BatchOp op = hdr->ops[q];
             bool ok = true;
             if (op.op == BOP_ADD) {
-                b_add<T>(g, op.a, op.span, vecs + op.vec, vecs + op.vec + op.span, s0, s1);
+                b_add<T>(g, op.a, op.span, vecs + op.vec, vecs + op.vec + op.span, s0, s1, s2, s3);
             } else if (op.op == BOP_DECREASE) {
                 b_decrease<T>(g, op.a, op.b, bits_as<T>(op.w_bits), op.span, s0, s1);
             } else if (op.op == BOP_INCREASE) {
@@ -333,7 +409,13 @@ template <typename T> __global__ void __launch_bounds__(256) k_batch(BatchHeader
             }
             if (!ok) err |= ERR_PASSES;
         }
-        if (threadIdx.x == 0) bg.status = err;
+        if (threadIdx.x == 0) {
+            bg.status = err;
+            if (hdr->done) {
+                __threadfence_system();   // the graph's results are written before its flag
+                hdr->done[gi] = 1 + err;
+            }
+        }
         __syncthreads();
     }
 }

@@ -9,7 +9,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
+#include <deque>
+#include <thread>
 #include <limits>
 #include <new>
 #include <map>
@@ -149,8 +152,12 @@ void hook_post(void *ctx, const char *name) {
     }
 }
 
+// The CUDA error behind the last APSP_E_CUDA / APSP_E_NOMEM of this thread.
+thread_local int g_last_cuda_error = 0;
+
 apsp_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return APSP_OK;
+    g_last_cuda_error = (int)e;
     if (e == cudaErrorMemoryAllocation) return APSP_E_NOMEM;
     return APSP_E_CUDA;
 }
@@ -562,6 +569,11 @@ extern "C" {
 
 const char *apsp_version(void) { return "0.1.0"; }
 
+int32_t apsp_last_cuda_error(const char **name) {
+    if (name) *name = cudaGetErrorName((cudaError_t)g_last_cuda_error);
+    return g_last_cuda_error;
+}
+
 const char *apsp_status_string(apsp_status s) {
     switch (s) {
     case APSP_OK: return "ok";
@@ -822,6 +834,11 @@ apsp_status apsp_profile_reset(apsp_graph *g) {
 struct apsp_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int32_t *h_done = nullptr;    // mapped completion flags, one per graph of the last launch
+    int32_t *d_done = nullptr;
+    int done_cap = 0;
+    size_t o_tab = 0;             // where the graph table sits in the last upload
+    int n_graphs = 0;
     char *h_blob = nullptr;   // pinned staging of the upload
     size_t h_cap = 0;
     char *d_blob = nullptr;
@@ -857,9 +874,11 @@ template <typename T> int32_t bits_of(T v) {
     return b;
 }
 
+// Validates, resolves and launches the batch on b->stream without waiting;
+// per-graph completion flags go to b->h_done when `flags` is set.
 template <typename T>
-apsp_status batch_impl(apsp_batch *b, apsp_graph *const *graphs, int n_graphs, const apsp_batch_item *items, int count,
-                       int32_t *new_ids) {
+apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs, const apsp_batch_item *items,
+                         int count, int32_t *new_ids, bool flags) {
     using apsp::BatchGraph;
     using apsp::BatchHeader;
     using apsp::BatchOp;
@@ -1031,13 +1050,27 @@ apsp_status batch_impl(apsp_batch *b, apsp_graph *const *graphs, int n_graphs, c
     hdr.n_graphs = n_graphs;
     hdr.max_span = max_span;
     hdr.queue = 0;
+    hdr.done = nullptr;
+    if (flags) {
+        if (n_graphs > b->done_cap) {
+            if (b->h_done) cudaFreeHost(b->h_done);
+            b->h_done = nullptr;
+            b->done_cap = 0;
+            if (cudaHostAlloc(&b->h_done, (size_t)n_graphs * sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess)
+                return APSP_E_NOMEM;
+            if (cudaHostGetDevicePointer((void **)&b->d_done, b->h_done, 0) != cudaSuccess) return APSP_E_CUDA;
+            b->done_cap = n_graphs;
+        }
+        std::memset(b->h_done, 0, (size_t)n_graphs * sizeof(int32_t));
+        hdr.done = b->d_done;
+    }
     std::memcpy(b->h_blob + o_hdr, &hdr, sizeof(hdr));
     std::memcpy(b->h_blob + o_tab, table.data(), table.size() * sizeof(BatchGraph));
     if (!ops.empty()) std::memcpy(b->h_blob + o_ops, ops.data(), ops.size() * sizeof(BatchOp));
     if (!vecs.empty()) std::memcpy(b->h_blob + o_vec, vecs.data(), vecs.size() * sizeof(T));
     cudaError_t e = cudaMemcpyAsync(b->d_blob, b->h_blob, total, cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const size_t smem = (size_t)max_span * (2 * sizeof(T) + sizeof(int32_t));
+    const size_t smem = (size_t)max_span * (4 * sizeof(T) + sizeof(int32_t));
     int per_sm = 0, dev = 0, sms = 1;
     if ((e = apsp::batch_occupancy<T>(smem, &per_sm)) != cudaSuccess) return cuda_status(e);
     cudaGetDevice(&dev);
@@ -1048,12 +1081,27 @@ apsp_status batch_impl(apsp_batch *b, apsp_graph *const *graphs, int n_graphs, c
     // statuses back (the graph table is re-read after the kernel)
     e = cudaMemcpyAsync(b->h_blob + o_tab, b->d_blob + o_tab, table.size() * sizeof(BatchGraph), cudaMemcpyDeviceToHost,
                         b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const BatchGraph *done = reinterpret_cast<const BatchGraph *>(b->h_blob + o_tab);
-    for (int gi = 0; gi < n_graphs; ++gi)
+    b->o_tab = o_tab;
+    b->n_graphs = n_graphs;
+    return APSP_OK;
+}
+
+// Waits for the last launch and returns its status.
+apsp_status batch_finish(apsp_batch *b) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const apsp::BatchGraph *done = reinterpret_cast<const apsp::BatchGraph *>(b->h_blob + b->o_tab);
+    for (int gi = 0; gi < b->n_graphs; ++gi)
         if (done[gi].status) return APSP_E_TIMEOUT;
     return APSP_OK;
+}
+
+template <typename T>
+apsp_status batch_impl(apsp_batch *b, apsp_graph *const *graphs, int n_graphs, const apsp_batch_item *items, int count,
+                       int32_t *new_ids) {
+    apsp_status s = batch_launch<T>(b, graphs, n_graphs, items, count, new_ids, false);
+    return s != APSP_OK ? s : batch_finish(b);
 }
 
 }  // namespace
@@ -1083,6 +1131,7 @@ apsp_status apsp_batch_destroy(apsp_batch *b) {
     if (b->h_blob) cudaFreeHost(b->h_blob);
     if (b->d_blob) cudaFree(b->d_blob);
     if (b->d_mask) cudaFree(b->d_mask);
+    if (b->h_done) cudaFreeHost(b->h_done);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return APSP_OK;
@@ -1106,3 +1155,234 @@ apsp_status apsp_batch_run(apsp_batch *b, apsp_graph *const *graphs, int32_t n_g
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving loop (apsp_serve): real-time replay of a request trace with
+// wave-level continuous batching.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Clock {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+// One graph's share of a wave.
+struct Segment {
+    int graph;
+    std::vector<int> reqs;   // request indices, in arrival order
+    bool small = false;
+    int small_index = -1;    // index among the wave's batched graphs
+    int query = -1;          // the closing query, if any
+    cudaEvent_t ev = nullptr;
+    bool done = false;
+};
+
+template <typename T>
+apsp_status serve_impl(apsp_graph *const *graphs, int n_graphs, const apsp_request *reqs, int count,
+                       const apsp_serve_config &cfg, apsp_request_result *res) {
+    std::vector<bool> small(n_graphs);
+    std::vector<double> bytes(n_graphs);
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        apsp_graph *g = graphs[gi];
+        small[gi] = cfg.small_max_slots > 0 && g->cap <= cfg.small_max_slots && !g->undirected && g->DT &&
+                    g->cap <= APSP_BATCH_MAX_SLOTS;
+        bytes[gi] = (double)g->ld * g->ld * g->esz * (g->undirected ? 2 : 3);
+    }
+    apsp_batch *b = nullptr;
+    apsp_status st = apsp_batch_create(&b, nullptr);
+    if (st != APSP_OK) return st;
+    T *qbuf = nullptr;   // pinned query results
+    if (cudaMallocHost(&qbuf, std::max(1, count) * sizeof(T)) != cudaSuccess) {
+        apsp_batch_destroy(b);
+        return APSP_E_NOMEM;
+    }
+    for (int q = 0; q < count; ++q) {
+        res[q] = apsp_request_result{};
+        res[q].new_id = -1;
+        res[q].wave = -1;
+    }
+    std::vector<std::deque<int>> pend(n_graphs);
+    Clock clk;
+    int next = 0, finished = 0, wave = 0, rr = 0;
+    cudaEvent_t small_q_ev = nullptr;
+    cudaEventCreateWithFlags(&small_q_ev, cudaEventDisableTiming);
+    while (finished < count) {
+        double now = clk.now();
+        while (next < count && reqs[next].arrival_s <= now) pend[reqs[next].item.graph].push_back(next++);
+        bool any = false;
+        for (auto &p : pend) any |= !p.empty();
+        if (!any) {
+            // idle until the next arrival (sleep for long gaps, then spin)
+            const double gap = reqs[next].arrival_s - now;
+            if (gap > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(gap - 1e-4));
+            continue;
+        }
+        // ---- form the wave: round-robin over graphs, within the budget
+        std::vector<Segment> segs;
+        double used = 0;
+        int taken = 0;
+        for (int k = 0; k < n_graphs; ++k) {
+            const int gi = (rr + k) % n_graphs;
+            if (pend[gi].empty()) continue;
+            if (cfg.hbm_budget_bytes > 0 && !segs.empty() && used + bytes[gi] > cfg.hbm_budget_bytes) continue;
+            if (cfg.max_wave_requests > 0 && taken >= cfg.max_wave_requests) break;
+            Segment s;
+            s.graph = gi;
+            s.small = small[gi];
+            while (!pend[gi].empty()) {
+                if (cfg.max_wave_requests > 0 && taken >= cfg.max_wave_requests) break;
+                const int q = pend[gi].front();
+                pend[gi].pop_front();
+                s.reqs.push_back(q);
+                ++taken;
+                if (reqs[q].item.op == APSP_BATCH_QUERY) {
+                    s.query = q;
+                    break;
+                }
+            }
+            used += bytes[gi];
+            segs.push_back(std::move(s));
+        }
+        rr = (rr + 1) % n_graphs;
+        const double admit = clk.now();
+        for (auto &s : segs)
+            for (int q : s.reqs) {
+                res[q].admit_s = admit;
+                res[q].wave = wave;
+            }
+        // ---- batched graphs: one persistent launch
+        std::vector<apsp_graph *> bgraphs;
+        std::vector<apsp_batch_item> bitems;
+        std::vector<int> bmap;   // batch item -> request
+        for (auto &s : segs) {
+            if (!s.small) continue;
+            s.small_index = (int)bgraphs.size();
+            bgraphs.push_back(graphs[s.graph]);
+            for (int q : s.reqs) {
+                if (reqs[q].item.op == APSP_BATCH_QUERY) continue;
+                apsp_batch_item it = reqs[q].item;
+                it.graph = s.small_index;
+                bitems.push_back(it);
+                bmap.push_back(q);
+            }
+        }
+        apsp_status bst = APSP_OK;
+        std::vector<int32_t> bids(bitems.size(), -1);
+        if (!bgraphs.empty()) {
+            bst = batch_launch<T>(b, bgraphs.data(), (int)bgraphs.size(), bitems.data(), (int)bitems.size(),
+                                  bids.data(), true);
+            bool any_q = false;
+            for (auto &s : segs)
+                if (s.small && s.query >= 0 && bst == APSP_OK) {
+                    const apsp_batch_item &it = reqs[s.query].item;
+                    apsp_graph *g = graphs[s.graph];
+                    cudaMemcpyAsync(qbuf + s.query, (T *)g->D + (int64_t)it.u * g->ld + it.v, sizeof(T),
+                                    cudaMemcpyDeviceToHost, b->stream);
+                    any_q = true;
+                }
+            if (any_q) cudaEventRecord(small_q_ev, b->stream);
+        }
+        // ---- other graphs: the one-call-per-update path on their own streams
+        for (auto &s : segs) {
+            if (s.small) continue;
+            apsp_graph *g = graphs[s.graph];
+            for (int q : s.reqs) {
+                const apsp_batch_item &it = reqs[q].item;
+                apsp_status r = APSP_OK;
+                if (it.op == APSP_BATCH_ADD) {
+                    int32_t id = -1;
+                    r = apsp_add_node(g, it.in_w, it.out_w, &id);
+                    res[q].new_id = id;
+                } else if (it.op == APSP_BATCH_REMOVE) {
+                    r = apsp_remove_node(g, it.u);
+                } else if (it.op == APSP_BATCH_EDGE) {
+                    T w;
+                    r = batch_weight<T>(it.w, &w);
+                    if (r == APSP_OK) r = apsp_update_edge(g, it.u, it.v, &w);
+                } else {
+                    if (it.u < 0 || it.v < 0 || it.u >= g->cap || it.v >= g->cap) {
+                        r = APSP_E_NODE;
+                    } else {
+                        settle_fetch<T>(g);
+                        cudaMemcpyAsync(qbuf + q, (T *)g->D + (int64_t)it.u * g->ld + it.v, sizeof(T),
+                                        cudaMemcpyDeviceToHost, g->stream);
+                    }
+                }
+                res[q].status = r;
+            }
+            cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+            cudaEventRecord(s.ev, g->stream);
+        }
+        // ---- completions
+        int left = (int)segs.size();
+        bool small_q_done = false;
+        while (left > 0) {
+            for (auto &s : segs) {
+                if (s.done) continue;
+                bool ok = false;
+                if (s.small) {
+                    if (bst != APSP_OK) {
+                        ok = true;
+                    } else {
+                        const int flag = ((volatile int32_t *)b->h_done)[s.small_index];
+                        if (flag != 0 && s.query >= 0 && !small_q_done)
+                            small_q_done = cudaEventQuery(small_q_ev) == cudaSuccess;
+                        ok = flag != 0 && (s.query < 0 || small_q_done);
+                        if (flag > 1) bst = APSP_E_TIMEOUT;
+                    }
+                } else {
+                    ok = cudaEventQuery(s.ev) == cudaSuccess;
+                }
+                if (!ok) continue;
+                const double t = clk.now();
+                for (int q : s.reqs) {
+                    res[q].done_s = t;
+                    if (s.small) res[q].status = bst;
+                    if (reqs[q].item.op == APSP_BATCH_QUERY && res[q].status == APSP_OK) res[q].dist = (double)qbuf[q];
+                    ++finished;
+                }
+                s.done = true;
+                --left;
+            }
+        }
+        if (!bgraphs.empty()) {
+            const apsp_status fst = batch_finish(b);
+            for (size_t k = 0; k < bmap.size(); ++k) {
+                if (fst != APSP_OK) res[bmap[k]].status = fst;
+                if (reqs[bmap[k]].item.op == APSP_BATCH_ADD) res[bmap[k]].new_id = bids[k];
+            }
+        }
+        for (auto &s : segs)
+            if (s.ev) {
+                cudaEventSynchronize(s.ev);
+                cudaEventDestroy(s.ev);
+            }
+        ++wave;
+    }
+    cudaEventDestroy(small_q_ev);
+    cudaFreeHost(qbuf);
+    apsp_batch_destroy(b);
+    return APSP_OK;
+}
+
+}  // namespace
+
+extern "C" apsp_status apsp_serve(apsp_graph *const *graphs, int32_t n_graphs, const apsp_request *reqs,
+                                  int32_t count, const apsp_serve_config *cfg, apsp_request_result *results) {
+    if (!graphs || n_graphs <= 0 || count < 0 || (count > 0 && (!reqs || !results)) || !cfg) return APSP_E_ARG;
+    const int dtype = graphs[0] ? graphs[0]->dtype : -1;
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        if (!graphs[gi] || graphs[gi]->dtype != dtype) return APSP_E_ARG;
+        for (int gj = 0; gj < gi; ++gj)
+            if (graphs[gj] == graphs[gi]) return APSP_E_ARG;
+    }
+    for (int q = 0; q < count; ++q) {
+        const apsp_request &r = reqs[q];
+        if (r.item.graph < 0 || r.item.graph >= n_graphs || r.item.op < 0 || r.item.op > APSP_BATCH_QUERY) return APSP_E_ARG;
+        if (!(r.arrival_s >= 0) || (q > 0 && r.arrival_s < reqs[q - 1].arrival_s)) return APSP_E_ARG;
+    }
+    if (dtype == APSP_F32) return serve_impl<float>(graphs, n_graphs, reqs, count, *cfg, results);
+    return serve_impl<int32_t>(graphs, n_graphs, reqs, count, *cfg, results);
+}

@@ -3,6 +3,8 @@
 // declarations in launch.h.
 #pragma once
 
+#include <mutex>
+
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -92,6 +94,36 @@ static cudaError_t run_detect(const LaunchCtx &c, const Dev<T> &d, int kind, int
     return run_detect_t<T, false>(c, d, kind, a, w_old, w_new, name);
 }
 
+// Cooperative grids of different graphs (streams) must not be resident at
+// the same time: each needs all its CTAs on the device at once, so two of
+// them sharing the SMs could each wait for the other's.  Every cooperative
+// launch of the process waits for the previous one (an event chain on the
+// device; other kernels stay concurrent).
+struct CoopChain {
+    std::mutex mu;
+    cudaEvent_t last[64] = {};
+};
+inline CoopChain &coop_chain() {
+    static CoopChain c;
+    return c;
+}
+
+template <typename F> static cudaError_t coop_launch(cudaStream_t stream, F &&launch_fn) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    CoopChain &cc = coop_chain();
+    std::lock_guard<std::mutex> lock(cc.mu);
+    if (!cc.last[dev]) {
+        if ((e = cudaEventCreateWithFlags(&cc.last[dev], cudaEventDisableTiming)) != cudaSuccess) return e;
+    } else if ((e = cudaStreamWaitEvent(stream, cc.last[dev], 0)) != cudaSuccess) {
+        return e;
+    }
+    if ((e = launch_fn()) != cudaSuccess) return e;
+    return cudaEventRecord(cc.last[dev], stream);
+}
+
 // Both repair kernels are launched; the one whose path the device-side
 // decision did not choose returns at once.
 template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d, const RepairCfg &cfg) {
@@ -100,12 +132,17 @@ template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d
     void *args[] = {(void *)&dd, (void *)&cc};
     cudaError_t le = cudaSuccess;
     cudaError_t e = launch(c, "repair_warm", [&] {
-        le = cudaLaunchCooperativeKernel((void *)k_repair_warm<T>, dim3(c.warm_grid), dim3(256), args, 0, c.stream);
+        le = coop_launch(c.stream, [&] {
+            return cudaLaunchCooperativeKernel((void *)k_repair_warm<T>, dim3(c.warm_grid), dim3(256), args, 0, c.stream);
+        });
     });
     if (le != cudaSuccess) return le;
     if (e != cudaSuccess) return e;
     e = launch(c, "repair_cold", [&] {
-        le = cudaLaunchCooperativeKernel((void *)k_repair_cold<T>, dim3(c.repair_grid), dim3(256), args, c.repair_smem, c.stream);
+        le = coop_launch(c.stream, [&] {
+            return cudaLaunchCooperativeKernel((void *)k_repair_cold<T>, dim3(c.repair_grid), dim3(256), args,
+                                               c.repair_smem, c.stream);
+        });
     });
     return le != cudaSuccess ? le : e;
 }
@@ -126,13 +163,28 @@ cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_
     return run_repair<T>(c, d, cfg);
 }
 
+// The dynamic shared memory limit is a per-function setting shared by every
+// graph of the process, so it is raised once to the device's maximum (graphs
+// of different sizes then never lower it under each other); occupancy is
+// computed from each launch's actual bytes.
+template <typename F> static cudaError_t allow_max_smem(F *kernel) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)   // the opt-in limit covers static and dynamic shared memory together
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 // Occupancy-derived launch shapes for a graph of leading dimension ld.
 template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int undirected) {
     cudaError_t e;
     size_t row = (size_t)ld * sizeof(T);
     size_t fw = sizeof(FwSmem<T>) > sizeof(FwDiagSmem<T>) ? sizeof(FwSmem<T>) : sizeof(FwDiagSmem<T>);
     c.repair_smem = std::max<size_t>(fw, 32 * 33 * sizeof(T));
-    if ((e = cudaFuncSetAttribute(k_repair_cold<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.repair_smem)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_repair_cold<T>)) != cudaSuccess) return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_repair_cold<T>, 256, c.repair_smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -141,18 +193,18 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&warm_sm, k_repair_warm<T>, 256, 0)) != cudaSuccess) return e;
     if (warm_sm < 1) return cudaErrorInvalidConfiguration;
     c.warm_grid = warm_sm * c.num_sms;
-    if ((e = cudaFuncSetAttribute(k_det_scan<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_det_scan<T, false>)) != cudaSuccess) return e;
     int det_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_det_scan<T, false>, 256, row)) != cudaSuccess) return e;
     c.detect_grid = std::max(1, det_sm) * c.num_sms;
-    if ((e = cudaFuncSetAttribute(k_det_scan<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * row))) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_det_scan<T, true>)) != cudaSuccess) return e;
     int det2_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det2_sm, k_det_scan<T, true>, 256, 2 * row)) != cudaSuccess) return e;
     c.detect2_grid = std::max(1, det2_sm) * c.num_sms;
     c.detunit_grid = 4 * c.num_sms;
     c.detalloc_grid = (int)((ld + 255) / 256);   // a lane per row: 256 rows a CTA
     size_t rel = (size_t)ld * sizeof(int32_t);
-    if ((e = cudaFuncSetAttribute(k_insert_relax<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rel)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_insert_relax<T>)) != cudaSuccess) return e;
     int rel_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rel_sm, k_insert_relax<T>, 256, rel)) != cudaSuccess) return e;
     c.relax_grid = std::max(1, rel_sm) * c.num_sms;
@@ -166,7 +218,7 @@ template <typename T> cudaError_t run_batch(cudaStream_t s, BatchHeader *hdr, in
 }
 
 template <typename T> cudaError_t batch_occupancy(size_t smem, int *per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(k_batch<T>);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T>, 256, smem);
 }

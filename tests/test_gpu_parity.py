@@ -396,3 +396,29 @@ def test_chunked_repair_n2048_full_check(fp):
         apply(g, mir, up)
     assert_same(g, mir, "after 24 updates")
     g.close()
+
+
+def test_graphs_of_different_sizes_coexist():
+    """A smaller graph created later must not restrict the launches of a
+    larger one (per-function launch limits are process-wide)."""
+    import synth
+    from oracle import apsp as O
+    from paper_2412_15122_gb300 import Graph, build
+    build.build()
+    Wb = synth.complete_digraph_i32(700, 1, 1000, 71)
+    big = Graph(Wb, 720)
+    small = Graph(synth.complete_digraph_i32(40, 1, 1000, 72), 48)
+    big.remove_node(5)
+    big.update_edge(3, 9, 1)
+    big.update_edge(10, 11, 4000)
+    p = big.add_node(synth.uniform_int(73, 1, 720, 1, 1000).astype(np.int32),
+                     synth.uniform_int(73, 2, 720, 1, 1000).astype(np.int32))
+    small.remove_node(3)
+    m = big.info()["n_slots"]
+    alive = big.alive().astype(bool)
+    live = np.flatnonzero(alive)
+    ref = O.to_i32(O.fw(big.W()[:m, :m], alive[:m]))
+    np.testing.assert_array_equal(big.D()[np.ix_(live, live)], ref[np.ix_(live, live)])
+    assert alive[p]
+    big.close()
+    small.close()

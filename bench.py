@@ -527,6 +527,150 @@ def run_batch_study(args):
     print(json.dumps(out))
 
 
+class _ServeState:
+    """Host view of one resident graph for generating valid requests: live
+    slots (lowest-free-slot rule for adds) and the current edge weights."""
+
+    def __init__(self, W, cap):
+        self.n0, self.cap = W.shape[0], cap
+        self.W0 = W
+        self.alive = np.zeros(cap, bool)
+        self.alive[:self.n0] = True
+        self.mods = {}
+        self.added = {}   # slot -> (in_w, out_w) of a node added later
+
+    def weight(self, u, v):
+        if (u, v) in self.mods:
+            return self.mods[(u, v)]
+        if v in self.added:
+            return int(self.added[v][0][u])
+        if u in self.added:
+            return int(self.added[u][1][v])
+        return int(self.W0[u, v])
+
+
+def _serve_requests(states, count, seed, stream):
+    """count requests: 70 % edge updates (half halve, half x4), 20 % node
+    add / remove (half each), 10 % distance queries; graph and targets
+    uniform."""
+    pick = synth.uniform_int(seed, stream, count, 0, len(states) - 1)
+    kind = synth.uniform_f64(seed, stream + 1, count)
+    r = synth.u64(seed, stream + 2, 2 * count)
+    reqs = []
+    for q in range(count):
+        gi = int(pick[q])
+        st = states[gi]
+        live = np.flatnonzero(st.alive)
+        a = int(r[2 * q] % np.uint64(len(live)))
+        b = int(r[2 * q + 1] % np.uint64(len(live) - 1))
+        b += b >= a
+        u, v = int(live[a]), int(live[b])
+        k = kind[q]
+        if k < 0.10:
+            reqs.append((gi, "query", u, v))
+            continue
+        if k < 0.20:
+            if len(live) < st.cap:
+                iw = np.full(st.cap, synth.INF_I32, np.int32)
+                ow = np.full(st.cap, synth.INF_I32, np.int32)
+                iw[live] = synth.uniform_int(seed, 100000 + 2 * q + stream, len(live), 1, 10**6)
+                ow[live] = synth.uniform_int(seed, 100001 + 2 * q + stream, len(live), 1, 10**6)
+                p = int(np.flatnonzero(~st.alive)[0])
+                st.alive[p] = True
+                st.added[p] = (iw, ow)
+                for key in [kk for kk in st.mods if p in kk]:
+                    del st.mods[key]
+                reqs.append((gi, "add", iw, ow))
+                continue
+            k = 0.25
+        if k < 0.30:
+            st.alive[u] = False
+            reqs.append((gi, "remove", u))
+        else:
+            w0 = st.weight(u, v)
+            w = w0 // 2 if k < 0.65 else min(w0 * 4, 1 << 26)
+            st.mods[(u, v)] = w
+            reqs.append((gi, "edge", u, v, float(w)))
+    return reqs
+
+
+def run_serve_study(args):
+    """Serving: 64 resident directed complete graphs (16 each of n = 1024,
+    2048, 4096, 8192; int32 U[1, 1e6]); Poisson arrivals swept from 10 % to
+    110 % of the measured capacity; p50 / p99 latency and throughput; a tight
+    HBM budget that forces queuing; and the alone-vs-in-the-mix identity
+    (graphs replayed alone give the same matrices)."""
+    from paper_2412_15122_gb300 import Graph, build
+    from paper_2412_15122_gb300 import apsp as A
+    build.build()
+    sizes = [n for n in (1024, 2048, 4096, 8192) for _ in range(args.serve_per_size)]
+    specs, graphs, states = [], [], []
+    t_gen = time.perf_counter()
+    for k, n in enumerate(sizes):
+        W = synth.complete_digraph_i32(n, 1, 10**6, 500 + k)
+        cap = n + 64
+        specs.append((W, cap))
+        graphs.append(Graph(W, cap))
+        states.append(_ServeState(W, cap))
+    gen_s = time.perf_counter() - t_gen
+    small = 2048 + 64
+    history = [[] for _ in graphs]
+    hs = [g.h for g in graphs]
+
+    def run(reqs, arrivals, budget=0.0):
+        res = A.apsp_serve(hs, reqs, arrivals, hbm_budget_bytes=budget, small_max_slots=small)
+        for q, it in enumerate(reqs):
+            history[it[0]].append(it)
+        lat = res["done_s"] - np.asarray(arrivals)
+        span = float(res["done_s"].max() - np.asarray(arrivals).min())
+        return {"requests": len(reqs), "ok": int((res["status"] == 0).sum()),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "throughput_per_s": len(reqs) / span, "waves": int(res["wave"].max() + 1)}, res
+
+    N = args.serve_requests
+    stream = 10
+    # capacity: everything arrives at once
+    reqs = _serve_requests(states, N, 5, stream)
+    stream += 10
+    cal, _ = run(reqs, np.zeros(len(reqs)))
+    C = cal["throughput_per_s"]
+    sweep = {}
+    for frac in (0.1, 0.5, 0.9, 1.1):
+        reqs = _serve_requests(states, N, 5, stream)
+        stream += 10
+        gaps = -np.log1p(-synth.uniform_f64(5, stream + 7, N)) / (frac * C)
+        sweep[f"{frac:.1f}"], _ = run(reqs, np.cumsum(gaps))
+    # tight budget: about four of the smallest graphs per wave
+    reqs = _serve_requests(states, N, 5, stream)
+    stream += 10
+    gaps = -np.log1p(-synth.uniform_f64(5, stream + 7, N)) / (0.5 * C)
+    budget = 4 * 3 * (1024 + 128) ** 2 * 4.0
+    tight, _ = run(reqs, np.cumsum(gaps), budget)
+    # alone vs in the mix: the n=1024 graphs replayed alone
+    same = True
+    for gi in range(args.serve_per_size):
+        W, cap = specs[gi]
+        g = Graph(W, cap)
+        for it in history[gi]:
+            if it[1] == "add":
+                g.add_node(it[2], it[3])
+            elif it[1] == "remove":
+                g.remove_node(it[2])
+            elif it[1] == "edge":
+                g.update_edge(it[2], it[3], it[4])
+        same &= bool(np.array_equal(g.D(), graphs[gi].D()))
+        g.close()
+    for g in graphs:
+        g.close()
+    print(json.dumps({
+        "study": "serving", "graphs": len(sizes), "sizes": [1024, 2048, 4096, 8192], "per_size": args.serve_per_size,
+        "mix": "70% edge updates (half halve, half x4), 20% node add/remove (half each), 10% queries; uniform graph and targets",
+        "batched_graphs": f"capacity <= {small} (n = 1024, 2048) in the persistent batched kernel, larger via one call per update",
+        "capacity_requests_per_s": C, "calibration": cal, "poisson_sweep_fraction_of_capacity": sweep,
+        "tight_budget": {"budget_bytes": budget, "at_fraction": 0.5, **tight},
+        "alone_vs_mix_identical_n1024": same, "setup_seconds": gen_s}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,7 +684,9 @@ def main():
     ap.add_argument("--case", choices=["removals", "inserts"],
                     help="run a small fixed case of the workload (for profiler captures) and exit")
     ap.add_argument("--study-graphs", type=int, default=512)
-    ap.add_argument("--study", choices=["dispatch", "batch"],
+    ap.add_argument("--serve-per-size", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--study", choices=["dispatch", "batch", "serve"],
                     help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
                          "always-warm and always-cold on n=16384 undirected Euclidean updates")
     ap.add_argument("--study-updates", type=int, default=100)
@@ -554,6 +700,8 @@ def main():
         return run_dispatch_study(args)
     if args.study == "batch":
         return run_batch_study(args)
+    if args.study == "serve":
+        return run_serve_study(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -24,6 +24,10 @@ What each function follows:
 * ``modify_edge_alg6``        Algorithm 6.
 * ``apsp_after``              the plain definition: the APSP matrix of the
                               updated graph, by ``fw``.
+* ``warm_shortest_path``      Algorithm 7 (candidate_node_list, small matrix,
+                              Dijkstra on it; Theorem al_correct).
+* ``all_shortest_paths_alg8`` Algorithm 8 on Algorithm 7's small graph.
+* ``need_update_list_alg12``  Algorithm 12 (Theorem theo_algo12).
 """
 from __future__ import annotations
 
@@ -415,3 +419,175 @@ def itertools_paths_min(W: np.ndarray) -> np.ndarray:
                     if ok and L < D[s, t]:
                         D[s, t] = L
     return D
+
+
+# ---------------------------------------------------------------------------
+# Warm-start path queries: Algorithm 7, Algorithm 8, Theorem al_correct
+# (Section 4); exact removal list: Algorithm 12, Theorem theo_algo12
+# ---------------------------------------------------------------------------
+
+#: Relative slack of the float candidate test (the same reading as the float
+#: tightness test): extra candidates only enlarge the small graph; a missed
+#: one could drop every shortest path from it.
+FLOAT_SLACK = 2.0 ** -16
+
+
+def _on_some_shortest_path(M: np.ndarray, i: int, j: int, t: int) -> bool:
+    """Algorithm 7's candidate test: t is kept unless SPD(i, j) < SPD(i, t) + SPD(t, j)."""
+    miss = missing(M)
+    via = _add(M[i, t], M[t, j], miss)
+    if via == miss:
+        return False
+    if is_float(M):
+        return bool(via <= M[i, j] * (1.0 + FLOAT_SLACK))
+    return not (M[i, j] < via)
+
+
+def candidate_node_list(M: np.ndarray, alive: np.ndarray, i: int, j: int) -> List[int]:
+    """Algorithm 7's candidate_node_list: i, then every other live node t
+    (in increasing slot order) that is on some shortest i -> j path, then j."""
+    live = [int(t) for t in np.flatnonzero(np.asarray(alive, dtype=bool))]
+    cand = [i]
+    for t in live:
+        if t == i or t == j:
+            continue
+        if _on_some_shortest_path(M, i, j, t):
+            cand.append(t)
+    cand.append(j)
+    return cand
+
+
+def small_dijkstra(A: np.ndarray, s: int):
+    """Dense Dijkstra on a small matrix A (A[a][b] = weight a -> b, missing =
+    INF / inf) from node s.  Returns (dist, pred); pred[s] = -1 and -1 for
+    unreachable nodes.  The next node is the unvisited one of least distance,
+    the lowest index on a tie; a node's predecessor changes only on a strict
+    improvement."""
+    K = A.shape[0]
+    miss = missing(A)
+    dist = np.full(K, miss, dtype=A.dtype)
+    pred = np.full(K, -1, dtype=np.int64)
+    done = np.zeros(K, dtype=bool)
+    dist[s] = 0
+    for _ in range(K):
+        best, a = miss, -1
+        for b in range(K):
+            if not done[b] and dist[b] < best:
+                best, a = dist[b], b
+        if a < 0:
+            break
+        done[a] = True
+        for b in range(K):
+            if done[b] or A[a, b] == miss:
+                continue
+            nd = dist[a] + A[a, b]
+            if nd < dist[b]:
+                dist[b] = nd
+                pred[b] = a
+    return dist, pred
+
+
+def _tree_path(pred: np.ndarray, s: int, t: int) -> List[int]:
+    out = [t]
+    while out[-1] != s:
+        p = int(pred[out[-1]])
+        if p < 0:
+            return []
+        out.append(p)
+    return out[::-1]
+
+
+def warm_shortest_path(M: np.ndarray, W: np.ndarray, alive: np.ndarray, i: int, j: int) -> List[int]:
+    """Algorithm 7, warm_cal_shortest_path(M_G, A_G, i, j).
+
+    In the algorithm's order: [i] when i == j; the candidate_node_list (i, the
+    nodes t with not SPD(i, j) < SPD(i, t) + SPD(t, j), then j); the small
+    matrix of the adjacency among the candidates; Dijkstra from small node 0
+    to small node K - 1; the path translated back to slot ids.  Theorem
+    al_correct: the small graph holds every shortest i -> j path.  An
+    unreachable pair (the paper is silent) gives the empty list.
+    """
+    if i == j:
+        return [i]
+    if M[i, j] == missing(M):
+        return []
+    cand = candidate_node_list(M, alive, i, j)
+    E = exact(W, alive)
+    small = E[np.ix_(cand, cand)]
+    _, pred = small_dijkstra(small, 0)
+    return [cand[a] for a in _tree_path(pred, 0, len(cand) - 1)]
+
+
+def all_shortest_paths_alg8(M: np.ndarray, W: np.ndarray, alive: np.ndarray, i: int, j: int) -> List[List[int]]:
+    """Algorithm 8, warm_cal_all_shortest_paths, on Algorithm 7's small graph.
+
+    One shortest path Psi(i, j) first; then for every candidate t other than
+    i and j, a shortest i -> t path joined to a shortest t -> j path (both on
+    the small graph), appended unless already listed.  A join that visits a
+    node twice (possible only through zero-weight cycles; the paper is
+    silent) is a walk, not a path, and is skipped.  Every listed path is a
+    shortest i -> j path; the list need not hold every one of them.
+    """
+    if i == j:
+        return [[i]]
+    if M[i, j] == missing(M):
+        return []
+    cand = candidate_node_list(M, alive, i, j)
+    E = exact(W, alive)
+    small = E[np.ix_(cand, cand)]
+    K = len(cand)
+    _, pred_i = small_dijkstra(small, 0)
+    _, pred_j = small_dijkstra(np.ascontiguousarray(small.T), K - 1)   # reverse graph: t -> j
+    out = [[cand[a] for a in _tree_path(pred_i, 0, K - 1)]]
+    for t in range(1, K - 1):
+        first = _tree_path(pred_i, 0, t)
+        second = _tree_path(pred_j, K - 1, t)[::-1]
+        if not first or not second:
+            continue
+        p = [cand[a] for a in first + second[1:]]
+        if len(set(p)) != len(p):      # zero-weight cycles can make the join a walk, not a path
+            continue
+        if p not in out:
+            out.append(p)
+    return out
+
+
+def path_length(W: np.ndarray, path: Sequence[int]):
+    """Sum of the edge weights along `path` in exact arithmetic (missing if an edge is missing)."""
+    E = exact(W)
+    miss = missing(E)
+    L = E.dtype.type(0)
+    for a, b in zip(path, path[1:]):
+        if E[a, b] == miss:
+            return miss
+        L = L + E[a, b]
+    return L
+
+
+def need_update_list_alg12(M: np.ndarray, W: np.ndarray, alive: np.ndarray, k: int) -> Dict[int, List[int]]:
+    """Algorithm 12's need_update_list for removing node k.
+
+    For every ordered pair (i, j) of remaining nodes with SPD(i, j) >= SPD(i, k)
+    + SPD(k, j) (Corollary 3's list): the candidate list of Algorithm 7 without
+    k, its small matrix, and Dijkstra from i to j on it (Phi_ij); the pair is
+    listed iff Phi_ij > SPD(i, j).  By Theorem theo_algo12 these are exactly
+    the pairs whose distance grows when k is removed.
+    """
+    alive = np.asarray(alive, dtype=bool)
+    miss = missing(M)
+    E = exact(W, alive)
+    rem = [int(v) for v in np.flatnonzero(alive) if v != k]
+    lst: Dict[int, List[int]] = {}
+    for i in rem:
+        row = []
+        for j in rem:
+            if j == i or M[i, j] == miss:
+                continue
+            if M[i, j] < _add(M[i, k], M[k, j], miss):
+                continue
+            cand = [i] + [t for t in rem if t not in (i, j) and _on_some_shortest_path(M, i, j, t)] + [j]
+            dist, _ = small_dijkstra(E[np.ix_(cand, cand)], 0)
+            if dist[len(cand) - 1] > M[i, j]:
+                row.append(j)
+        lst[i] = row
+    return lst

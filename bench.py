@@ -527,6 +527,77 @@ def run_batch_study(args):
     print(json.dumps(out))
 
 
+def run_path_study(args):
+    """Warm-start path queries (Algorithm 7) on directed complete graphs with
+    int32 weights U[1, 1e6]: uniform random pairs, answered in batches through
+    apsp_query_paths and one at a time through apsp_query_path.  The CPU side
+    times the oracle's Algorithm 7 and its dense Dijkstra per query (the
+    paper's cold comparison) at n = 2048."""
+    import torch
+    from paper_2412_15122_gb300 import Graph, build
+    from paper_2412_15122_gb300 import apsp as A
+    build.build()
+    from oracle import apsp as O
+    hbm, peak_kind = peaks()
+    out = {"study": "path queries", "workload": "directed complete graph, int32 U[1,1e6], uniform pairs",
+           "gpu": {}}
+    nq = args.study_queries
+    for n in (2048, 8192):
+        W = synth.complete_digraph_i32(n, W_LO, W_HI, 20 + n)
+        g = Graph(W, n + 256)
+        g.sync()
+        uv = np.stack([synth.uniform_int(21, n, nq, 0, n - 1), synth.uniform_int(22, n, nq, 0, n - 1)], 1)
+        uv = uv.astype(np.int32)
+        for _ in range(3):
+            g.query_paths(uv, stride=64)
+        A.apsp_profile_enable(g.h, True)
+        A.apsp_profile_reset(g.h)
+        reps = 5
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            _, lens = g.query_paths(uv, stride=64)
+        api_s = (time.perf_counter() - t0) / reps
+        prof = A.apsp_profile_read(g.h)
+        A.apsp_profile_enable(g.h, False)
+        kl, kms = prof.get("path_query", (0, 0.0))
+        kern_s = kms / 1000.0 / max(1, kl)
+        span = g.info()["n_slots"]
+        lat = []
+        for q in range(200):
+            u, v = int(uv[q, 0]), int(uv[q, 1])
+            t1 = time.perf_counter()
+            g.query_path(u, v, 64)
+            lat.append(time.perf_counter() - t1)
+        algo_bytes = 8.0 * span * nq          # row u of D and row v of D^T per query
+        out["gpu"][str(n)] = {
+            "queries": nq, "api_queries_per_s": nq / api_s, "kernel_us_per_batch": kern_s * 1e6,
+            "kernel_queries_per_s": nq / kern_s if kern_s > 0 else None,
+            "kernel_read_gbs": algo_bytes / kern_s / 1e9 if kern_s > 0 else None,
+            "kernel_read_frac_of_peak": (algo_bytes / kern_s / 1e9) / hbm if kern_s > 0 else None,
+            "peak": f"{hbm} GB/s {peak_kind}", "single_query_us_p50": 1e6 * statistics.median(lat),
+            "mean_path_nodes": float(np.mean(lens)), "wide_pass_launches": prof.get("path_query_wide", (0, 0))[0]}
+        g.close()
+        torch.cuda.synchronize()
+    # CPU oracle at n = 2048: Algorithm 7 vs dense Dijkstra per query
+    n = 2048
+    W = synth.complete_digraph_i32(n, W_LO, W_HI, 20 + n)
+    M = O.fw(W)
+    alive = np.ones(n, dtype=bool)
+    uv = np.stack([synth.uniform_int(23, n, 20, 0, n - 1), synth.uniform_int(24, n, 20, 0, n - 1)], 1)
+    t0 = time.perf_counter()
+    for u, v in uv:
+        O.warm_shortest_path(M, W, alive, int(u), int(v))
+    warm = (time.perf_counter() - t0) / len(uv)
+    t0 = time.perf_counter()
+    for u, _ in uv:
+        O.dijkstra_rows(W, [int(u)])
+    cold = (time.perf_counter() - t0) / len(uv)
+    out["cpu_oracle_n2048"] = {"queries": len(uv), "alg7_ms_per_query": warm * 1e3,
+                               "dijkstra_ms_per_query": cold * 1e3, "warm_over_cold": warm / cold,
+                               "note": "oracle code as it stands (numpy / C), not tuned"}
+    print(json.dumps(out))
+
+
 class _ServeState:
     """Host view of one resident graph for generating valid requests: live
     slots (lowest-free-slot rule for adds) and the current edge weights."""
@@ -686,7 +757,8 @@ def main():
     ap.add_argument("--study-graphs", type=int, default=512)
     ap.add_argument("--serve-per-size", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=1000)
-    ap.add_argument("--study", choices=["dispatch", "batch", "serve"],
+    ap.add_argument("--study-queries", type=int, default=4096)
+    ap.add_argument("--study", choices=["dispatch", "batch", "serve", "paths"],
                     help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
                          "always-warm and always-cold on n=16384 undirected Euclidean updates")
     ap.add_argument("--study-updates", type=int, default=100)
@@ -702,6 +774,8 @@ def main():
         return run_batch_study(args)
     if args.study == "serve":
         return run_serve_study(args)
+    if args.study == "paths":
+        return run_path_study(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -187,6 +187,42 @@ apsp_status apsp_query(apsp_graph *g, int32_t u, int32_t v, void *dist_out);
  * (host, count elements).  Waits. */
 apsp_status apsp_query_batch(apsp_graph *g, const int32_t *uv, int32_t count, void *out);
 
+/* ----- path queries (Section 4) -----------------------------------------
+ * Algorithm 7 (warm-start shortest path): from the resident APSP matrix, the
+ * candidate list of the pair -- u, every live node t with not
+ * D[u][v] < D[u][t] + D[t][v] (in increasing slot order), then v; by Theorem
+ * al_correct it holds every shortest u -> v path -- and Dijkstra on the small
+ * graph of the weights among the candidates.  Ties: the next settled node is
+ * the one of least distance and lowest candidate index; a predecessor changes
+ * only on a strict improvement.  The float candidate test keeps t within a
+ * relative slack of 2^-16 (extra candidates only enlarge the small graph).
+ * Result: the slots of one shortest path u, ..., v; [u] when u == v; empty
+ * (length 0) when v is unreachable.  All buffers are host memory owned by the
+ * caller; the calls wait for the GPU.  Errors: APSP_E_NODE for a dead or
+ * out-of-range id; APSP_E_ARG for bad sizes / null pointers, or if the small
+ * graph does not reach v (possible only when an APSP_D_GIVEN matrix was not
+ * the APSP matrix of W). */
+
+/* count queries: pairs uv[2*q], uv[2*q+1].  lens[q] receives the number of
+ * nodes of path q and paths[q*stride ..] its first min(lens[q], stride)
+ * slots (a longer path is cut; lens[q] still gives its full length). */
+apsp_status apsp_query_paths(apsp_graph *g, const int32_t *uv, int32_t count, int32_t *paths, int32_t stride,
+                             int32_t *lens);
+/* One query: path[0 .. min(*len, cap)) as above. */
+apsp_status apsp_query_path(apsp_graph *g, int32_t u, int32_t v, int32_t *path, int32_t cap, int32_t *len);
+/* Algorithm 8 (warm-start "all shortest paths") on Algorithm 7's small graph:
+ * Algorithm 7's path first, then for each candidate t other than u and v (in
+ * candidate order) the tree path u -> t of the forward Dijkstra joined to the
+ * tree path t -> v of a Dijkstra from v on the reversed small graph, unless
+ * already listed or not loop-free (a zero-weight cycle can make the join a
+ * walk).  Every listed path is a shortest path; the list need not hold all
+ * of them.  Path p is nodes[offsets[p] .. offsets[p + 1]); *n_paths and
+ * *n_nodes receive the counts.  With nodes or offsets NULL only the counts
+ * are returned; if paths_cap < *n_paths or nodes_cap < *n_nodes nothing is
+ * written and APSP_E_ARG is returned (offsets needs paths_cap + 1 entries). */
+apsp_status apsp_query_all_paths(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, int64_t nodes_cap,
+                                 int64_t *offsets, int32_t paths_cap, int32_t *n_paths, int64_t *n_nodes);
+
 /* Copy the n_slots x n_slots top-left block of D (or W) to dst with leading
  * dimension ld_dst (elements); dst is device memory if dst_on_device, else
  * host.  Dead slots read as missing.  Waits. */

@@ -512,8 +512,7 @@ def warm_shortest_path(M: np.ndarray, W: np.ndarray, alive: np.ndarray, i: int, 
     if M[i, j] == missing(M):
         return []
     cand = candidate_node_list(M, alive, i, j)
-    E = exact(W, alive)
-    small = E[np.ix_(cand, cand)]
+    small = exact(np.asarray(W)[np.ix_(cand, cand)])     # small_matrix[a][b] = A_G[cand[a]][cand[b]]
     _, pred = small_dijkstra(small, 0)
     return [cand[a] for a in _tree_path(pred, 0, len(cand) - 1)]
 
@@ -533,8 +532,7 @@ def all_shortest_paths_alg8(M: np.ndarray, W: np.ndarray, alive: np.ndarray, i: 
     if M[i, j] == missing(M):
         return []
     cand = candidate_node_list(M, alive, i, j)
-    E = exact(W, alive)
-    small = E[np.ix_(cand, cand)]
+    small = exact(np.asarray(W)[np.ix_(cand, cand)])
     K = len(cand)
     _, pred_i = small_dijkstra(small, 0)
     _, pred_j = small_dijkstra(np.ascontiguousarray(small.T), K - 1)   # reverse graph: t -> j

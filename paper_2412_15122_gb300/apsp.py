@@ -110,6 +110,9 @@ def _load():
         "apsp_recompute": [P],
         "apsp_query": [P, I32, I32, P],
         "apsp_query_batch": [P, P, I32, P],
+        "apsp_query_paths": [P, P, I32, P, I32, P],
+        "apsp_query_path": [P, I32, I32, P, I32, ctypes.POINTER(I32)],
+        "apsp_query_all_paths": [P, I32, I32, P, I64, P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64)],
         "apsp_copy_D": [P, P, I64, I32],
         "apsp_copy_W": [P, P, I64, I32],
         "apsp_copy_alive": [P, P],
@@ -253,6 +256,37 @@ def apsp_query_batch(g: int, uv: np.ndarray, dtype: int) -> np.ndarray:
     out = np.zeros(len(uv), dtype=_np_dtype(dtype))
     _check(_load().apsp_query_batch(g, uv.ctypes.data, len(uv), out.ctypes.data), "apsp_query_batch")
     return out
+
+
+def apsp_query_paths(g: int, uv: np.ndarray, stride: int):
+    """Algorithm 7 for each pair: (paths count x stride, lens count)."""
+    uv = np.ascontiguousarray(uv, dtype=np.int32).reshape(-1, 2)
+    paths = np.full((len(uv), max(stride, 1)), -1, dtype=np.int32)
+    lens = np.zeros(len(uv), dtype=np.int32)
+    _check(_load().apsp_query_paths(g, uv.ctypes.data, len(uv), paths.ctypes.data, stride, lens.ctypes.data),
+           "apsp_query_paths")
+    return paths[:, :stride], lens
+
+
+def apsp_query_path(g: int, u: int, v: int, cap: int) -> list:
+    """Algorithm 7 for one pair: the slots of a shortest path (cut to cap; see apsp_query_paths for the full length)."""
+    buf = np.zeros(max(cap, 1), dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(_load().apsp_query_path(g, u, v, buf.ctypes.data, cap, ctypes.byref(n)), "apsp_query_path")
+    return [int(x) for x in buf[:min(n.value, cap)]]
+
+
+def apsp_query_all_paths(g: int, u: int, v: int) -> list:
+    """Algorithm 8: list of shortest paths (lists of slots); sizes first, then the paths."""
+    npaths, nnodes = ctypes.c_int32(), ctypes.c_int64()
+    L = _load()
+    _check(L.apsp_query_all_paths(g, u, v, None, 0, None, 0, ctypes.byref(npaths), ctypes.byref(nnodes)),
+           "apsp_query_all_paths")
+    nodes = np.zeros(max(nnodes.value, 1), dtype=np.int32)
+    offs = np.zeros(npaths.value + 1, dtype=np.int64)
+    _check(L.apsp_query_all_paths(g, u, v, nodes.ctypes.data, nnodes.value, offs.ctypes.data, npaths.value,
+                                  ctypes.byref(npaths), ctypes.byref(nnodes)), "apsp_query_all_paths")
+    return [[int(x) for x in nodes[offs[p]:offs[p + 1]]] for p in range(npaths.value)]
 
 
 def apsp_copy_D(g: int, dst, ld: int, on_device: bool):
@@ -540,6 +574,15 @@ class Graph:
 
     def query_batch(self, uv):
         return apsp_query_batch(self.h, uv, self.dtype)
+
+    def query_path(self, u: int, v: int, cap: Optional[int] = None) -> list:
+        return apsp_query_path(self.h, u, v, self.capacity + 1 if cap is None else cap)
+
+    def query_paths(self, uv, stride: Optional[int] = None):
+        return apsp_query_paths(self.h, uv, self.capacity + 1 if stride is None else stride)
+
+    def query_all_paths(self, u: int, v: int) -> list:
+        return apsp_query_all_paths(self.h, u, v)
 
     def info(self) -> dict:
         return apsp_info_get(self.h)

@@ -16,6 +16,7 @@
 #include <limits>
 #include <new>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -63,6 +64,9 @@ struct apsp_graph {
     uint8_t *pstamp = nullptr, *rstamp = nullptr;
     int4 *items = nullptr;
     Ctl *ctl = nullptr;
+    // path queries (Section 4): per-call buffers, grown on demand
+    void *pq_uv = nullptr, *pq_out = nullptr, *pq_wide = nullptr;
+    int64_t pq_uv_bytes = 0, pq_out_bytes = 0, pq_wide_bytes = 0;
     float *model = nullptr;
     int64_t pair_cap = 0;
     int32_t item_cap = 0;
@@ -175,6 +179,32 @@ void *dalloc(apsp_graph *g, size_t bytes) {
         g->dev_bytes += (int64_t)bytes;
     }
     return p;
+}
+
+// Frees one buffer from dalloc before the handle is destroyed.
+void dfree(apsp_graph *g, void *p) {
+    if (!p) return;
+    for (size_t k = 0; k < g->allocs.size(); ++k) {
+        if (g->allocs[k].first != p) continue;
+        if (g->free_fn) {
+            g->free_fn(p, g->allocs[k].second, (void *)g->stream, g->alloc_ctx);
+        } else {
+            cudaStreamSynchronize(g->stream);
+            cudaFree(p);
+        }
+        g->dev_bytes -= (int64_t)g->allocs[k].second;
+        g->allocs.erase(g->allocs.begin() + (std::ptrdiff_t)k);
+        return;
+    }
+}
+
+// Grows a library-owned device buffer to at least `bytes` (contents are not kept).
+bool ensure_buf(apsp_graph *g, void **p, int64_t *have, int64_t bytes) {
+    if (*p && *have >= bytes) return true;
+    dfree(g, *p);
+    *p = dalloc(g, (size_t)bytes);
+    *have = *p ? bytes : 0;
+    return *p != nullptr;
 }
 
 void release(apsp_graph *g) {
@@ -562,6 +592,164 @@ template <typename T> apsp_status recompute_impl(apsp_graph *g) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Path queries (Section 4): Algorithm 7 for batches of pairs, Algorithm 8 for
+// one pair (its joins assembled here from the device's trees).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int PQ_CHUNK = 65536;
+
+inline int pq_slots(const apsp_graph *g) { return (int)round_up(g->ld + 2, 4); }
+
+bool pq_nodes_ok(const apsp_graph *g, int u, int v) {
+    return u >= 0 && v >= 0 && u < g->cap && v < g->cap && g->alive_h[u] && g->alive_h[v];
+}
+
+// Runs the path kernel over nb queries (uv host) and copies the rows of
+// `row` int32 back into out_h; redoes deferred queries with the wide pass.
+template <typename T>
+apsp_status pq_run(apsp_graph *g, const int32_t *uv, int nb, int mode, int stride, int64_t row,
+                   std::vector<int32_t> &out_h) {
+    const int S = pq_slots(g);
+    const int64_t wide_stride = 5 * (int64_t)S + (2 * (int64_t)S + 3) / 4;
+    if (!ensure_buf(g, &g->pq_uv, &g->pq_uv_bytes, (int64_t)nb * 8) ||
+        !ensure_buf(g, &g->pq_out, &g->pq_out_bytes, (int64_t)nb * row * 4) ||
+        !ensure_buf(g, &g->pq_wide, &g->pq_wide_bytes, apsp::PQ_WIDE_GRID * wide_stride * 4))
+        return APSP_E_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(g->pq_uv, uv, (size_t)nb * 8, cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    apsp::PathQuery q;
+    q.uv = (const int32_t *)g->pq_uv;
+    q.count = nb;
+    q.out = (int32_t *)g->pq_out;
+    q.row = row;
+    q.stride = stride;
+    q.mode = mode;
+    q.wide = (int32_t *)g->pq_wide;
+    q.wide_stride = wide_stride;
+    q.wide_slots = S;
+    const Dev<T> d = dev_of<T>(g);
+    out_h.resize((size_t)nb * row);
+    for (int pass = 0; pass < 2; ++pass) {
+        if ((e = apsp::run_path_query<T>(g->lc, d, q, pass == 1)) != cudaSuccess) return cuda_status(e);
+        e = cudaMemcpyAsync(out_h.data(), g->pq_out, (size_t)nb * row * 4, cudaMemcpyDeviceToHost, g->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        apsp_status st = sync_ctl(g, nullptr);
+        if (st != APSP_OK) return st;
+        bool deferred = false;
+        for (int k = 0; k < nb && !deferred; ++k) deferred = out_h[(size_t)k * row] == apsp::PQ_DEFERRED;
+        if (!deferred) break;
+    }
+    for (int k = 0; k < nb; ++k)
+        if (out_h[(size_t)k * row] < 0) return APSP_E_ARG;   // D is not the APSP matrix of W
+    return APSP_OK;
+}
+
+template <typename T>
+apsp_status paths_impl(apsp_graph *g, const int32_t *uv, int32_t count, int32_t *paths, int32_t stride,
+                       int32_t *lens) {
+    if (count < 0 || stride < 0 || (count > 0 && (!uv || !lens)) || (count > 0 && stride > 0 && !paths))
+        return APSP_E_ARG;
+    for (int32_t k = 0; k < count; ++k)
+        if (!pq_nodes_ok(g, uv[2 * k], uv[2 * k + 1])) return APSP_E_NODE;
+    settle_fetch<T>(g);
+    const int64_t row = 1 + (int64_t)stride;
+    std::vector<int32_t> out_h;
+    for (int32_t b0 = 0; b0 < count; b0 += PQ_CHUNK) {
+        const int nb = std::min(PQ_CHUNK, count - b0);
+        apsp_status st = pq_run<T>(g, uv + 2 * (int64_t)b0, nb, 0, stride, row, out_h);
+        if (st != APSP_OK) return st;
+        for (int k = 0; k < nb; ++k) {
+            const int32_t *o = out_h.data() + (size_t)k * row;
+            lens[b0 + k] = o[0];
+            const int keep = std::min<int32_t>(o[0], stride);
+            if (keep > 0) std::memcpy(paths + (int64_t)(b0 + k) * stride, o + 1, (size_t)keep * 4);
+        }
+    }
+    return APSP_OK;
+}
+
+// Walks a predecessor array from small node `from` until `to`; empty if it
+// does not get there within K steps.
+std::vector<int32_t> pq_walk(const int32_t *pred, int K, int from, int to) {
+    std::vector<int32_t> w{from};
+    while (w.back() != to) {
+        const int32_t p = pred[w.back()];
+        if (p < 0 || (int)w.size() > K) return {};
+        w.push_back(p);
+    }
+    return w;
+}
+
+template <typename T>
+apsp_status all_paths_impl(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, int64_t nodes_cap,
+                           int64_t *offsets, int32_t paths_cap, int32_t *n_paths, int64_t *n_nodes) {
+    if (!n_paths || !n_nodes || nodes_cap < 0 || paths_cap < 0) return APSP_E_ARG;
+    if (!pq_nodes_ok(g, u, v)) return APSP_E_NODE;
+    settle_fetch<T>(g);
+    std::vector<std::vector<int32_t>> out;
+    if (u == v) {
+        out.push_back({u});
+    } else {
+        const int S = pq_slots(g);
+        const int64_t row = 1 + 3 * (int64_t)S;
+        const int32_t uv[2] = {u, v};
+        std::vector<int32_t> o;
+        apsp_status st = pq_run<T>(g, uv, 1, 1, 0, row, o);
+        if (st != APSP_OK) return st;
+        const int K = o[0];
+        if (K >= 2) {
+            const int32_t *cand = o.data() + 1, *pf = cand + K, *pb = pf + K;
+            // Psi(i, j): the forward tree path to small node K - 1
+            std::vector<int32_t> psi = pq_walk(pf, K, K - 1, 0);
+            if (psi.empty()) return APSP_E_ARG;
+            std::reverse(psi.begin(), psi.end());
+            std::set<std::vector<int32_t>> seen;
+            auto emit = [&](const std::vector<int32_t> &small) {
+                std::vector<int32_t> p(small.size());
+                for (size_t k = 0; k < small.size(); ++k) p[k] = cand[small[k]];
+                if (seen.insert(p).second) out.push_back(std::move(p));
+            };
+            emit(psi);
+            std::vector<int32_t> stamp(K, -1);
+            for (int t = 1; t < K - 1; ++t) {
+                std::vector<int32_t> first = pq_walk(pf, K, t, 0);       // t .. 0
+                std::vector<int32_t> second = pq_walk(pb, K, t, K - 1);  // t .. K - 1
+                if (first.empty() || second.empty()) continue;
+                std::reverse(first.begin(), first.end());
+                first.insert(first.end(), second.begin() + 1, second.end());
+                bool simple = true;   // a join through a zero-weight cycle is a walk, not a path
+                for (int32_t a : first) {
+                    if (stamp[a] == t) {
+                        simple = false;
+                        break;
+                    }
+                    stamp[a] = t;
+                }
+                if (simple) emit(first);
+            }
+        }
+    }
+    int64_t total = 0;
+    for (auto &p : out) total += (int64_t)p.size();
+    *n_paths = (int32_t)out.size();
+    *n_nodes = total;
+    if (!nodes || !offsets) return APSP_OK;   // size query
+    if ((int64_t)out.size() > paths_cap || total > nodes_cap) return APSP_E_ARG;
+    int64_t at = 0;
+    for (size_t k = 0; k < out.size(); ++k) {
+        offsets[k] = at;
+        std::memcpy(nodes + at, out[k].data(), out[k].size() * 4);
+        at += (int64_t)out[k].size();
+    }
+    offsets[out.size()] = at;
+    return APSP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 
@@ -699,6 +887,26 @@ apsp_status apsp_query_batch(apsp_graph *g, const int32_t *uv, int32_t count, vo
         std::memcpy((char *)out + (size_t)b0 * g->esz, h, (size_t)nb * g->esz);
     }
     return APSP_OK;
+}
+
+// Path queries (Section 4): Algorithm 7 and Algorithm 8.
+apsp_status apsp_query_paths(apsp_graph *g, const int32_t *uv, int32_t count, int32_t *paths, int32_t stride,
+                             int32_t *lens) {
+    if (!g) return APSP_E_ARG;
+    return g->dtype == APSP_F32 ? paths_impl<float>(g, uv, count, paths, stride, lens)
+                                : paths_impl<int32_t>(g, uv, count, paths, stride, lens);
+}
+
+apsp_status apsp_query_path(apsp_graph *g, int32_t u, int32_t v, int32_t *path, int32_t cap, int32_t *len) {
+    const int32_t uv[2] = {u, v};
+    return apsp_query_paths(g, uv, 1, path, cap, len);
+}
+
+apsp_status apsp_query_all_paths(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, int64_t nodes_cap,
+                                 int64_t *offsets, int32_t paths_cap, int32_t *n_paths, int64_t *n_nodes) {
+    if (!g) return APSP_E_ARG;
+    return g->dtype == APSP_F32 ? all_paths_impl<float>(g, u, v, nodes, nodes_cap, offsets, paths_cap, n_paths, n_nodes)
+                                : all_paths_impl<int32_t>(g, u, v, nodes, nodes_cap, offsets, paths_cap, n_paths, n_nodes);
 }
 
 static apsp_status copy_mat(apsp_graph *g, const void *src, void *dst, int64_t ld_dst, int32_t on_dev) {

@@ -284,28 +284,42 @@ __global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d, int rows_per_ct
             col[q * 4 + e] = M::inf();
         }
     }
-#pragma unroll 2
-    for (int row = r0 + w; row < r1; row += 8) {
-        if (!d.alive[row]) continue;
-        const T wo = d.w_out[row];
-        const T *Dr = d.D + (int64_t)row * d.ld + c0 + lane * 4;
-        V4 v[4];
+    // Two rows per warp and step, all eight loads issued before any use.  No
+    // per-row liveness test: a dead row has w_out = missing and an all-missing
+    // row of D, so it changes neither reduction.
+    for (int row = r0 + w; row < r1; row += 16) {
+        const int rows2 = row + 8 < r1 ? 2 : 1;
+        V4 v[2][4];
+        T wo[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (cin[q]) v[q] = *reinterpret_cast<const V4 *>(Dr + q * 128);
-        T racc = M::inf();
+        for (int h = 0; h < 2; ++h) {
+            wo[h] = M::inf();
+            if (h < rows2) {
+                const int r = row + 8 * h;
+                wo[h] = d.w_out[r];
+                const T *Dr = d.D + (int64_t)r * d.ld + c0 + lane * 4;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!cin[q]) continue;
-            T e4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                col[q * 4 + e] = M::add_min(wo, e4[e], col[q * 4 + e]);
-                racc = M::add_min(e4[e], win[q * 4 + e], racc);
+                for (int q = 0; q < 4; ++q)
+                    if (cin[q]) v[h][q] = *reinterpret_cast<const V4 *>(Dr + q * 128);
             }
         }
-        racc = warp_min(racc);
-        if (lane == 0 && M::finite(racc)) atomicMin(&d.vin_k[row], M::key(racc));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h >= rows2) break;
+            T racc = M::inf();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!cin[q]) continue;
+                T e4[4] = {v[h][q].x, v[h][q].y, v[h][q].z, v[h][q].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    col[q * 4 + e] = M::add_min(wo[h], e4[e], col[q * 4 + e]);
+                    racc = M::add_min(e4[e], win[q * 4 + e], racc);
+                }
+            }
+            racc = warp_min(racc);
+            if (lane == 0 && M::finite(racc)) atomicMin(&d.vin_k[row + 8 * h], M::key(racc));
+        }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)

@@ -55,9 +55,10 @@ template <typename T>
 cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
     cudaError_t e;
     if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
-    // one wave: about 3 CTAs per SM split into column bands x row ranges
+    // exactly one wave (never a partial second one): the resident CTAs split
+    // into column bands x row ranges
     const int bands = cdiv(d.span, INS_CB);
-    const int ranges = std::max(1, std::min(cdiv(d.span, 8), (3 * c.num_sms + bands - 1) / bands));
+    const int ranges = std::max(1, std::min(cdiv(d.span, 16), c.insred_per_sm * c.num_sms / bands));
     const int rows_per = cdiv(d.span, ranges);
     dim3 g(bands, cdiv(d.span, rows_per));
     if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d, rows_per); })) != cudaSuccess) return e;
@@ -203,12 +204,27 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     c.detect2_grid = std::max(1, det2_sm) * c.num_sms;
     c.detunit_grid = 4 * c.num_sms;
     c.detalloc_grid = (int)((ld + 255) / 256);   // a lane per row: 256 rows a CTA
+    int ir_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ir_sm, k_insert_reduce<T>, 256, 0)) != cudaSuccess) return e;
+    c.insred_per_sm = std::max(1, ir_sm);
     size_t rel = (size_t)ld * sizeof(int32_t);
     if ((e = allow_max_smem(k_insert_relax<T>)) != cudaSuccess) return e;
     int rel_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rel_sm, k_insert_relax<T>, 256, rel)) != cudaSuccess) return e;
     c.relax_grid = std::max(1, rel_sm) * c.num_sms;
     return cudaSuccess;
+}
+
+// Path queries (paths.cuh): the shared-memory pass over every query, or the
+// pass of PQ_WIDE_GRID CTAs over the queries the first one deferred.
+template <typename T> cudaError_t run_path_query(const LaunchCtx &c, const Dev<T> &d, const PathQuery &q, bool wide) {
+    if (q.count <= 0) return cudaSuccess;
+    if (wide)
+        return launch(c, "path_query_wide",
+                      [&] { k_path_query<T, true><<<PQ_WIDE_GRID, PQ_THREADS, 0, c.stream>>>(d, q); });
+    const int grid = std::min(q.count, 4 * c.num_sms);
+    return launch(c, "path_query",
+                  [&] { k_path_query<T, false><<<grid, PQ_THREADS, pq_smem_bytes<T>(), c.stream>>>(d, q); });
 }
 
 // One persistent launch for a whole batch of graphs (batch.cuh).
@@ -233,6 +249,7 @@ template <typename T> cudaError_t batch_occupancy(size_t smem, int *per_sm) {
     template cudaError_t run_remove<T>(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);            \
     template cudaError_t run_increase<T>(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &); \
     template cudaError_t run_repair<T>(const LaunchCtx &, const Dev<T> &, const RepairCfg &);                 \
+    template cudaError_t run_path_query<T>(const LaunchCtx &, const Dev<T> &, const PathQuery &, bool);       \
     template cudaError_t setup_shapes<T>(LaunchCtx &, int64_t, int);                                          \
     template cudaError_t run_batch<T>(cudaStream_t, BatchHeader *, int, size_t);                              \
     template cudaError_t batch_occupancy<T>(size_t, int *);

@@ -7,6 +7,7 @@
 
 #include "batch.cuh"
 #include "kernels.cuh"
+#include "paths.cuh"
 
 namespace apsp {
 
@@ -22,6 +23,7 @@ struct LaunchCtx {
     int detect2_grid = 1;
     int detunit_grid = 1;
     int detalloc_grid = 1;
+    int insred_per_sm = 1;
 };
 
 template <typename T> cudaError_t run_fill(const LaunchCtx &, T *, T, int64_t);
@@ -33,6 +35,7 @@ template <typename T> cudaError_t run_decrease(const LaunchCtx &, const Dev<T> &
 template <typename T> cudaError_t run_remove(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);
 template <typename T> cudaError_t run_increase(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &);
 template <typename T> cudaError_t run_repair(const LaunchCtx &, const Dev<T> &, const RepairCfg &);
+template <typename T> cudaError_t run_path_query(const LaunchCtx &, const Dev<T> &, const PathQuery &, bool);
 template <typename T> cudaError_t setup_shapes(LaunchCtx &, int64_t, int);
 template <typename T> cudaError_t run_batch(cudaStream_t, BatchHeader *, int, size_t);
 template <typename T> cudaError_t batch_occupancy(size_t, int *);

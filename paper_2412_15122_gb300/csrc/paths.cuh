@@ -1,0 +1,290 @@
+// Warm-start path queries (Section 4): Algorithm 7 and the trees behind
+// Algorithm 8, on the device.
+//
+// One CTA per query (a grid-stride loop over a batch of queries):
+//   1. candidate scan: the live nodes t other than i and j that are not
+//      excluded by the test SPD(i, j) < SPD(i, t) + SPD(t, j) (Algorithm 7;
+//      Theorem al_correct: every shortest i -> j path uses only them).  Row i
+//      of D and row j of D^T (column j of D) are read with 16-byte vectors,
+//      each thread owning a contiguous run of slots, so a block-wide
+//      exclusive scan gives the candidates in increasing slot order:
+//      cand = [i, t..., j], K entries.
+//   2. Dijkstra on the small graph (adjacency among the candidates: gathered
+//      into shared memory by the whole CTA when K <= PQ_SK, else read from W
+//      as it goes): one warp, lanes owning candidates a = lane (mod 32);
+//      the next node is the unvisited one of least distance, the lowest small
+//      index on a tie, and a predecessor changes only on a strict
+//      improvement.  Forward from small node 0 (stops when K - 1 settles for
+//      a single path); for Algorithm 8 a second warp runs it backward from
+//      K - 1 on the reversed small graph.
+//   3. output: the path i -> j (Algorithm 7's translation back to slot ids),
+//      or the candidate list and both predecessor arrays (Algorithm 8's
+//      joins are assembled by the host library).
+// Small graphs of up to PQ_KS candidates live in shared memory.  A query with
+// more candidates (only possible with many equal-length routes, e.g. zero
+// weights) is marked deferred and redone by a second launch of PQ_WIDE_GRID
+// CTAs whose per-CTA arrays sit in a library-owned global scratch area.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace apsp {
+
+constexpr int PQ_THREADS = 512;
+constexpr int PQ_KS = 1024;
+constexpr int PQ_SK = 64;           // small graphs of up to PQ_SK nodes have their matrix staged in shared memory
+constexpr int PQ_WIDE_GRID = 4;
+constexpr int32_t PQ_DEFERRED = -2;
+constexpr int32_t PQ_BROKEN = -1;   // the small graph does not reach j: D is not the APSP matrix of W
+
+struct PathQuery {
+    const int32_t *uv;     // count (i, j) pairs, device
+    int count;
+    int32_t *out;          // count rows of `row` int32, device
+    int64_t row;
+    int stride;            // mode 0: path entries kept per query (row = 1 + stride)
+    int mode;              // 0: Algorithm 7 path; 1: Algorithm 8 trees (row = 1 + 3 * wide_slots)
+    int32_t *wide;         // PQ_WIDE_GRID * wide_stride int32
+    int64_t wide_stride;
+    int wide_slots;        // candidates a wide CTA can hold (>= span + 2)
+};
+
+// Per-CTA arrays of one query.
+template <typename T> struct PqArrays {
+    int32_t *cand;
+    T *fdist, *bdist;
+    int32_t *fpred, *bpred;
+    uint8_t *fdone, *bdone;
+};
+
+template <typename T> __device__ __forceinline__ uint32_t pq_okey(T v) { return (uint32_t)MinPlus<T>::key(v); }
+
+// Candidate test of Algorithm 7 for one slot: kept unless D[i][j] < D[i][t] +
+// D[t][j].  Float: within the same relative slack as the tightness test (an
+// extra candidate only enlarges the small graph).
+template <typename T> __device__ __forceinline__ bool pq_keep(T a, T b, T dij) {
+    return MinPlus<T>::tight(a + b, dij);
+}
+
+// Step 1.  Writes the interior candidates to cand[1 ..] in slot order (only
+// those that fit in kcap - 2 entries) and returns their number.  All threads.
+template <typename T>
+__device__ int pq_scan(const Dev<T> &d, int i, int j, T dij, int32_t *cand, int kcap, int *wtot) {
+    using V4 = typename MinPlus<T>::V4;
+    const int nv = d.span >> 2;
+    const int per = (nv + (int)blockDim.x - 1) / (int)blockDim.x;   // <= 16: span <= 32768
+    const int v0 = threadIdx.x * per;
+    const int v1 = min(v0 + per, nv);
+    const V4 *ri = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+    const V4 *rj = reinterpret_cast<const V4 *>((d.DT ? d.DT : d.D) + (int64_t)j * d.ld);
+    const int4 *al = reinterpret_cast<const int4 *>(d.alive);
+    unsigned long long mask = 0ull;
+#pragma unroll 4
+    for (int v = v0; v < v1; ++v) {
+        const V4 a = ri[v], b = rj[v];
+        const int4 l = al[v];
+        const int t = v << 2;
+        const unsigned bit = (unsigned)(v - v0) << 2;
+        if (l.x && t != i && t != j && pq_keep<T>(a.x, b.x, dij)) mask |= 1ull << bit;
+        if (l.y && t + 1 != i && t + 1 != j && pq_keep<T>(a.y, b.y, dij)) mask |= 1ull << (bit + 1);
+        if (l.z && t + 2 != i && t + 2 != j && pq_keep<T>(a.z, b.z, dij)) mask |= 1ull << (bit + 2);
+        if (l.w && t + 3 != i && t + 3 != j && pq_keep<T>(a.w, b.w, dij)) mask |= 1ull << (bit + 3);
+    }
+    const int mine = __popcll(mask);
+    int wsum;
+    const int wex = warp_exclusive_scan(mine, &wsum);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wtot[warp] = wsum;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)blockDim.x >> 5;
+        int x = lane < nw ? wtot[lane] : 0, tot;
+        const int ex = warp_exclusive_scan(x, &tot);
+        __syncwarp();
+        if (lane < nw) wtot[lane] = ex;
+        if (lane == 0) wtot[32] = tot;
+    }
+    __syncthreads();
+    int pos = 1 + wtot[warp] + wex;
+    const int total = wtot[32];
+    while (mask) {
+        const int b = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        if (pos < kcap - 1) cand[pos] = (v0 << 2) + b;
+        ++pos;
+    }
+    return total;
+}
+
+// Step 2, one warp.  Dijkstra over the K candidates from small node `src`;
+// `reverse` relaxes a -> b with the weight of edge cand[b] -> cand[a].
+template <typename T>
+__device__ void pq_dijkstra(const Dev<T> &d, const int32_t *cand, int K, int src, bool reverse, bool stop_at_last,
+                            const T *small, T *dist, int32_t *pred, uint8_t *done) {
+    using M = MinPlus<T>;
+    const int lane = threadIdx.x & 31;
+    for (int a = lane; a < K; a += 32) {
+        dist[a] = a == src ? (T)0 : M::inf();
+        pred[a] = -1;
+        done[a] = 0;
+    }
+    __syncwarp();
+    for (int it = 0; it < K; ++it) {
+        unsigned long long best = ~0ull;
+        for (int a = lane; a < K; a += 32)
+            if (!done[a]) {
+                const unsigned long long key = ((unsigned long long)pq_okey<T>(dist[a]) << 32) | (unsigned)a;
+                best = key < best ? key : best;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+            best = y < best ? y : best;
+        }
+        if (best == ~0ull) break;
+        const int a = (int)(best & 0xffffffffu);
+        const T da = M::unkey((int32_t)(best >> 32));
+        if (!M::finite(da)) break;
+        if ((a & 31) == lane) done[a] = 1;
+        if (stop_at_last && a == K - 1) break;
+        const int ca = cand[a];
+        for (int b = lane; b < K; b += 32) {
+            if (done[b]) continue;
+            T w;
+            if (small) {
+                w = reverse ? small[b * K + a] : small[a * K + b];
+            } else {
+                const int cb = cand[b];
+                w = reverse ? d.W[(int64_t)cb * d.ld + ca] : d.W[(int64_t)ca * d.ld + cb];
+            }
+            if (!M::finite(w)) continue;
+            const T nd = M::add(da, w);
+            if (nd < dist[b]) {
+                dist[b] = nd;
+                pred[b] = a;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T, bool WIDE>
+__global__ void __launch_bounds__(PQ_THREADS) k_path_query(Dev<T> d, PathQuery q) {
+    using M = MinPlus<T>;
+    extern __shared__ __align__(16) unsigned char pq_smem[];
+    __shared__ int wtot[33];
+    __shared__ int32_t o0_s;
+    PqArrays<T> A;
+    int kcap;
+    if (!WIDE) {
+        kcap = PQ_KS;
+        A.cand = reinterpret_cast<int32_t *>(pq_smem);
+        A.fdist = reinterpret_cast<T *>(A.cand + PQ_KS);
+        A.bdist = A.fdist + PQ_KS;
+        A.fpred = reinterpret_cast<int32_t *>(A.bdist + PQ_KS);
+        A.bpred = A.fpred + PQ_KS;
+        A.fdone = reinterpret_cast<uint8_t *>(A.bpred + PQ_KS);
+        A.bdone = A.fdone + PQ_KS;
+    } else {
+        kcap = q.wide_slots;
+        int32_t *base = q.wide + (int64_t)blockIdx.x * q.wide_stride;
+        A.cand = base;
+        A.fdist = reinterpret_cast<T *>(base + kcap);
+        A.bdist = A.fdist + kcap;
+        A.fpred = reinterpret_cast<int32_t *>(A.bdist + kcap);
+        A.bpred = A.fpred + kcap;
+        A.fdone = reinterpret_cast<uint8_t *>(A.bpred + kcap);
+        A.bdone = A.fdone + kcap;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int qi = blockIdx.x; qi < q.count; qi += gridDim.x) {
+        int32_t *o = q.out + (int64_t)qi * q.row;
+        if (WIDE) {
+            if (threadIdx.x == 0) o0_s = o[0];
+            __syncthreads();
+            const int32_t o0 = o0_s;
+            __syncthreads();
+            if (o0 != PQ_DEFERRED) continue;
+        }
+        const int i = q.uv[2 * qi], j = q.uv[2 * qi + 1];
+        if (i == j) {   // Algorithm 7: the path of a node to itself is [i]
+            if (threadIdx.x == 0) {
+                o[0] = 1;
+                if (q.mode == 0) {
+                    if (q.stride > 0) o[1] = i;
+                } else {
+                    o[1] = i;
+                    o[2] = -1;
+                    o[3] = -1;
+                }
+            }
+            continue;
+        }
+        const T dij = d.D[(int64_t)i * d.ld + j];
+        if (!M::finite(dij)) {   // unreachable: no path
+            if (threadIdx.x == 0) o[0] = 0;
+            continue;
+        }
+        const int K = pq_scan<T>(d, i, j, dij, A.cand, kcap, wtot) + 2;
+        if (K > kcap) {
+            if (threadIdx.x == 0) o[0] = WIDE ? PQ_BROKEN : PQ_DEFERRED;
+            __syncthreads();
+            continue;
+        }
+        if (threadIdx.x == 0) {
+            A.cand[0] = i;
+            A.cand[K - 1] = j;
+        }
+        __syncthreads();
+        // Algorithm 7's small_matrix: gathered at once by the whole CTA when
+        // it fits, else read from W by the Dijkstra warp as it goes
+        const T *small = nullptr;
+        if (!WIDE && K <= PQ_SK) {
+            T *sm = reinterpret_cast<T *>(A.bdone + PQ_KS);
+            for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+                const int a = e / K, b = e - a * K;
+                sm[e] = d.W[(int64_t)A.cand[a] * d.ld + A.cand[b]];
+            }
+            __syncthreads();
+            small = sm;
+        }
+        if (warp == 0) pq_dijkstra<T>(d, A.cand, K, 0, false, q.mode == 0, small, A.fdist, A.fpred, A.fdone);
+        else if (warp == 1 && q.mode == 1)
+            pq_dijkstra<T>(d, A.cand, K, K - 1, true, false, small, A.bdist, A.bpred, A.bdone);
+        __syncthreads();
+        if (q.mode == 0) {
+            if (threadIdx.x == 0) {
+                int L = 1, b = K - 1;
+                while (b != 0 && L <= K) {
+                    b = A.fpred[b];
+                    if (b < 0) break;
+                    ++L;
+                }
+                if (b != 0) {
+                    o[0] = PQ_BROKEN;
+                } else {
+                    o[0] = L;
+                    b = K - 1;
+                    for (int p = L - 1; p >= 0; --p) {
+                        if (p < q.stride) o[1 + p] = A.cand[b];
+                        b = A.fpred[b];
+                    }
+                }
+            }
+        } else if (warp == 0) {
+            for (int a = lane; a < K; a += 32) {
+                o[1 + a] = A.cand[a];
+                o[1 + K + a] = A.fpred[a];
+                o[1 + 2 * K + a] = A.bpred[a];
+            }
+            if (lane == 0) o[0] = K;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T> constexpr size_t pq_smem_bytes() {
+    return (size_t)PQ_KS * (3 * sizeof(int32_t) + 2 * sizeof(T) + 2) + (size_t)PQ_SK * PQ_SK * sizeof(T);
+}
+
+}  // namespace apsp

@@ -1,0 +1,207 @@
+"""Parity of the device path queries (Algorithm 7, Algorithm 8) with the CPU
+oracle, through the C ABI.
+
+Int32: the device follows the same candidate order and tie rules as the
+oracle, so paths (and Algorithm 8's path lists) must be identical.  Float:
+several paths can be shortest up to rounding, so each device path is checked
+for validity and its length against the fp64 oracle within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import apsp as O
+
+pytestmark = pytest.mark.gpu
+
+F32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2412_15122_gb300 import build
+    build.build()
+
+
+def G(*a, **k):
+    from paper_2412_15122_gb300 import Graph
+    return Graph(*a, **k)
+
+
+def make_graph(n, seed, fp=False, undirected=False, lo=1, hi=1000, p_missing=0.0):
+    W = synth.lognormal_digraph_f32(n, seed) if fp else synth.complete_digraph_i32(n, lo, hi, seed)
+    if p_missing > 0:
+        m = synth.uniform_f64(seed, 77, n * n).reshape(n, n) < p_missing
+        np.fill_diagonal(m, False)
+        W = W.copy()
+        W[m] = np.inf if fp else synth.INF_I32
+    if undirected:
+        W = np.minimum(W, W.T)
+    return W
+
+
+def check_valid(path, u, v, W, alive, dist):
+    """A loop-free path u -> v over live slots whose exact length is `dist`."""
+    assert path[0] == u and path[-1] == v
+    assert len(set(path)) == len(path)
+    assert all(alive[x] for x in path)
+    L = O.path_length(W, path)
+    if O.is_float(np.asarray(dist)):
+        assert abs(float(L) - float(dist)) <= F32_RTOL * abs(float(dist)) + 1e-30, (path, L, dist)
+    else:
+        assert L == dist, (path, L, dist)
+
+
+def pairs_of(n, count, seed):
+    u = synth.uniform_int(seed, 31, count, 0, n - 1)
+    v = synth.uniform_int(seed, 32, count, 0, n - 1)
+    return np.stack([u, v], 1).astype(np.int32)
+
+
+CASES = [(n, fp, und, lo, pm) for n in (2, 31, 130, 257) for fp in (False, True) for und in (False, True)
+         for (lo, pm) in ((1, 0.0), (0, 0.3))]
+
+
+@pytest.mark.parametrize("n,fp,und,lo,pm", CASES)
+def test_alg7_paths_match_oracle(n, fp, und, lo, pm):
+    hi = 4 if lo == 0 else 1000           # small weights: many equal routes
+    W = make_graph(n, 40 + n, fp=fp, undirected=und, lo=lo, hi=hi, p_missing=pm)
+    g = G(W, n + 7, undirected=und)
+    alive = np.ones(n, dtype=bool)
+    M = O.fw(W)
+    if n <= 31:
+        uv = np.array([(i, j) for i in range(n) for j in range(n)], dtype=np.int32)
+    else:
+        uv = np.concatenate([pairs_of(n, 400, n), np.array([[3, 3], [0, n - 1]], np.int32)])
+    paths, lens = g.query_paths(uv)
+    for (u, v), p, L in zip(uv, paths, lens):
+        got = [int(x) for x in p[:L]]
+        if M[u, v] == O.missing(M):
+            assert L == 0 and u != v
+            continue
+        if fp:
+            check_valid(got, u, v, W, alive, M[u, v])
+        else:
+            assert got == O.warm_shortest_path(M, W, alive, int(u), int(v)), (u, v)
+    g.close()
+
+
+@pytest.mark.parametrize("fp", [False, True])
+@pytest.mark.parametrize("lo", [0, 1])
+def test_alg8_path_lists_match_oracle(fp, lo):
+    n = 60
+    W = make_graph(n, 5, fp=fp, lo=lo, hi=5 if lo == 0 else 1000, p_missing=0.2)
+    g = G(W, n)
+    alive = np.ones(n, dtype=bool)
+    M = O.fw(W)
+    for u, v in pairs_of(n, 40, 6):
+        got = g.query_all_paths(int(u), int(v))
+        if fp:
+            for p in got:
+                check_valid(p, u, v, W, alive, M[u, v])
+            assert len({tuple(p) for p in got}) == len(got)
+            if M[u, v] < np.inf:
+                assert got[0] == g.query_path(int(u), int(v))
+        else:
+            assert got == O.all_shortest_paths_alg8(M, W, alive, int(u), int(v)), (u, v)
+    g.close()
+
+
+def test_paths_after_updates_avoid_dead_slots():
+    n, cap = 200, 240
+    W = make_graph(n, 9, lo=1, hi=50)
+    g = G(W, cap)
+    Wm = np.full((cap, cap), synth.INF_I32, dtype=np.int32)
+    Wm[:n, :n] = W
+    alive = np.zeros(cap, dtype=bool)
+    alive[:n] = True
+    for k in (5, 77, 150):
+        g.remove_node(k)
+        alive[k] = False
+        Wm[k, :] = synth.INF_I32
+        Wm[:, k] = synth.INF_I32
+    in_w = synth.uniform_int(9, 50, cap, 1, 50).astype(np.int32)
+    out_w = synth.uniform_int(9, 51, cap, 1, 50).astype(np.int32)
+    p = g.add_node(in_w, out_w)
+    live = alive.copy()
+    Wm[:, p] = np.where(live, in_w, synth.INF_I32)
+    Wm[p, :] = np.where(live, out_w, synth.INF_I32)
+    Wm[p, p] = 0
+    alive[p] = True
+    m = g.info()["n_slots"]
+    M = O.fw(Wm[:m, :m], alive[:m])
+    lv = np.flatnonzero(alive[:m])
+    uv = np.stack([lv[synth.uniform_int(9, 52, 300, 0, len(lv) - 1)],
+                   lv[synth.uniform_int(9, 53, 300, 0, len(lv) - 1)]], 1).astype(np.int32)
+    paths, lens = g.query_paths(uv)
+    for (u, v), q, L in zip(uv, paths, lens):
+        got = [int(x) for x in q[:L]]
+        assert got == O.warm_shortest_path(M, Wm[:m, :m], alive[:m], int(u), int(v))
+        assert all(alive[x] for x in got)
+    assert p == 5 and not alive[77] and not alive[150]     # the new node reused the lowest free slot
+    from paper_2412_15122_gb300 import apsp as A
+    with pytest.raises(A.ApspError):
+        g.query_path(77, 0)
+    g.close()
+
+
+def test_many_candidates_use_the_wide_pass():
+    # All weights zero: every node is on a shortest path, so K = n exceeds the
+    # shared-memory candidate capacity (1024) and the wide pass answers.
+    n = 1500
+    W = np.zeros((n, n), dtype=np.int32)
+    g = G(W, n)
+    alive = np.ones(n, dtype=bool)
+    uv = np.array([[0, n - 1], [700, 3], [n - 1, 0]], dtype=np.int32)
+    paths, lens = g.query_paths(uv)
+    for (u, v), q, L in zip(uv, paths, lens):
+        got = [int(x) for x in q[:L]]
+        check_valid(got, int(u), int(v), W, alive, 0)
+        # Dijkstra settles small node 0 first and then, at distance 0 on a
+        # tie, the lowest candidate index: v is reached directly from u.
+        assert got == [int(u), int(v)]
+    g.close()
+
+
+def test_path_edge_cases():
+    n = 40
+    W = make_graph(n, 12, lo=1, hi=100, p_missing=0.0)
+    W[:, 7] = synth.INF_I32            # node 7 unreachable from everyone else
+    W[7, 7] = 0
+    g = G(W, n)
+    M = O.fw(W)
+    assert g.query_path(3, 3) == [3]
+    assert g.query_path(3, 7) == []
+    full = g.query_path(7, 20)
+    assert full == O.warm_shortest_path(M, W, np.ones(n, bool), 7, 20)
+    paths, lens = g.query_paths(np.array([[7, 20]], np.int32), stride=1)
+    assert lens[0] == len(full) and paths[0, 0] == 7        # cut to the stride, full length reported
+    p0, l0 = g.query_paths(np.zeros((0, 2), np.int32), stride=4)
+    assert len(l0) == 0
+    from paper_2412_15122_gb300 import apsp as A
+    with pytest.raises(A.ApspError):
+        g.query_path(0, n + 3)
+    assert g.query_all_paths(5, 5) == [[5]]
+    assert g.query_all_paths(3, 7) == []
+    g.close()
+
+
+def test_full_size_paths_n8192_sampled():
+    # The benchmark graph (n = 8192, U[1, 1e6]): 128 sampled pairs, each path
+    # valid and as long as the oracle's dense Dijkstra distance.
+    n = 8192
+    W = synth.complete_digraph_i32(n, 1, 10**6, 2)
+    g = G(W, n + 256)
+    alive = np.ones(n, dtype=bool)
+    uv = pairs_of(n, 128, 8)
+    paths, lens = g.query_paths(uv, stride=64)
+    src = np.unique(uv[:, 0])
+    rows = O.dijkstra_rows(W, src)
+    at = {int(s): k for k, s in enumerate(src)}
+    for (u, v), q, L in zip(uv, paths, lens):
+        assert 1 <= L <= 64
+        got = [int(x) for x in q[:L]]
+        check_valid(got, int(u), int(v), W, alive, rows[at[int(u)], v])
+    g.close()

@@ -41,7 +41,7 @@ WORKLOAD = "n=8192 directed complete graph, int32 weights U[1,1e6], mixed update
 SWEEP_KERNELS = ("insert_reduce", "insert_relax", "detect_remove")
 # DRAM bytes (read + write) per launch of each sweep, from the ncu captures
 # summarised in profiles/traffic_sweeps_n8192.md (mean of two launches)
-SWEEP_TRAFFIC = {"insert_reduce": 271.32e6, "insert_relax": 274.83e6, "detect_remove": 274.49e6}
+SWEEP_TRAFFIC = {"insert_reduce": 272.19e6, "insert_relax": 274.83e6, "detect_remove": 274.49e6}
 
 
 def peaks():
@@ -186,7 +186,8 @@ def run_reference(args):
 def run_case(case: str):
     """The workload's graph plus a few fixed updates, for profiler captures:
     "removals" removes nodes 7115 (about 5k affected pairs) and 5533 (about
-    284k), "inserts" adds two nodes with the workload's weight distribution."""
+    284k), "inserts" adds two nodes with the workload's weight distribution,
+    "paths" answers two batches of 4096 uniform path queries (Algorithm 7)."""
     import torch
     from paper_2412_15122_gb300 import Graph, build
     build.build()
@@ -199,6 +200,11 @@ def run_case(case: str):
             st = g.stats()
             print(json.dumps({"op": "remove", "node": k, "pairs": st["affected_pairs"], "rows": st["affected_rows"],
                               "passes": st["passes"], "warm_us": st["warm_total_us"]}))
+    elif case == "paths":
+        uv = np.stack([synth.uniform_int(SEED, 80, 4096, 0, N - 1), synth.uniform_int(SEED, 81, 4096, 0, N - 1)], 1)
+        for _ in range(2):
+            _, lens = g.query_paths(uv.astype(np.int32), stride=64)
+        print(json.dumps({"op": "paths", "queries": 4096, "mean_nodes": float(np.mean(lens))}))
     else:
         for t in range(2):
             iw = synth.uniform_int(SEED, 60 + t, CAP, W_LO, W_HI).astype(np.int32)
@@ -468,20 +474,32 @@ def run_batch_study(args):
     for dtype in ("i32", "f32"):
         specs, items = _batch_workload(args.study_graphs, per, dtype, 40 if dtype == "i32" else 41)
         n_upd = sum(len(x) for x in items)
-        # (a) batched
-        G = [Graph(W, cap) for W, cap in specs]
-        for g in G:
-            g.sync()
-        b = Batch()
         flat = [it for its in items for it in its]
-        # warm-up of the executor's buffers on a copy of the first graph
-        gw = Graph(specs[0][0], specs[0][1])
-        b.run([gw], items[0])
-        gw.close()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        b.run(G, flat)
-        batch_s = time.perf_counter() - t0
+        # (a) batched: one persistent launch (a replayed CUDA graph), timed for
+        # each CTA width on fresh copies of the graphs; the fastest is kept
+        per_width = {}
+        G = None
+        for width in (128, 256, 512):
+            if G is not None:
+                for g in G:
+                    g.close()
+            G = [Graph(W, cap) for W, cap in specs]
+            for g in G:
+                g.sync()
+            b = Batch()
+            b.set_width(width)
+            # warm-up: capture the executor's graph on a copy of the first graph
+            gw = Graph(specs[0][0], specs[0][1])
+            b.run([gw], items[0])
+            gw.close()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.run(G, flat)
+            per_width[width] = time.perf_counter() - t0
+            binfo = b.info()
+            b.close()
+        best_w = min(per_width, key=per_width.get)
+        batch_s = per_width[best_w]
         # (b) one call per update
         S = [Graph(W, cap) for W, cap in specs]
         for g in S:
@@ -519,8 +537,9 @@ def run_batch_study(args):
         cold_s = time.perf_counter() - t0
         for g in G + S:
             g.close()
-        b.close()
         out[dtype] = {"updates": n_upd, "batched_seconds": batch_s, "batched_updates_per_s": n_upd / batch_s,
+                      "batched_seconds_per_width": per_width, "best_width": best_w,
+                      "graph_replays_last_executor": binfo["graph_replays"],
                       "single_call_seconds": single_s, "single_call_updates_per_s": n_upd / single_s,
                       "cold_fw_all_graphs_seconds": cold_s,
                       ("mismatched_entries" if dtype == "i32" else "max_rel_diff"): worst}
@@ -752,7 +771,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--no-stats", action="store_true")
-    ap.add_argument("--case", choices=["removals", "inserts"],
+    ap.add_argument("--case", choices=["removals", "inserts", "paths"],
                     help="run a small fixed case of the workload (for profiler captures) and exit")
     ap.add_argument("--study-graphs", type=int, default=512)
     ap.add_argument("--serve-per-size", type=int, default=16)
@@ -945,6 +964,16 @@ def main():
                     "bytes_per_launch": bytes_per_launch, "launches": nl,
                     "avg_launch_us": 1000 * tot_ms / nl}
 
+    # cold FW against the CUDA cores' measured min-plus issue rate (ALU bound)
+    fw_roofline = None
+    if cold_ms:
+        peak_ops = A.apsp_probe_addmin_rate(A.APSP_I32)
+        fw_ops = float(span) ** 3 / (cold_ms / 1000.0)
+        fw_roofline = {"bound": "alu", "kernel": "fw_phase1/2/3", "achieved": fw_ops / 1e9, "peak": peak_ops / 1e9,
+                       "unit": "Gpair-op/s", "frac": fw_ops / peak_ops,
+                       "peak_kind": "measured: register-tile probe of min(a + b, c), int32 (apsp_probe_addmin_rate)",
+                       "work": "span^3 add-min pairs"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, dt = cpu_oracle_rate(W, args.cpu_rows)
@@ -967,6 +996,7 @@ def main():
             "clocks": clk.summary(),
             "gpu_launches": gpu_launches,
             "cold_fw_ms": cold_ms,
+            "cold_fw_roofline": fw_roofline,
             "profiled_pass_ms": prof_ms,
             "update_stats": stats,
             "warm_updates_per_cold_fw": value * cold_ms / 1000.0,

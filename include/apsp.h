@@ -319,6 +319,26 @@ apsp_status apsp_batch_create(apsp_batch **b, void *cuda_stream);
 apsp_status apsp_batch_run(apsp_batch *b, apsp_graph *const *graphs, int32_t n_graphs, const apsp_batch_item *items,
                            int32_t count, int32_t *new_ids);
 apsp_status apsp_batch_destroy(apsp_batch *b);
+/* Each launch is one CUDA graph (upload, persistent kernel, status
+ * read-back), captured once per dtype and CTA width on the executor and then
+ * replayed with updated parameters.  The CTA width (128, 256 or 512 threads)
+ * is chosen by a process-wide autotuner per dtype and size bucket
+ * (ceil(log2) of the batch's widest span): each width runs two batches of at
+ * least 2^20 span^2 of work, then the one with the least device time per
+ * span^2 is kept.  Widths never change results.  threads = 0 restores the
+ * autotuner; 128 / 256 / 512 fixes the width for this executor. */
+apsp_status apsp_batch_set_width(apsp_batch *b, int32_t threads);
+typedef struct {
+    int64_t launches;         /* batches launched */
+    int64_t graph_captures;   /* CUDA graphs captured */
+    int64_t graph_replays;    /* launches that replayed a captured graph */
+    int32_t last_width;       /* CTA width of the last launch */
+    int32_t fixed_width;      /* 0 when the autotuner chooses */
+} apsp_batch_info;
+apsp_status apsp_batch_info_get(apsp_batch *b, apsp_batch_info *info);
+/* The autotuner's settled width for batches whose widest span is max_span (0
+ * while it is still measuring). */
+apsp_status apsp_batch_tuned_width(apsp_dtype dtype, int32_t max_span, int32_t *threads);
 
 /* ----- serving loop ---------------------------------------------------------
  * Replays a trace of timed requests against resident graphs in real time with
@@ -371,6 +391,13 @@ typedef struct {
 /* Waits, then copies up to cap entries; *count = number of distinct kernels. */
 apsp_status apsp_profile_read(apsp_graph *g, apsp_profile_entry *out, int32_t cap, int32_t *count);
 apsp_status apsp_profile_reset(apsp_graph *g);
+
+/* Measures, on the current CUDA device, how many min-plus steps min(a + b, c)
+ * of the given dtype the CUDA cores issue per second when every thread keeps
+ * an 8 x 8 register tile of them (the inner loop of the cold Floyd-Warshall)
+ * and touches no memory: the ceiling against which the cold path's n^3 steps
+ * are reported.  Takes a few milliseconds; waits for the device. */
+apsp_status apsp_probe_addmin_rate(apsp_dtype dtype, double *pair_ops_per_s);
 
 /* ----- insertion without allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that

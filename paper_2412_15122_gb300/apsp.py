@@ -75,6 +75,11 @@ class apsp_serve_config(ctypes.Structure):
                 ("max_wave_requests", ctypes.c_int32)]
 
 
+class apsp_batch_info(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("graph_captures", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("last_width", ctypes.c_int32), ("fixed_width", ctypes.c_int32)]
+
+
 class apsp_info(ctypes.Structure):
     _fields_ = [("n_live", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("capacity", ctypes.c_int32),
                 ("ld", ctypes.c_int32), ("dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
@@ -113,6 +118,7 @@ def _load():
         "apsp_query_paths": [P, P, I32, P, I32, P],
         "apsp_query_path": [P, I32, I32, P, I32, ctypes.POINTER(I32)],
         "apsp_query_all_paths": [P, I32, I32, P, I64, P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64)],
+        "apsp_probe_addmin_rate": [I32, ctypes.POINTER(ctypes.c_double)],
         "apsp_copy_D": [P, P, I64, I32],
         "apsp_copy_W": [P, P, I64, I32],
         "apsp_copy_alive": [P, P],
@@ -127,6 +133,9 @@ def _load():
         "apsp_batch_create": [ctypes.POINTER(P), P],
         "apsp_batch_run": [P, ctypes.POINTER(P), I32, ctypes.POINTER(apsp_batch_item), I32, ctypes.POINTER(I32)],
         "apsp_batch_destroy": [P],
+        "apsp_batch_set_width": [P, I32],
+        "apsp_batch_info_get": [P, ctypes.POINTER(apsp_batch_info)],
+        "apsp_batch_tuned_width": [I32, I32, ctypes.POINTER(I32)],
         "apsp_serve": [ctypes.POINTER(P), I32, ctypes.POINTER(apsp_request), I32, ctypes.POINTER(apsp_serve_config),
                        ctypes.POINTER(apsp_request_result)],
         "apsp_set_model": [P, P],
@@ -289,6 +298,13 @@ def apsp_query_all_paths(g: int, u: int, v: int) -> list:
     return [[int(x) for x in nodes[offs[p]:offs[p + 1]]] for p in range(npaths.value)]
 
 
+def apsp_probe_addmin_rate(dtype: int) -> float:
+    """Min-plus steps per second of the CUDA cores (register-tile probe, current device)."""
+    r = ctypes.c_double()
+    _check(_load().apsp_probe_addmin_rate(dtype, ctypes.byref(r)), "apsp_probe_addmin_rate")
+    return r.value
+
+
 def apsp_copy_D(g: int, dst, ld: int, on_device: bool):
     _check(_load().apsp_copy_D(g, _ptr(dst), ld, 1 if on_device else 0), "apsp_copy_D")
 
@@ -382,6 +398,22 @@ def apsp_batch_destroy(b: int):
     _check(_load().apsp_batch_destroy(b), "apsp_batch_destroy")
 
 
+def apsp_batch_set_width(b: int, threads: int):
+    _check(_load().apsp_batch_set_width(b, threads), "apsp_batch_set_width")
+
+
+def apsp_batch_info_get(b: int) -> dict:
+    i = apsp_batch_info()
+    _check(_load().apsp_batch_info_get(b, ctypes.byref(i)), "apsp_batch_info_get")
+    return {k: getattr(i, k) for k, _ in i._fields_}
+
+
+def apsp_batch_tuned_width(dtype: int, max_span: int) -> int:
+    t = ctypes.c_int32()
+    _check(_load().apsp_batch_tuned_width(dtype, max_span, ctypes.byref(t)), "apsp_batch_tuned_width")
+    return t.value
+
+
 def apsp_batch_run(b: int, graphs: Sequence[int], items) -> np.ndarray:
     """items: sequence of (graph index, op, ...): ("add", in_w, out_w), ("remove", u)
     or ("edge", u, v, w).  Returns the new slot of every add (-1 elsewhere)."""
@@ -440,6 +472,12 @@ class Batch:
 
     def run(self, graphs, items) -> np.ndarray:
         return apsp_batch_run(self.h, [g.h for g in graphs], items)
+
+    def set_width(self, threads: int):
+        apsp_batch_set_width(self.h, threads)
+
+    def info(self) -> dict:
+        return apsp_batch_info_get(self.h)
 
     def close(self):
         if self.h:

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libapsp_gb300.so")
-UNITS = ["graph.cu", "kern_i32.cu", "kern_f32.cu", "mlp_train.cu", "noalloc.cu"]
+UNITS = ["graph.cu", "kern_i32.cu", "kern_f32.cu", "mlp_train.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

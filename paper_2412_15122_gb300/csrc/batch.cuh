@@ -376,7 +376,10 @@ __device__ __noinline__ bool b_remove(const BG<T> &g, int k, int span, uint32_t 
     return b_relax(g, mask, words, span, rows, nrows);
 }
 
-template <typename T> __global__ void __launch_bounds__(256, 3) k_batch(BatchHeader *hdr) {
+// Widths (threads per CTA) the executor's autotuner chooses from.
+constexpr int BATCH_WIDTHS[3] = {128, 256, 512};
+
+template <typename T, int NT> __global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int gi_s, nrows_s;
     const T *vecs = reinterpret_cast<const T *>(hdr->vecs);

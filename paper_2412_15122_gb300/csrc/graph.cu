@@ -16,6 +16,7 @@
 #include <limits>
 #include <new>
 #include <map>
+#include <mutex>
 #include <set>
 #include <string>
 #include <vector>
@@ -1053,6 +1054,23 @@ struct apsp_batch {
     size_t d_cap = 0;
     uint32_t *d_mask = nullptr;   // listed-pair bitmasks
     size_t mask_cap = 0;          // words
+    // One CUDA graph per (dtype, CTA width) holding a whole launch: the
+    // upload, the persistent kernel and the status read-back.  Later launches
+    // of the same kind only update the three nodes' parameters (sizes,
+    // pointers, grid, shared memory) and replay it.
+    struct Captured {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t h2d = nullptr, kern = nullptr, d2h = nullptr;
+        void *func = nullptr;
+    };
+    Captured cap[2][3];
+    int nt_fixed = 0;             // 0: the autotuner picks the CTA width
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int pend_dtype = -1, pend_bucket = -1, pend_k = -1;   // launch awaiting its time for the autotuner
+    double pend_work = 0.0;
+    int64_t launches = 0, captures = 0, replays = 0;
+    int last_nt = 0;
 };
 
 namespace {
@@ -1080,6 +1098,127 @@ template <typename T> int32_t bits_of(T v) {
     int32_t b;
     std::memcpy(&b, &v, sizeof(b));
     return b;
+}
+
+// ---- autotuner of the batched kernel's CTA width -------------------------
+// Process-wide table per (dtype, log2 of the batch's widest span).  Results
+// never depend on the width, so tuning runs on live batches: each width is
+// used for TUNE_SAMPLES batches of enough work, the cost of a batch being its
+// device time per span^2 summed over its updates, and the cheapest mean wins
+// and is kept for the rest of the process.
+constexpr int TUNE_SAMPLES = 2;
+constexpr double TUNE_MIN_WORK = 1 << 20;
+struct TuneCell {
+    double cost[3] = {0, 0, 0};
+    int n[3] = {0, 0, 0};
+    int chosen = -1;
+};
+std::mutex g_tune_mu;
+TuneCell g_tune[2][32];
+
+int tune_bucket(int max_span) {
+    int b = 0;
+    while ((1 << b) < max_span && b < 31) ++b;
+    return b;
+}
+
+int tune_pick(int dtype, int bucket) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneCell &c = g_tune[dtype][bucket];
+    if (c.chosen >= 0) return c.chosen;
+    for (int k = 0; k < 3; ++k)
+        if (c.n[k] < TUNE_SAMPLES) return k;
+    int best = 0;
+    for (int k = 1; k < 3; ++k)
+        if (c.cost[k] / c.n[k] < c.cost[best] / c.n[best]) best = k;
+    c.chosen = best;
+    return best;
+}
+
+void tune_record(int dtype, int bucket, int k, double cost) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneCell &c = g_tune[dtype][bucket];
+    if (c.chosen >= 0 || c.n[k] >= TUNE_SAMPLES) return;
+    c.cost[k] += cost;
+    c.n[k]++;
+}
+
+// Captures one launch (upload, kernel, read-back) as a CUDA graph.
+template <typename T>
+cudaError_t batch_capture(apsp_batch *b, apsp_batch::Captured &cp, size_t total, size_t o_tab, size_t tab_bytes,
+                          int grid, size_t smem, int nt) {
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaMemcpyAsync(b->d_blob, b->h_blob, total, cudaMemcpyHostToDevice, b->stream);
+    apsp::run_batch<T>(b->stream, reinterpret_cast<apsp::BatchHeader *>(b->d_blob), grid, smem, nt);
+    cudaMemcpyAsync(b->h_blob + o_tab, b->d_blob + o_tab, tab_bytes, cudaMemcpyDeviceToHost, b->stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t nodes[8];
+    size_t num = 8;
+    if ((e = cudaGraphGetNodes(graph, nodes, &num)) != cudaSuccess || num != 3) {
+        cudaGraphDestroy(graph);
+        return e != cudaSuccess ? e : cudaErrorStreamCaptureInvalidated;
+    }
+    for (size_t k = 0; k < num; ++k) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nodes[k], &t);
+        if (t == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams kp{};
+            cudaGraphKernelNodeGetParams(nodes[k], &kp);
+            cp.kern = nodes[k];
+            cp.func = kp.func;
+        } else if (t == cudaGraphNodeTypeMemcpy) {
+            cudaMemcpy3DParms mp{};
+            cudaGraphMemcpyNodeGetParams(nodes[k], &mp);
+            if (mp.srcPtr.ptr == b->h_blob) cp.h2d = nodes[k];
+            else cp.d2h = nodes[k];
+        }
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (!cp.kern || !cp.h2d || !cp.d2h || (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return e != cudaSuccess ? e : cudaErrorStreamCaptureInvalidated;
+    }
+    cp.graph = graph;
+    cp.exec = exec;
+    b->captures++;
+    return cudaSuccess;
+}
+
+// Enqueues one launch: replays the captured graph of this (dtype, width)
+// with updated parameters, capturing it first if needed.
+template <typename T>
+cudaError_t batch_enqueue(apsp_batch *b, size_t total, size_t o_tab, size_t tab_bytes, int grid, size_t smem, int nt,
+                          int k) {
+    const int dt = std::is_same<T, float>::value ? 1 : 0;
+    apsp_batch::Captured &cp = b->cap[dt][k];
+    cudaError_t e;
+    if (!cp.exec) {
+        if ((e = batch_capture<T>(b, cp, total, o_tab, tab_bytes, grid, smem, nt)) != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+    }
+    if ((e = cudaGraphExecMemcpyNodeSetParams1D(cp.exec, cp.h2d, b->d_blob, b->h_blob, total,
+                                                cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    apsp::BatchHeader *dh = reinterpret_cast<apsp::BatchHeader *>(b->d_blob);
+    void *args[] = {&dh};
+    cudaKernelNodeParams kp{};
+    kp.func = cp.func;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(nt);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    if ((e = cudaGraphExecKernelNodeSetParams(cp.exec, cp.kern, &kp)) != cudaSuccess) return e;
+    if ((e = cudaGraphExecMemcpyNodeSetParams1D(cp.exec, cp.d2h, b->h_blob + o_tab, b->d_blob + o_tab, tab_bytes,
+                                                cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    if ((e = cudaGraphLaunch(cp.exec, b->stream)) != cudaSuccess) return e;
+    b->replays++;
+    return cudaSuccess;
 }
 
 // Validates, resolves and launches the batch on b->stream without waiting;
@@ -1276,20 +1415,46 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
     std::memcpy(b->h_blob + o_tab, table.data(), table.size() * sizeof(BatchGraph));
     if (!ops.empty()) std::memcpy(b->h_blob + o_ops, ops.data(), ops.size() * sizeof(BatchOp));
     if (!vecs.empty()) std::memcpy(b->h_blob + o_vec, vecs.data(), vecs.size() * sizeof(T));
-    cudaError_t e = cudaMemcpyAsync(b->d_blob, b->h_blob, total, cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+    // CTA width: fixed by the caller, else the autotuner's choice for this size
+    const int dt = std::is_same<T, float>::value ? 1 : 0;
+    const int bucket = tune_bucket(max_span);
+    int k = 1;
+    if (b->nt_fixed) k = b->nt_fixed == 128 ? 0 : b->nt_fixed == 512 ? 2 : 1;
+    else k = tune_pick(dt, bucket);
+    const int nt = apsp::BATCH_WIDTHS[k];
     const size_t smem = (size_t)max_span * (4 * sizeof(T) + sizeof(int32_t));
+    cudaError_t e;
     int per_sm = 0, dev = 0, sms = 1;
-    if ((e = apsp::batch_occupancy<T>(smem, &per_sm)) != cudaSuccess) return cuda_status(e);
+    if ((e = apsp::batch_occupancy<T>(smem, nt, &per_sm)) != cudaSuccess) return cuda_status(e);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(n_graphs, std::max(1, per_sm) * sms));
-    if ((e = apsp::run_batch<T>(b->stream, reinterpret_cast<BatchHeader *>(b->d_blob), grid, smem)) != cudaSuccess)
-        return cuda_status(e);
-    // statuses back (the graph table is re-read after the kernel)
-    e = cudaMemcpyAsync(b->h_blob + o_tab, b->d_blob + o_tab, table.size() * sizeof(BatchGraph), cudaMemcpyDeviceToHost,
-                        b->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+    const size_t tab_bytes = table.size() * sizeof(BatchGraph);
+    double work = 0.0;
+    for (const BatchOp &op : ops) work += (double)op.span * op.span;
+    if (!b->ev0) {
+        cudaEventCreate(&b->ev0);
+        cudaEventCreate(&b->ev1);
+    }
+    cudaEventRecord(b->ev0, b->stream);
+    if (batch_enqueue<T>(b, total, o_tab, tab_bytes, grid, smem, nt, k) != cudaSuccess) {
+        // no graph (for example a stream that cannot be captured): plain launches
+        if ((e = cudaMemcpyAsync(b->d_blob, b->h_blob, total, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+            return cuda_status(e);
+        if ((e = apsp::run_batch<T>(b->stream, reinterpret_cast<BatchHeader *>(b->d_blob), grid, smem, nt)) !=
+            cudaSuccess)
+            return cuda_status(e);
+        // statuses back (the graph table is re-read after the kernel)
+        e = cudaMemcpyAsync(b->h_blob + o_tab, b->d_blob + o_tab, tab_bytes, cudaMemcpyDeviceToHost, b->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaEventRecord(b->ev1, b->stream);
+    b->launches++;
+    b->last_nt = nt;
+    b->pend_dtype = (!b->nt_fixed && work >= TUNE_MIN_WORK) ? dt : -1;
+    b->pend_bucket = bucket;
+    b->pend_k = k;
+    b->pend_work = work;
     b->o_tab = o_tab;
     b->n_graphs = n_graphs;
     return APSP_OK;
@@ -1299,6 +1464,12 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
 apsp_status batch_finish(apsp_batch *b) {
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    if (b->pend_dtype >= 0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess && ms > 0.f)
+            tune_record(b->pend_dtype, b->pend_bucket, b->pend_k, ms / b->pend_work);
+        b->pend_dtype = -1;
+    }
     const apsp::BatchGraph *done = reinterpret_cast<const apsp::BatchGraph *>(b->h_blob + b->o_tab);
     for (int gi = 0; gi < b->n_graphs; ++gi)
         if (done[gi].status) return APSP_E_TIMEOUT;
@@ -1340,8 +1511,39 @@ apsp_status apsp_batch_destroy(apsp_batch *b) {
     if (b->d_blob) cudaFree(b->d_blob);
     if (b->d_mask) cudaFree(b->d_mask);
     if (b->h_done) cudaFreeHost(b->h_done);
+    for (auto &row : b->cap)
+        for (auto &cp : row) {
+            if (cp.exec) cudaGraphExecDestroy(cp.exec);
+            if (cp.graph) cudaGraphDestroy(cp.graph);
+        }
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
+    return APSP_OK;
+}
+
+apsp_status apsp_batch_set_width(apsp_batch *b, int32_t threads) {
+    if (!b || (threads != 0 && threads != 128 && threads != 256 && threads != 512)) return APSP_E_ARG;
+    b->nt_fixed = threads;
+    return APSP_OK;
+}
+
+apsp_status apsp_batch_info_get(apsp_batch *b, apsp_batch_info *info) {
+    if (!b || !info) return APSP_E_ARG;
+    info->launches = b->launches;
+    info->graph_captures = b->captures;
+    info->graph_replays = b->replays;
+    info->last_width = b->last_nt;
+    info->fixed_width = b->nt_fixed;
+    return APSP_OK;
+}
+
+apsp_status apsp_batch_tuned_width(apsp_dtype dtype, int32_t max_span, int32_t *threads) {
+    if (!threads || (dtype != APSP_I32 && dtype != APSP_F32) || max_span < 1) return APSP_E_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const TuneCell &c = g_tune[dtype == APSP_F32 ? 1 : 0][tune_bucket(max_span)];
+    *threads = c.chosen >= 0 ? apsp::BATCH_WIDTHS[c.chosen] : 0;
     return APSP_OK;
 }
 

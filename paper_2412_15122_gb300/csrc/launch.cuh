@@ -228,15 +228,25 @@ template <typename T> cudaError_t run_path_query(const LaunchCtx &c, const Dev<T
 }
 
 // One persistent launch for a whole batch of graphs (batch.cuh).
-template <typename T> cudaError_t run_batch(cudaStream_t s, BatchHeader *hdr, int grid, size_t smem) {
-    k_batch<T><<<grid, 256, smem, s>>>(hdr);
+template <typename T> cudaError_t run_batch(cudaStream_t s, BatchHeader *hdr, int grid, size_t smem, int nt) {
+    if (nt == 128) k_batch<T, 128><<<grid, 128, smem, s>>>(hdr);
+    else if (nt == 512) k_batch<T, 512><<<grid, 512, smem, s>>>(hdr);
+    else k_batch<T, 256><<<grid, 256, smem, s>>>(hdr);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t batch_occupancy(size_t smem, int *per_sm) {
-    cudaError_t e = allow_max_smem(k_batch<T>);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T>, 256, smem);
+template <typename T> cudaError_t batch_occupancy(size_t smem, int nt, int *per_sm) {
+    cudaError_t e;
+    if (nt == 128) {
+        if ((e = allow_max_smem(k_batch<T, 128>)) != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T, 128>, 128, smem);
+    }
+    if (nt == 512) {
+        if ((e = allow_max_smem(k_batch<T, 512>)) != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T, 512>, 512, smem);
+    }
+    if ((e = allow_max_smem(k_batch<T, 256>)) != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T, 256>, 256, smem);
 }
 
 #define APSP_INSTANTIATE(T)                                                                                   \
@@ -251,7 +261,7 @@ template <typename T> cudaError_t batch_occupancy(size_t smem, int *per_sm) {
     template cudaError_t run_repair<T>(const LaunchCtx &, const Dev<T> &, const RepairCfg &);                 \
     template cudaError_t run_path_query<T>(const LaunchCtx &, const Dev<T> &, const PathQuery &, bool);       \
     template cudaError_t setup_shapes<T>(LaunchCtx &, int64_t, int);                                          \
-    template cudaError_t run_batch<T>(cudaStream_t, BatchHeader *, int, size_t);                              \
-    template cudaError_t batch_occupancy<T>(size_t, int *);
+    template cudaError_t run_batch<T>(cudaStream_t, BatchHeader *, int, size_t, int);                         \
+    template cudaError_t batch_occupancy<T>(size_t, int, int *);
 
 }  // namespace apsp

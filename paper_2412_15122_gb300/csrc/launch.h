@@ -37,7 +37,7 @@ template <typename T> cudaError_t run_increase(const LaunchCtx &, const Dev<T> &
 template <typename T> cudaError_t run_repair(const LaunchCtx &, const Dev<T> &, const RepairCfg &);
 template <typename T> cudaError_t run_path_query(const LaunchCtx &, const Dev<T> &, const PathQuery &, bool);
 template <typename T> cudaError_t setup_shapes(LaunchCtx &, int64_t, int);
-template <typename T> cudaError_t run_batch(cudaStream_t, BatchHeader *, int, size_t);
-template <typename T> cudaError_t batch_occupancy(size_t, int *);
+template <typename T> cudaError_t run_batch(cudaStream_t, BatchHeader *, int, size_t, int);
+template <typename T> cudaError_t batch_occupancy(size_t, int, int *);
 
 }  // namespace apsp

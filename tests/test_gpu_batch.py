@@ -163,3 +163,74 @@ def test_batch_then_single_calls_continue(lib):
     np.testing.assert_array_equal(g.D()[np.ix_(live, live)], ref[np.ix_(live, live)])
     b.close()
     g.close()
+
+
+def _workload(seed, sizes, per):
+    """Graphs of the given sizes with `per` mixed updates each (int32 U[1, 1000])."""
+    specs, items = [], []
+    for gi, n in enumerate(sizes):
+        cap = n + 24
+        W, ups = _graph_and_updates(n, cap, seed + gi, per, "i32", False)
+        Wm = np.full((cap, cap), synth.INF_I32, np.int32)
+        Wm[:n, :n] = W
+        alive = np.zeros(cap, bool)
+        alive[:n] = True
+        specs.append((W, cap))
+        items += _items_for(gi, ups, Wm, alive, cap, "i32")
+    return specs, items
+
+
+def test_batch_widths_give_identical_results_and_replay_graphs(lib):
+    # Every CTA width gives the same int32 matrices; repeated launches of one
+    # executor replay its captured CUDA graph with new parameters.
+    from paper_2412_15122_gb300 import Batch, Graph
+    specs, items = _workload(300, [70, 129, 200], 12)
+    ref = None
+    for width in (128, 256, 512):
+        graphs = [Graph(W, cap) for W, cap in specs]
+        b = Batch()
+        b.set_width(width)
+        half = len(items) // 2
+        first = [it for it in items[:half]]
+        b.run(graphs, first)
+        b.run(graphs, items[half:])
+        info = b.info()
+        assert info["launches"] == 2 and info["graph_captures"] == 1 and info["graph_replays"] == 2
+        assert info["last_width"] == width and info["fixed_width"] == width
+        Ds = [g.D() for g in graphs]
+        if ref is None:
+            ref = Ds
+        else:
+            for a, c in zip(ref, Ds):
+                np.testing.assert_array_equal(a, c)
+        for g in graphs:
+            g.close()
+        b.close()
+
+
+def test_batch_autotuner_settles_on_a_width(lib):
+    # Batches of enough work (>= 2^20 span^2) in one size bucket: after two
+    # samples of each width the tuner keeps one of them.
+    from paper_2412_15122_gb300 import Batch, Graph
+    from paper_2412_15122_gb300 import apsp as A
+    specs, items = _workload(400, [600, 700, 760, 640], 8)
+    graphs = [Graph(W, cap) for W, cap in specs]
+    Wm = [g.W() for g in graphs]
+    b = Batch()
+    settled_before = A.apsp_batch_tuned_width(A.APSP_I32, 784)
+    widths = []
+    for rep in range(8):
+        # the same edge items again (weights toggled back and forth) keep the work per batch alike
+        its = [it for it in items if it[1] == "edge"]
+        if rep % 2:
+            its = [(gi, "edge", u, v, float(Wm[gi][u, v])) for (gi, _, u, v, _) in its]
+        b.run(graphs, its)
+        widths.append(b.info()["last_width"])
+    tuned = A.apsp_batch_tuned_width(A.APSP_I32, 784)
+    assert tuned in (128, 256, 512)
+    if settled_before == 0:
+        assert set(widths[:6]) == {128, 256, 512}     # each width measured first
+    assert widths[-1] == tuned
+    for g in graphs:
+        g.close()
+    b.close()

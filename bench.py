@@ -594,7 +594,8 @@ def run_path_study(args):
             "kernel_read_gbs": algo_bytes / kern_s / 1e9 if kern_s > 0 else None,
             "kernel_read_frac_of_peak": (algo_bytes / kern_s / 1e9) / hbm if kern_s > 0 else None,
             "peak": f"{hbm} GB/s {peak_kind}", "single_query_us_p50": 1e6 * statistics.median(lat),
-            "mean_path_nodes": float(np.mean(lens)), "wide_pass_launches": prof.get("path_query_wide", (0, 0))[0]}
+            "mean_path_nodes": float(np.mean(lens)), "block_tier_launches": prof.get("path_query_block", (0, 0))[0],
+            "wide_tier_launches": prof.get("path_query_wide", (0, 0))[0]}
         g.close()
         torch.cuda.synchronize()
     # CPU oracle at n = 2048: Algorithm 7 vs dense Dijkstra per query

@@ -632,15 +632,17 @@ apsp_status pq_run(apsp_graph *g, const int32_t *uv, int nb, int mode, int strid
     q.wide_slots = S;
     const Dev<T> d = dev_of<T>(g);
     out_h.resize((size_t)nb * row);
-    for (int pass = 0; pass < 2; ++pass) {
-        if ((e = apsp::run_path_query<T>(g->lc, d, q, pass == 1)) != cudaSuccess) return cuda_status(e);
+    q.all = nb < g->lc.num_sms ? 1 : 0;
+    for (int tier = q.all ? 1 : 0; tier < 3; ++tier) {
+        if ((e = apsp::run_path_query<T>(g->lc, d, q, tier)) != cudaSuccess) return cuda_status(e);
         e = cudaMemcpyAsync(out_h.data(), g->pq_out, (size_t)nb * row * 4, cudaMemcpyDeviceToHost, g->stream);
         if (e != cudaSuccess) return cuda_status(e);
         apsp_status st = sync_ctl(g, nullptr);
         if (st != APSP_OK) return st;
+        const int32_t marker = tier == 0 ? apsp::PQ_DEFERRED : apsp::PQ_DEFERRED_WIDE;
         bool deferred = false;
-        for (int k = 0; k < nb && !deferred; ++k) deferred = out_h[(size_t)k * row] == apsp::PQ_DEFERRED;
-        if (!deferred) break;
+        for (int k = 0; k < nb && !deferred; ++k) deferred = out_h[(size_t)k * row] == marker;
+        if (!deferred || tier == 2) break;   // the next tier reads the markers from the device copy
     }
     for (int k = 0; k < nb; ++k)
         if (out_h[(size_t)k * row] < 0) return APSP_E_ARG;   // D is not the APSP matrix of W

@@ -1024,16 +1024,24 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
             for (int k = 0; k < CW; ++k)
                 if (lane + 32 * k < nv) cp_async16(rb + lane + 32 * k, r4 + lane + 32 * k);
             T pacc = M::inf();
-            for (int q = 0; q < cnt; ++q) {
-                const int jq = __shfl_sync(0xffffffffu, jl, q);
-                const V4 *c4 = reinterpret_cast<const V4 *>(cols + (int64_t)jq * ld + x0);
-                V4 a[CW];
+            // two pairs per step: both column slices (16 vectors a lane) are
+            // in flight before either is used
+            for (int q = 0; q < cnt; q += 2) {
+                const bool two = q + 1 < cnt;
+                const int ja = __shfl_sync(0xffffffffu, jl, q);
+                const int jb = __shfl_sync(0xffffffffu, jl, two ? q + 1 : q);
+                const V4 *ca = reinterpret_cast<const V4 *>(cols + (int64_t)ja * ld + x0);
+                const V4 *cb = reinterpret_cast<const V4 *>(cols + (int64_t)jb * ld + x0);
+                V4 a[CW], b[CW];
 #pragma unroll
                 for (int k = 0; k < CW; ++k)
-                    if (lane + 32 * k < nv) a[k] = __ldcg(c4 + lane + 32 * k);
-                cp_async_wait_all();   // the row slice (in flight with the first column)
+                    if (lane + 32 * k < nv) {
+                        a[k] = __ldcg(ca + lane + 32 * k);
+                        if (two) b[k] = __ldcg(cb + lane + 32 * k);
+                    }
+                cp_async_wait_all();   // the row slice (in flight with the first columns)
                 __syncwarp();
-                T acc = M::inf();
+                T acc = M::inf(), acc2 = M::inf();
 #pragma unroll
                 for (int k = 0; k < CW; ++k) {
                     if (lane + 32 * k < nv) {
@@ -1042,10 +1050,18 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
                         acc = M::add_min(r.y, a[k].y, acc);
                         acc = M::add_min(r.z, a[k].z, acc);
                         acc = M::add_min(r.w, a[k].w, acc);
+                        if (two) {
+                            acc2 = M::add_min(r.x, b[k].x, acc2);
+                            acc2 = M::add_min(r.y, b[k].y, acc2);
+                            acc2 = M::add_min(r.z, b[k].z, acc2);
+                            acc2 = M::add_min(r.w, b[k].w, acc2);
+                        }
                     }
                 }
                 acc = warp_min(acc);
+                acc2 = warp_min(acc2);
                 if (lane == q) pacc = acc;
+                if (two && lane == q + 1) pacc = acc2;
             }
             if (lane < cnt) atomicMin(d.pmin + item.y + lane, M::key(pacc));
             t = __shfl_sync(0xffffffffu, t, 0);
@@ -1265,7 +1281,7 @@ __device__ inline void repair_record(Ctl *ctl, int reason, float cost, float pw,
 
 // Warm repair (cooperative launch): restricted re-relaxation.
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_repair_warm(Dev<T> d, RepairCfg cfg) {
+__global__ void __launch_bounds__(256, 2) k_repair_warm(Dev<T> d, RepairCfg cfg) {
     float cost, pw, pc;
     int n_items;
     const int reason = repair_decide(d.ctl, cfg, &cost, &pw, &pc, &n_items);

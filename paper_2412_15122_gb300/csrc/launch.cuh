@@ -204,6 +204,12 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     c.detect2_grid = std::max(1, det2_sm) * c.num_sms;
     c.detunit_grid = 4 * c.num_sms;
     c.detalloc_grid = (int)((ld + 255) / 256);   // a lane per row: 256 rows a CTA
+    if ((e = allow_max_smem(k_path_warp<T>)) != cudaSuccess) return e;
+    int pw_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pw_sm, k_path_warp<T>, PW_WARPS * 32, pw_smem_bytes<T>())) !=
+        cudaSuccess)
+        return e;
+    c.pw_grid = std::max(1, pw_sm) * c.num_sms;
     int ir_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ir_sm, k_insert_reduce<T>, 256, 0)) != cudaSuccess) return e;
     c.insred_per_sm = std::max(1, ir_sm);
@@ -215,16 +221,22 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     return cudaSuccess;
 }
 
-// Path queries (paths.cuh): the shared-memory pass over every query, or the
-// pass of PQ_WIDE_GRID CTAs over the queries the first one deferred.
-template <typename T> cudaError_t run_path_query(const LaunchCtx &c, const Dev<T> &d, const PathQuery &q, bool wide) {
+// Path queries (paths.cuh), tier 0: a warp per query over every query;
+// tier 1: a CTA per query over those tier 0 deferred; tier 2: PQ_WIDE_GRID
+// CTAs over those tier 1 deferred.
+template <typename T> cudaError_t run_path_query(const LaunchCtx &c, const Dev<T> &d, const PathQuery &q, int tier) {
     if (q.count <= 0) return cudaSuccess;
-    if (wide)
+    if (tier == 2)
         return launch(c, "path_query_wide",
                       [&] { k_path_query<T, true><<<PQ_WIDE_GRID, PQ_THREADS, 0, c.stream>>>(d, q); });
-    const int grid = std::min(q.count, 4 * c.num_sms);
+    if (tier == 1) {
+        const int grid = std::min(q.count, 4 * c.num_sms);
+        return launch(c, "path_query_block",
+                      [&] { k_path_query<T, false><<<grid, PQ_THREADS, pq_smem_bytes<T>(), c.stream>>>(d, q); });
+    }
+    const int grid = std::max(1, std::min(cdiv(q.count, PW_WARPS), c.pw_grid));
     return launch(c, "path_query",
-                  [&] { k_path_query<T, false><<<grid, PQ_THREADS, pq_smem_bytes<T>(), c.stream>>>(d, q); });
+                  [&] { k_path_warp<T><<<grid, PW_WARPS * 32, pw_smem_bytes<T>(), c.stream>>>(d, q); });
 }
 
 // One persistent launch for a whole batch of graphs (batch.cuh).
@@ -259,7 +271,7 @@ template <typename T> cudaError_t batch_occupancy(size_t smem, int nt, int *per_
     template cudaError_t run_remove<T>(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);            \
     template cudaError_t run_increase<T>(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &); \
     template cudaError_t run_repair<T>(const LaunchCtx &, const Dev<T> &, const RepairCfg &);                 \
-    template cudaError_t run_path_query<T>(const LaunchCtx &, const Dev<T> &, const PathQuery &, bool);       \
+    template cudaError_t run_path_query<T>(const LaunchCtx &, const Dev<T> &, const PathQuery &, int);        \
     template cudaError_t setup_shapes<T>(LaunchCtx &, int64_t, int);                                          \
     template cudaError_t run_batch<T>(cudaStream_t, BatchHeader *, int, size_t, int);                         \
     template cudaError_t batch_occupancy<T>(size_t, int, int *);

@@ -24,6 +24,7 @@ struct LaunchCtx {
     int detunit_grid = 1;
     int detalloc_grid = 1;
     int insred_per_sm = 1;
+    int pw_grid = 1;
 };
 
 template <typename T> cudaError_t run_fill(const LaunchCtx &, T *, T, int64_t);
@@ -35,7 +36,7 @@ template <typename T> cudaError_t run_decrease(const LaunchCtx &, const Dev<T> &
 template <typename T> cudaError_t run_remove(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);
 template <typename T> cudaError_t run_increase(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &);
 template <typename T> cudaError_t run_repair(const LaunchCtx &, const Dev<T> &, const RepairCfg &);
-template <typename T> cudaError_t run_path_query(const LaunchCtx &, const Dev<T> &, const PathQuery &, bool);
+template <typename T> cudaError_t run_path_query(const LaunchCtx &, const Dev<T> &, const PathQuery &, int);
 template <typename T> cudaError_t setup_shapes(LaunchCtx &, int64_t, int);
 template <typename T> cudaError_t run_batch(cudaStream_t, BatchHeader *, int, size_t, int);
 template <typename T> cudaError_t batch_occupancy(size_t, int, int *);

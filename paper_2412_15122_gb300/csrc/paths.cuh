@@ -1,7 +1,15 @@
 // Warm-start path queries (Section 4): Algorithm 7 and the trees behind
 // Algorithm 8, on the device.
 //
-// One CTA per query (a grid-stride loop over a batch of queries):
+// Three tiers, by the number K of candidates a query turns out to have:
+//   warp tier   (K <= PW_K, nearly every query): one warp per query, no
+//               CTA-wide barrier anywhere, per-warp arrays in shared memory;
+//   block tier  (K <= PQ_KS): one CTA per query, as below;
+//   wide tier   (any K): PQ_WIDE_GRID CTAs, arrays in global scratch.
+// A tier that meets a larger K marks the query deferred and the next tier
+// (a later launch) redoes it.  Batches smaller than the SM count start at the
+// block tier, whose 512 threads read a query's rows with more loads in flight
+// than one warp.  The block tier, per query:
 //   1. candidate scan: the live nodes t other than i and j that are not
 //      excluded by the test SPD(i, j) < SPD(i, t) + SPD(t, j) (Algorithm 7;
 //      Theorem al_correct: every shortest i -> j path uses only them).  Row i
@@ -34,8 +42,12 @@ constexpr int PQ_THREADS = 512;
 constexpr int PQ_KS = 1024;
 constexpr int PQ_SK = 64;           // small graphs of up to PQ_SK nodes have their matrix staged in shared memory
 constexpr int PQ_WIDE_GRID = 4;
-constexpr int32_t PQ_DEFERRED = -2;
+constexpr int PW_K = 128;           // warp tier: candidates per query
+constexpr int PW_SK = 32;           // warp tier: small matrix staged when K <= PW_SK
+constexpr int PW_WARPS = 8;         // warp tier: warps per CTA
 constexpr int32_t PQ_BROKEN = -1;   // the small graph does not reach j: D is not the APSP matrix of W
+constexpr int32_t PQ_DEFERRED = -2; // for the block tier
+constexpr int32_t PQ_DEFERRED_WIDE = -3;   // for the wide tier
 
 struct PathQuery {
     const int32_t *uv;     // count (i, j) pairs, device
@@ -47,6 +59,7 @@ struct PathQuery {
     int32_t *wide;         // PQ_WIDE_GRID * wide_stride int32
     int64_t wide_stride;
     int wide_slots;        // candidates a wide CTA can hold (>= span + 2)
+    int all;               // block tier: answer every query (small batches start there), not only deferred ones
 };
 
 // Per-CTA arrays of one query.
@@ -199,12 +212,12 @@ __global__ void __launch_bounds__(PQ_THREADS) k_path_query(Dev<T> d, PathQuery q
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int qi = blockIdx.x; qi < q.count; qi += gridDim.x) {
         int32_t *o = q.out + (int64_t)qi * q.row;
-        if (WIDE) {
+        {   // only the queries the previous tier deferred
             if (threadIdx.x == 0) o0_s = o[0];
             __syncthreads();
             const int32_t o0 = o0_s;
             __syncthreads();
-            if (o0 != PQ_DEFERRED) continue;
+            if (!(WIDE ? o0 == PQ_DEFERRED_WIDE : (q.all || o0 == PQ_DEFERRED))) continue;
         }
         const int i = q.uv[2 * qi], j = q.uv[2 * qi + 1];
         if (i == j) {   // Algorithm 7: the path of a node to itself is [i]
@@ -227,7 +240,7 @@ __global__ void __launch_bounds__(PQ_THREADS) k_path_query(Dev<T> d, PathQuery q
         }
         const int K = pq_scan<T>(d, i, j, dij, A.cand, kcap, wtot) + 2;
         if (K > kcap) {
-            if (threadIdx.x == 0) o[0] = WIDE ? PQ_BROKEN : PQ_DEFERRED;
+            if (threadIdx.x == 0) o[0] = WIDE ? PQ_BROKEN : PQ_DEFERRED_WIDE;
             __syncthreads();
             continue;
         }
@@ -282,6 +295,141 @@ __global__ void __launch_bounds__(PQ_THREADS) k_path_query(Dev<T> d, PathQuery q
         __syncthreads();
     }
 }
+
+// Warp tier: one warp per query.
+template <typename T> struct PwWarpSmem {
+    int32_t cand[PW_K];
+    T fdist[PW_K], bdist[PW_K];
+    int32_t fpred[PW_K], bpred[PW_K];
+    uint8_t fdone[PW_K], bdone[PW_K];
+    T small[PW_SK * PW_SK];
+};
+
+template <typename T> __global__ void __launch_bounds__(PW_WARPS * 32) k_path_warp(Dev<T> d, PathQuery q) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    constexpr int B = 4;   // vectors of each row in flight per lane
+    extern __shared__ __align__(16) unsigned char pw_smem[];
+    PwWarpSmem<T> &S = reinterpret_cast<PwWarpSmem<T> *>(pw_smem)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * PW_WARPS;
+    const int nv = d.span >> 2;
+    for (int qi = blockIdx.x * PW_WARPS + (threadIdx.x >> 5); qi < q.count; qi += nwarps) {
+        int32_t *o = q.out + (int64_t)qi * q.row;
+        const int i = q.uv[2 * qi], j = q.uv[2 * qi + 1];
+        if (i == j) {   // Algorithm 7: the path of a node to itself is [i]
+            if (lane == 0) {
+                o[0] = 1;
+                if (q.mode == 0) {
+                    if (q.stride > 0) o[1] = i;
+                } else {
+                    o[1] = i;
+                    o[2] = -1;
+                    o[3] = -1;
+                }
+            }
+            continue;
+        }
+        const T dij = d.D[(int64_t)i * d.ld + j];
+        if (!M::finite(dij)) {   // unreachable: no path
+            if (lane == 0) o[0] = 0;
+            continue;
+        }
+        // Step 1, candidate scan in slot order.  Dead and never-used slots hold
+        // missing distances, so the test itself rejects them.
+        const V4 *ri = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+        const V4 *rj = reinterpret_cast<const V4 *>((d.DT ? d.DT : d.D) + (int64_t)j * d.ld);
+        int total = 0;
+        for (int base = 0; base < nv && total <= PW_K - 2; base += 32 * B) {
+            V4 a[B], c[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int v = base + 32 * b + lane;
+                if (v < nv) {
+                    a[b] = ri[v];
+                    c[b] = rj[v];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int v = base + 32 * b + lane;
+                unsigned m4 = 0;
+                if (v < nv) {
+                    const int t = v << 2;
+                    if (t != i && t != j && pq_keep<T>(a[b].x, c[b].x, dij)) m4 |= 1u;
+                    if (t + 1 != i && t + 1 != j && pq_keep<T>(a[b].y, c[b].y, dij)) m4 |= 2u;
+                    if (t + 2 != i && t + 2 != j && pq_keep<T>(a[b].z, c[b].z, dij)) m4 |= 4u;
+                    if (t + 3 != i && t + 3 != j && pq_keep<T>(a[b].w, c[b].w, dij)) m4 |= 8u;
+                }
+                int wsum;
+                int pos = 1 + total + warp_exclusive_scan(__popc(m4), &wsum);
+                while (m4) {
+                    const int e = __ffs(m4) - 1;
+                    m4 &= m4 - 1;
+                    if (pos < PW_K - 1) S.cand[pos] = (v << 2) + e;
+                    ++pos;
+                }
+                total += wsum;
+            }
+        }
+        const int K = total + 2;
+        if (K > PW_K) {
+            if (lane == 0) o[0] = PQ_DEFERRED;
+            __syncwarp();
+            continue;
+        }
+        if (lane == 0) {
+            S.cand[0] = i;
+            S.cand[K - 1] = j;
+        }
+        __syncwarp();
+        // Algorithm 7's small_matrix, staged when it fits
+        const T *small = nullptr;
+        if (K <= PW_SK) {
+            for (int e = lane; e < K * K; e += 32) {
+                const int a = e / K, b = e - a * K;
+                S.small[e] = d.W[(int64_t)S.cand[a] * d.ld + S.cand[b]];
+            }
+            __syncwarp();
+            small = S.small;
+        }
+        // Step 2
+        pq_dijkstra<T>(d, S.cand, K, 0, false, q.mode == 0, small, S.fdist, S.fpred, S.fdone);
+        if (q.mode == 1) pq_dijkstra<T>(d, S.cand, K, K - 1, true, false, small, S.bdist, S.bpred, S.bdone);
+        __syncwarp();
+        // Step 3
+        if (q.mode == 0) {
+            if (lane == 0) {
+                int L = 1, b = K - 1;
+                while (b != 0 && L <= K) {
+                    b = S.fpred[b];
+                    if (b < 0) break;
+                    ++L;
+                }
+                if (b != 0) {
+                    o[0] = PQ_BROKEN;
+                } else {
+                    o[0] = L;
+                    b = K - 1;
+                    for (int p = L - 1; p >= 0; --p) {
+                        if (p < q.stride) o[1 + p] = S.cand[b];
+                        b = S.fpred[b];
+                    }
+                }
+            }
+        } else {
+            for (int a = lane; a < K; a += 32) {
+                o[1 + a] = S.cand[a];
+                o[1 + K + a] = S.fpred[a];
+                o[1 + 2 * K + a] = S.bpred[a];
+            }
+            if (lane == 0) o[0] = K;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T> constexpr size_t pw_smem_bytes() { return PW_WARPS * sizeof(PwWarpSmem<T>); }
 
 template <typename T> constexpr size_t pq_smem_bytes() {
     return (size_t)PQ_KS * (3 * sizeof(int32_t) + 2 * sizeof(T) + 2) + (size_t)PQ_SK * PQ_SK * sizeof(T);

@@ -147,14 +147,15 @@ def test_paths_after_updates_avoid_dead_slots():
     g.close()
 
 
-def test_many_candidates_use_the_wide_pass():
+@pytest.mark.parametrize("n", [500, 1500])
+def test_many_candidates_use_the_later_tiers(n):
     # All weights zero: every node is on a shortest path, so K = n exceeds the
-    # shared-memory candidate capacity (1024) and the wide pass answers.
-    n = 1500
+    # warp tier's capacity (128); n = 500 is answered by the block tier, n =
+    # 1500 (above its 1024) by the wide tier.
     W = np.zeros((n, n), dtype=np.int32)
     g = G(W, n)
     alive = np.ones(n, dtype=bool)
-    uv = np.array([[0, n - 1], [700, 3], [n - 1, 0]], dtype=np.int32)
+    uv = np.array([[0, n - 1], [n // 2, 3], [n - 1, 0]], dtype=np.int32)
     paths, lens = g.query_paths(uv)
     for (u, v), q, L in zip(uv, paths, lens):
         got = [int(x) for x in q[:L]]

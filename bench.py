@@ -298,10 +298,11 @@ def run_dispatch_study(args):
     from paper_2412_15122_gb300 import apsp as A
     build.build()
     t_start = time.perf_counter()
+    arm_list = [a for a in args.study_arms.split(",") if a]
     sizes = (1024, 2048, 4096, 8192)
-    per = max(50, args.study_samples // (2 * len(sizes)))
+    per = max(50, args.study_samples // (2 * len(sizes))) if "model" in arm_list else 0
     X, Y = [], []
-    for euclid in (False, True):
+    for euclid in ((False, True) if per else ()):
         for n in sizes:
             seed = 300 + n + (1 if euclid else 0)
             if euclid:
@@ -344,17 +345,21 @@ def run_dispatch_study(args):
                 if got >= per:
                     break
             g.close()
-    X = np.asarray(X, np.float32)
-    Y = np.asarray(Y, np.float32)
-    order = np.argsort(synth.u64(7, 7, len(X)))
-    cut = int(0.8 * len(X))
-    tr, te = order[:cut], order[cut:]
-    t_train = time.perf_counter()
-    P, train_loss = A.apsp_model_train(X[tr], Y[tr], epochs=80, batch=256, lr=2e-3, seed=5)
-    train_s = time.perf_counter() - t_train
-    held_loss, _ = A.apsp_model_loss_grad(P, X[te], Y[te])
-    pred = A.apsp_model_predict(P, X[te])
-    acc = float(np.mean((pred[:, 0] <= pred[:, 1]) == (Y[te, 0] <= Y[te, 1])))
+    train_s = train_loss = held_loss = acc = None
+    P = None
+    tr = te = ()
+    if per:
+        X = np.asarray(X, np.float32)
+        Y = np.asarray(Y, np.float32)
+        order = np.argsort(synth.u64(7, 7, len(X)))
+        cut = int(0.8 * len(X))
+        tr, te = order[:cut], order[cut:]
+        t_train = time.perf_counter()
+        P, train_loss = A.apsp_model_train(X[tr], Y[tr], epochs=80, batch=256, lr=2e-3, seed=5)
+        train_s = time.perf_counter() - t_train
+        held_loss, _ = A.apsp_model_loss_grad(P, X[te], Y[te])
+        pred = A.apsp_model_predict(P, X[te])
+        acc = float(np.mean((pred[:, 0] <= pred[:, 1]) == (Y[te, 0] <= Y[te, 1])))
 
     # ---- the four arms on n = 16384 undirected Euclidean updates -------------
     n = 16384
@@ -363,7 +368,8 @@ def run_dispatch_study(args):
     ups = _euclid_stream(n, args.study_updates, 3, (0.1, 0.4, 0.1, 0.4), cap)
     arms = {}
     finals = {}
-    for arm in ("delta", "model", "warm", "cold"):
+    lists = {}
+    for arm in arm_list:
         tg = _Tracked(Graph, W, cap, True, pts0)
         g = tg.g
         if arm == "delta":
@@ -371,6 +377,13 @@ def run_dispatch_study(args):
         elif arm == "model":
             g.set_model(P)
             g.set_dispatch("model")
+        elif arm in ("warm_exact_list", "warm_direct_filter"):
+            # Experiment IV's question: how much of Corollary 3's list is
+            # Algorithm 12's (pairs whose distance really grows); and what the
+            # direct-edge filter keeps of it
+            g.set_dispatch("warm")
+            g.set_exact_list(True)
+            g.set_direct_edge_filter(arm == "warm_direct_filter")
         else:
             g.set_dispatch(arm)
         g.sync()
@@ -378,18 +391,27 @@ def run_dispatch_study(args):
         t0 = time.perf_counter()
         paths = {}
         for t, up in enumerate(ups):
-            tg.apply(up, 3, t)
+            kind = tg.apply(up, 3, t)[0]
             st = g.stats()
             paths[st["path"]] = paths.get(st["path"], 0) + 1
+            if arm.startswith("warm_") and kind in ("remove", "increase") and st["grown_pairs"] >= 0:
+                L = lists.setdefault(arm, {}).setdefault(kind, {"updates": 0, "listed_pairs": 0, "alg12_pairs": 0,
+                                                                "listed_rows": 0, "alg12_rows": 0})
+                L["updates"] += 1
+                L["listed_pairs"] += st["affected_pairs"]
+                L["alg12_pairs"] += st["grown_pairs"]
+                L["listed_rows"] += st["affected_rows"]
+                L["alg12_rows"] += st["grown_rows"]
         g.sync()
         arms[arm] = {"seconds": time.perf_counter() - t0, "paths": paths}
         finals[arm] = torch.from_numpy(g.D()).cuda()
         alive, Wf = tg.alive.copy(), tg.W
         g.close()
-    same = all(torch.equal(finals["warm"], finals[a]) for a in finals)
+    ref_arm = arm_list[0]
+    same = all(torch.equal(finals[ref_arm], finals[a]) for a in finals)
     # 64 sampled rows of the final matrix against the oracle's Dijkstra
     from oracle import apsp as O
-    Dw = finals["warm"].cpu().numpy()
+    Dw = finals[ref_arm].cpu().numpy()
     m = Dw.shape[0]
     live = np.flatnonzero(alive[:m])
     rows = live[synth.uniform_int(3, 77, 64, 0, len(live) - 1)]
@@ -402,7 +424,8 @@ def run_dispatch_study(args):
         "held_out_decision_accuracy": acc,
         "eval": {"workload": f"n={n} undirected Euclidean, {len(ups)} updates (10% add, 40% remove, "
                              "10% decrease, 40% increase on lightest out-edges)", "arms": arms,
-                 "identical_final_D": bool(same), "sampled_rows_match_oracle": ok_rows},
+                 "identical_final_D": bool(same), "sampled_rows_match_oracle": ok_rows,
+                 "affected_lists": lists},
         "wall_seconds": time.perf_counter() - t_start}))
 
 
@@ -782,6 +805,8 @@ def main():
                     help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
                          "always-warm and always-cold on n=16384 undirected Euclidean updates")
     ap.add_argument("--study-updates", type=int, default=100)
+    ap.add_argument("--study-arms", default="delta,model,warm,cold,warm_exact_list,warm_direct_filter",
+                    help="dispatch study: comma-separated arms to run")
     ap.add_argument("--study-samples", type=int, default=20000)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -122,6 +122,12 @@ typedef struct {
     int64_t pairs_rechecked;  /* pair evaluations in re-relaxation passes after the first */
     float warm_pass1_us;      /* device time of the first re-relaxation pass */
     float warm_total_us;      /* device time of the whole warm repair */
+    /* Algorithm 12's need_update_list (measured only after apsp_set_exact_list
+     * on; -1 otherwise or when the affected set overflowed): listed pairs whose
+     * distance grew, the rows holding them, and its Cost (rows / (N - 1)). */
+    int64_t grown_pairs;
+    int32_t grown_rows;
+    float grown_cost;
 } apsp_stats;
 
 typedef struct {
@@ -243,6 +249,27 @@ apsp_status apsp_sync(apsp_graph *g);
  * APSP_DISPATCH_DELTA with delta = 1.0, i.e. cold only when the affected set
  * overflows the scratch capacity). */
 apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta);
+
+/* Algorithm 12 (Theorem theo_algo12): the need_update_list of a removal is
+ * the set of Corollary 3's pairs whose distance actually grows (k needed by
+ * every shortest path), and likewise for an edge increase with the old edge.
+ * With `on`, each removal / increase also counts that list after its repair
+ * (one extra kernel over the listed pairs, comparing each final distance with
+ * its old tight sum) and apsp_last_stats reports grown_pairs / grown_rows /
+ * grown_cost.  int32: exact; fp32: "grew" beyond the 2^-16 tightness slack.
+ * The result of every update is the same either way. */
+apsp_status apsp_set_exact_list(apsp_graph *g, int32_t on);
+
+/* Direct-edge filter (a sufficient form of Algorithm 12's test).  With `on`,
+ * detection drops from Corollary 3's list every pair (i, j) whose direct edge
+ * is itself a shortest path (W[i][j] == D[i][j]): that edge avoids the
+ * removed node, and differs from an increased edge (whose weight is already
+ * the new one), so the pair keeps its distance and needs no re-relaxation.
+ * affected_pairs / affected_rows and Cost then count the filtered list (which
+ * still contains Algorithm 12's whole list).  Results are the same either way;
+ * it pays off on graphs where ties are common, such as Euclidean weights.
+ * Default off (the list is exactly Section 3.2's need_update_list). */
+apsp_status apsp_set_direct_edge_filter(apsp_graph *g, int32_t on);
 
 /* ----- learned warm/cold cost model ---------------------------------------
  * Algorithm 5 chooses between re-running the affected rows and recomputing

@@ -43,7 +43,8 @@ class apsp_stats(ctypes.Structure):
                 ("affected_pairs", ctypes.c_int64), ("sweep_rows", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("overflow", ctypes.c_int32), ("cold_reason", ctypes.c_int32), ("cost", ctypes.c_float),
                 ("model_warm", ctypes.c_float), ("model_cold", ctypes.c_float),
-                ("pairs_rechecked", ctypes.c_int64), ("warm_pass1_us", ctypes.c_float), ("warm_total_us", ctypes.c_float)]
+                ("pairs_rechecked", ctypes.c_int64), ("warm_pass1_us", ctypes.c_float), ("warm_total_us", ctypes.c_float),
+                ("grown_pairs", ctypes.c_int64), ("grown_rows", ctypes.c_int32), ("grown_cost", ctypes.c_float)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,6 +127,8 @@ def _load():
         "apsp_last_stats": [P, ctypes.POINTER(apsp_stats)],
         "apsp_sync": [P],
         "apsp_set_dispatch": [P, I32, ctypes.c_double],
+        "apsp_set_exact_list": [P, I32],
+        "apsp_set_direct_edge_filter": [P, I32],
         "apsp_profile_enable": [P, I32],
         "apsp_profile_read": [P, ctypes.POINTER(apsp_profile_entry), I32, ctypes.POINTER(I32)],
         "apsp_profile_reset": [P],
@@ -333,6 +336,14 @@ def apsp_last_stats(g: int) -> dict:
 
 def apsp_sync(g: int):
     _check(_load().apsp_sync(g), "apsp_sync")
+
+
+def apsp_set_exact_list(g: int, on: bool):
+    _check(_load().apsp_set_exact_list(g, 1 if on else 0), "apsp_set_exact_list")
+
+
+def apsp_set_direct_edge_filter(g: int, on: bool):
+    _check(_load().apsp_set_direct_edge_filter(g, 1 if on else 0), "apsp_set_direct_edge_filter")
 
 
 def apsp_set_dispatch(g: int, mode, delta: float = 1.0):
@@ -648,6 +659,12 @@ class Graph:
 
     def set_dispatch(self, mode, delta: float = 1.0):
         apsp_set_dispatch(self.h, mode, delta)
+
+    def set_direct_edge_filter(self, on: bool = True):
+        apsp_set_direct_edge_filter(self.h, on)
+
+    def set_exact_list(self, on: bool = True):
+        apsp_set_exact_list(self.h, on)
 
     def set_model(self, params):
         apsp_set_model(self.h, params)

@@ -122,6 +122,8 @@ struct Ctl {
     unsigned long long alloc; // detection reservations: (pairs << 24) | work items
     unsigned long long pairs_evaluated;  // semi-naive pair evaluations (passes >= 2)
     unsigned long long t_start, t_pass1, t_end;  // device timestamps (ns) of the warm repair
+    unsigned long long grown_pairs;  // listed pairs whose distance grew (Algorithm 12's list), when measured
+    int32_t grown_rows;              // rows holding one of them
     uint32_t err;             // sticky until the host reads it
 };
 

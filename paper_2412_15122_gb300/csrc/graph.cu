@@ -94,6 +94,8 @@ struct apsp_graph {
     int mode = APSP_DISPATCH_DELTA;
     float delta = 1.0f;
     bool has_model = false;
+    int32_t *grown_flag = nullptr;   // set when Algorithm 12's list is measured (apsp_set_exact_list)
+    int direct_filter = 0;           // apsp_set_direct_edge_filter
 
     apsp_stats last{};
     LaunchCtx lc;
@@ -336,6 +338,8 @@ template <typename T> RepairCfg repair_cfg(apsp_graph *g, int n_before, float ty
     c.model = g->model;
     c.feat_type = type_feat;
     c.feat_dw = dw;
+    c.grown_flag = g->grown_flag;
+    c.direct_filter = g->direct_filter;
     return c;
 }
 
@@ -953,6 +957,9 @@ apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *s) {
     Ctl c;
     apsp_status st = sync_ctl(g, &c);
     *s = g->last;
+    s->grown_pairs = -1;
+    s->grown_rows = -1;
+    s->grown_cost = -1.f;
     const int op = g->last.op;
     if (op == APSP_OP_REMOVE || op == APSP_OP_INCREASE) {
         s->affected_rows = c.n_rows;
@@ -965,6 +972,12 @@ apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *s) {
         s->model_cold = c.model_cold;
         s->sweep_rows = c.r_count;
         s->pairs_rechecked = (int64_t)c.pairs_evaluated;
+        if (g->grown_flag && !c.overflow) {
+            s->grown_pairs = (int64_t)c.grown_pairs;
+            s->grown_rows = c.grown_rows;
+            const int N = op == APSP_OP_REMOVE ? s->n_live + 1 : s->n_live;
+            s->grown_cost = N > 1 ? (float)c.grown_rows / (float)(N - 1) : 0.f;
+        }
         if (c.path == apsp::PATH_WARM && c.t_end > c.t_start) {
             s->warm_pass1_us = (float)((double)(c.t_pass1 - c.t_start) * 1e-3);
             s->warm_total_us = (float)((double)(c.t_end - c.t_start) * 1e-3);
@@ -983,6 +996,24 @@ apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta) {
     if (!g || mode < APSP_DISPATCH_DELTA || mode > APSP_DISPATCH_MODEL || !(delta >= 0.0)) return APSP_E_ARG;
     g->mode = mode;
     g->delta = (float)delta;
+    return APSP_OK;
+}
+
+apsp_status apsp_set_direct_edge_filter(apsp_graph *g, int32_t on) {
+    if (!g) return APSP_E_ARG;
+    g->direct_filter = on ? 1 : 0;
+    return APSP_OK;
+}
+
+apsp_status apsp_set_exact_list(apsp_graph *g, int32_t on) {
+    if (!g) return APSP_E_ARG;
+    if (on && !g->grown_flag) {
+        g->grown_flag = (int32_t *)dalloc(g, (size_t)g->ld * sizeof(int32_t));
+        if (!g->grown_flag) return APSP_E_NOMEM;
+    } else if (!on && g->grown_flag) {
+        dfree(g, g->grown_flag);
+        g->grown_flag = nullptr;
+    }
     return APSP_OK;
 }
 

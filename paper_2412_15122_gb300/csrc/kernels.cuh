@@ -607,6 +607,32 @@ __device__ __forceinline__ unsigned det_exact_mask(const Dev<T> &d, const typena
     return mask;
 }
 
+// Optional direct-edge filter: of the tight entries in `mask` (batch c0 of row
+// i, values v), drop those whose direct edge is itself a shortest path,
+// W[i][j] == D[i][j].  That edge avoids the removed node (and, for an
+// increase, differs from the changed edge, whose W already holds the new,
+// larger weight), so by Theorem theo_algo12 such a pair keeps its distance:
+// a sufficient test for leaving Corollary 3's pair out of Algorithm 12's list.
+template <typename T>
+__device__ __forceinline__ unsigned det_filter_direct(const Dev<T> &d, unsigned mask,
+                                                      const typename MinPlus<T>::V4 (&v)[SWEEP_B], int i, int c0) {
+    using V4 = typename MinPlus<T>::V4;
+    const int lane = threadIdx.x & 31;
+    const V4 *Wr4 = reinterpret_cast<const V4 *>(d.W + (int64_t)i * d.ld);
+    V4 w[SWEEP_B];
+#pragma unroll
+    for (int bb = 0; bb < SWEEP_B; ++bb)
+        if ((mask >> (4 * bb)) & 15u) w[bb] = __ldcg(Wr4 + c0 + bb * 32 + lane);
+#pragma unroll
+    for (int bb = 0; bb < SWEEP_B; ++bb) {
+        if (!((mask >> (4 * bb)) & 15u)) continue;
+        unsigned drop = (unsigned)(w[bb].x == v[bb].x) | (unsigned)(w[bb].y == v[bb].y) << 1 |
+                        (unsigned)(w[bb].z == v[bb].z) << 2 | (unsigned)(w[bb].w == v[bb].w) << 3;
+        mask &= ~(drop << (4 * bb));
+    }
+    return mask;
+}
+
 // Starting upper bound of listed pair (i, j): the direct edge, and for an
 // increase also the path through the edge at its new weight.
 template <typename T, bool TWO>
@@ -709,8 +735,42 @@ __global__ void __launch_bounds__(256) k_det_alloc(Dev<T> d) {
     if (rows_hit) atomicAdd(&d.ctl->n_rows, rows_hit);
 }
 
+// With the direct-edge filter on, the exact per-batch counts of the scan are
+// recounted after the filter (one warp per flagged (row, batch)) before the
+// reservation, so k_det_alloc and k_det_write see the same, filtered pairs.
 template <typename T, bool TWO>
-__global__ void __launch_bounds__(256, 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new) {
+__global__ void __launch_bounds__(256, 2) k_det_recount(Dev<T> d, int kind, int a, T w_old) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    const int lane = threadIdx.x & 31;
+    const int n_units = *(volatile const int32_t *)&d.ctl->hit_units;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int nv4 = d.span / 4;
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n_units; u += nwarps) {
+        const int4 ue = __ldcg(d.hunits + u);
+        const int i = ue.x;
+        const int c0 = ue.y * 32 * SWEEP_B;
+        const T xi = __ldcg(d.x + i);
+        const T x2i = TWO ? __ldcg(d.x2 + i) : M::inf();
+        const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+        V4 v[SWEEP_B];
+#pragma unroll
+        for (int bb = 0; bb < SWEEP_B; ++bb) {
+            const int c4 = c0 + bb * 32 + lane;
+            if (c4 < nv4) v[bb] = __ldcg(Dr4 + c4);
+        }
+        const T s1 = kind == 0 ? xi : M::add(xi, w_old);
+        const T s2 = M::add(x2i, w_old);
+        const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
+        unsigned mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
+        mask = det_filter_direct<T>(d, mask, v, i, c0);
+        const int c = warp_sum(__popc(mask));
+        if (lane == 0) d.rowcnt[(int64_t)i * DET_MAXB + ue.y] = c;
+    }
+}
+
+template <typename T, bool TWO, bool FILTER>
+__global__ void __launch_bounds__(256, FILTER ? 2 : 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     __shared__ int32_t hbuf[8][32 * SWEEP_B * 4];
@@ -747,7 +807,8 @@ __global__ void __launch_bounds__(256, 4) k_det_write(Dev<T> d, int kind, int a,
         const T s1 = kind == 0 ? xi : M::add(xi, w_old);
         const T s2 = M::add(x2i, w_old);
         const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
-        const unsigned mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
+        unsigned mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
+        if (FILTER) mask = det_filter_direct<T>(d, mask, v, i, c0);
         int tot;
         int off = warp_exclusive_scan(__popc(mask), &tot);
         __syncwarp();   // the previous unit's buffer reads are done
@@ -976,7 +1037,44 @@ struct RepairCfg {
     const float *model;  // cost-model parameters (device), may be null
     float feat_type;     // update-type feature
     float feat_dw;       // relative weight change
+    int32_t *grown_flag; // per-row flags (ld int32) for Algorithm 12's list; null: not measured
+    int direct_filter;   // drop listed pairs whose direct edge is a shortest path (det_filter_direct)
 };
+
+// Algorithm 12's need_update_list, measured once the repair is done.  A
+// listed pair belongs to it iff its distance grew: by Theorem theo_algo12 the
+// removed node (or, for an increase, the old edge) was then needed by every
+// shortest path.  The old distance of a listed pair is its tight sum through
+// the staged legs (removal: D[i][k] + D[k][j]; increase: D[i][u] + w_old +
+// D[v][j], or the reverse orientation of an undirected edge).  One warp per
+// work item; int32 exact, fp32 "grew" beyond the tightness slack.
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(256) k_grown_count(Dev<T> d, int kind, T w_old, int32_t *rflag) {
+    using M = MinPlus<T>;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long alloc = *(volatile const unsigned long long *)&d.ctl->alloc;
+    if (*(volatile const int32_t *)&d.ctl->overflow) return;
+    const int n_items = (int)(alloc & 0xFFFFFFull);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n_items; it += nwarps) {
+        const int4 item = __ldcg(d.items + it);
+        const int i = item.x, cnt = item.z & 0xff;
+        bool grown = false;
+        if (lane < cnt) {
+            const int j = __ldcg(d.pairs + item.y + lane);
+            const T xi = __ldcg(d.x + i);
+            T old = M::add(kind == 0 ? xi : M::add(xi, w_old), __ldcg(d.y + j));
+            if (TWO) old = M::mn(old, M::add(M::add(__ldcg(d.x2 + i), w_old), __ldcg(d.y2 + j)));
+            const T now = __ldcg(d.D + (int64_t)i * d.ld + j);
+            grown = !M::tight(now, old);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, grown);
+        if (lane == 0 && b) {
+            atomicAdd(&d.ctl->grown_pairs, (unsigned long long)__popc(b));
+            if (atomicExch(rflag + i, 1) == 0) atomicAdd(&d.ctl->grown_rows, 1);
+        }
+    }
+}
 
 template <typename T>
 __device__ void repair_warm(Dev<T> &d, int n_items) {

@@ -81,18 +81,25 @@ template <typename T> static size_t detect_smem(const Dev<T> &d, bool two) {
 // Detection: the streaming scan over the candidate rows (with exact counts of
 // the batches it flags), then the reservation and the writes of those units.
 template <typename T, bool TWO>
-static cudaError_t run_detect_t(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, const char *name) {
+static cudaError_t run_detect_t(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, int filter,
+                                const char *name) {
     cudaError_t e;
     const int scan_grid = TWO ? c.detect2_grid : c.detect_grid;
     if ((e = launch(c, name, [&] { k_det_scan<T, TWO><<<scan_grid, 256, detect_smem(d, TWO), c.stream>>>(d, kind, a, w_old); })) != cudaSuccess) return e;
+    if (filter &&
+        (e = launch(c, "detect_recount", [&] { k_det_recount<T, TWO><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old); })) != cudaSuccess)
+        return e;
     if ((e = launch(c, "detect_alloc", [&] { k_det_alloc<T><<<c.detalloc_grid, 256, 0, c.stream>>>(d); })) != cudaSuccess) return e;
-    return launch(c, "detect_write", [&] { k_det_write<T, TWO><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new); });
+    if (filter)
+        return launch(c, "detect_write", [&] { k_det_write<T, TWO, true><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new); });
+    return launch(c, "detect_write", [&] { k_det_write<T, TWO, false><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new); });
 }
 
 template <typename T>
-static cudaError_t run_detect(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, const char *name) {
-    if (d.undirected && kind == 1) return run_detect_t<T, true>(c, d, kind, a, w_old, w_new, name);
-    return run_detect_t<T, false>(c, d, kind, a, w_old, w_new, name);
+static cudaError_t run_detect(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, int filter,
+                              const char *name) {
+    if (d.undirected && kind == 1) return run_detect_t<T, true>(c, d, kind, a, w_old, w_new, filter, name);
+    return run_detect_t<T, false>(c, d, kind, a, w_old, w_new, filter, name);
 }
 
 // Cooperative grids of different graphs (streams) must not be resident at
@@ -148,20 +155,33 @@ template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d
     return le != cudaSuccess ? le : e;
 }
 
+// Optional: Algorithm 12's need_update_list measured after the repair.
+template <typename T> static cudaError_t run_grown(const LaunchCtx &c, const Dev<T> &d, int kind, T w_old, const RepairCfg &cfg) {
+    if (!cfg.grown_flag) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(cfg.grown_flag, 0, (size_t)d.ld * sizeof(int32_t), c.stream);
+    if (e != cudaSuccess) return e;
+    const int grid = 2 * c.num_sms;
+    if (d.undirected && kind == 1)
+        return launch(c, "grown_count", [&] { k_grown_count<T, true><<<grid, 256, 0, c.stream>>>(d, kind, w_old, cfg.grown_flag); });
+    return launch(c, "grown_count", [&] { k_grown_count<T, false><<<grid, 256, 0, c.stream>>>(d, kind, w_old, cfg.grown_flag); });
+}
+
 template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
-    if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, "detect_remove")) != cudaSuccess) return e;
+    if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, cfg.direct_filter, "detect_remove")) != cudaSuccess) return e;
     if ((e = launch(c, "tombstone", [&] { k_tombstone<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
-    return run_repair<T>(c, d, cfg);
+    if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
+    return run_grown<T>(c, d, 0, (T)0, cfg);
 }
 
 template <typename T>
 cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_old, T w_new, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "increase_prepass", [&] { k_inc_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w_old, w_new); })) != cudaSuccess) return e;
-    if ((e = run_detect<T>(c, d, 1, u, w_old, w_new, "detect_increase")) != cudaSuccess) return e;
-    return run_repair<T>(c, d, cfg);
+    if ((e = run_detect<T>(c, d, 1, u, w_old, w_new, cfg.direct_filter, "detect_increase")) != cudaSuccess) return e;
+    if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
+    return run_grown<T>(c, d, 1, w_old, cfg);
 }
 
 // The dynamic shared memory limit is a per-function setting shared by every

@@ -257,6 +257,71 @@ def test_affected_set_matches_oracle_need_update_list(seed):
     g.close()
 
 
+def _direct_edge_pairs(lst, Wx, M):
+    return sum(1 for i, js in lst.items() for j in js if Wx[i, j] != M[i, j])
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("undirected", [False, True])
+@pytest.mark.parametrize("direct_filter", [False, True])
+def test_exact_list_matches_oracle_algorithm12(seed, undirected, direct_filter):
+    # Small integer weights (0..4) make ties common, so Corollary 3 lists many
+    # pairs whose distance does not grow; Algorithm 12's list drops them.  With
+    # the direct-edge filter the device lists Corollary 3's pairs minus those
+    # whose direct edge is a shortest path.
+    n, cap = 60, 64
+    W = make_graph(n, 700 + seed, undirected=undirected, lo=0, hi=4, p_missing=0.2)
+    g = G(W, cap, undirected=undirected)
+    g.set_exact_list(True)
+    g.set_direct_edge_filter(direct_filter)
+    mir = Mirror(W, cap, undirected)
+    assert g.stats()["grown_pairs"] == -1            # init: not a removal or increase
+    for t in range(4):
+        live = mir.live()
+        M = mir.expected(cap)
+        k = int(live[synth.uniform_int(seed, 90 + t, 1, 0, len(live) - 1)[0]])
+        alg12 = O.need_update_list_alg12(M, mir.W, mir.alive, k)
+        cor3 = O.need_update_list(M, mir.alive, k)
+        Wx = O.exact(mir.W, mir.alive)
+        g.remove_node(k)
+        mir.remove(k)
+        st = g.stats()
+        if direct_filter:
+            assert st["affected_pairs"] == _direct_edge_pairs(cor3, Wx, M)
+        else:
+            assert st["affected_pairs"] == sum(len(v) for v in cor3.values())
+        assert st["grown_pairs"] == sum(len(v) for v in alg12.values())
+        assert st["grown_rows"] == sum(1 for v in alg12.values() if v)
+        N = len(live)
+        assert abs(st["grown_cost"] - st["grown_rows"] / (N - 1)) < 1e-6
+        assert_same(g, mir, f"remove {k}")
+    # an edge increase on a tight edge: the list is the pairs whose distance grows
+    live = mir.live()
+    u = int(live[3])
+    row = np.where(mir.alive, mir.W[u].astype(np.int64), 1 << 40)
+    row[u] = 1 << 40
+    v = int(np.argmin(row))
+    before = mir.expected(cap)
+    w_old = mir.W[u, v]
+    w = int(mir.W[u, v]) * 4 + 3
+    cand = O.edge_affected_pairs(before, mir.alive, u, v, int(w_old), undirected)
+    g.update_edge(u, v, w)
+    mir.edge(u, v, w)
+    after = mir.expected(cap)
+    st = g.stats()
+    Wx = O.exact(mir.W, mir.alive)                   # the new weight: the changed edge is never dropped
+    if direct_filter:
+        assert st["affected_pairs"] == sum(1 for (i, j) in cand if Wx[i, j] != before[i, j])
+    else:
+        assert st["affected_pairs"] == len(cand)
+    grown = (after > before) & np.outer(mir.alive, mir.alive)
+    np.fill_diagonal(grown, False)
+    assert st["grown_pairs"] == int(grown.sum())
+    assert st["grown_rows"] == int(grown.any(1).sum())
+    assert_same(g, mir, "increase")
+    g.close()
+
+
 def test_insert_every_node_from_empty_graph():
     # Algorithm 1's warm start used from scratch: n insertions give FW.
     n = 70

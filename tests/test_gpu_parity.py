@@ -463,6 +463,23 @@ def test_chunked_repair_n2048_full_check(fp):
     g.close()
 
 
+def test_config2_workload_n4096_full_matrix():
+    # The benchmark's workload at the largest size the oracle checks in full:
+    # n = 4096 directed complete graph, int32 U[1, 1e6], 100 mixed updates
+    # (25 % each kind, uniform targets, half of the edge updates on tight
+    # edges), then every entry against the oracle's Floyd-Warshall.
+    n, cap = 4096, 4096 + 128
+    W = synth.complete_digraph_i32(n, 1, 10**6, 42)
+    g = G(W, cap)
+    mir = Mirror(W, cap)
+    for t, up in enumerate(synth.mixed_updates(n, 100, 42, capacity=cap, w_lo=1, w_hi=10**6, cap=1 << 26)):
+        if up.kind in (synth.DECREASE, synth.INCREASE) and t % 2:
+            up.tight = True
+        apply(g, mir, up)
+    assert_same(g, mir, "after 100 mixed updates")
+    g.close()
+
+
 def test_graphs_of_different_sizes_coexist():
     """A smaller graph created later must not restrict the launches of a
     larger one (per-function launch limits are process-wide)."""

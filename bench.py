@@ -377,13 +377,15 @@ def run_dispatch_study(args):
         elif arm == "model":
             g.set_model(P)
             g.set_dispatch("model")
-        elif arm in ("warm_exact_list", "warm_direct_filter"):
+        elif arm in ("warm_exact_list", "warm_direct_filter", "warm_algorithm12"):
             # Experiment IV's question: how much of Corollary 3's list is
-            # Algorithm 12's (pairs whose distance really grows); and what the
-            # direct-edge filter keeps of it
+            # Algorithm 12's (pairs whose distance really grows); what the
+            # direct-edge filter keeps of it; and Algorithm 12 applied before
+            # the repair
             g.set_dispatch("warm")
             g.set_exact_list(True)
-            g.set_direct_edge_filter(arm == "warm_direct_filter")
+            g.set_list_mode({"warm_exact_list": "corollary3", "warm_direct_filter": "direct_edge",
+                             "warm_algorithm12": "algorithm12"}[arm])
         else:
             g.set_dispatch(arm)
         g.sync()
@@ -805,7 +807,7 @@ def main():
                     help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
                          "always-warm and always-cold on n=16384 undirected Euclidean updates")
     ap.add_argument("--study-updates", type=int, default=100)
-    ap.add_argument("--study-arms", default="delta,model,warm,cold,warm_exact_list,warm_direct_filter",
+    ap.add_argument("--study-arms", default="delta,model,warm,cold,warm_exact_list,warm_direct_filter,warm_algorithm12",
                     help="dispatch study: comma-separated arms to run")
     ap.add_argument("--study-samples", type=int, default=20000)
     args = ap.parse_args()

@@ -260,16 +260,25 @@ apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta);
  * The result of every update is the same either way. */
 apsp_status apsp_set_exact_list(apsp_graph *g, int32_t on);
 
-/* Direct-edge filter (a sufficient form of Algorithm 12's test).  With `on`,
- * detection drops from Corollary 3's list every pair (i, j) whose direct edge
- * is itself a shortest path (W[i][j] == D[i][j]): that edge avoids the
- * removed node, and differs from an increased edge (whose weight is already
- * the new one), so the pair keeps its distance and needs no re-relaxation.
- * affected_pairs / affected_rows and Cost then count the filtered list (which
- * still contains Algorithm 12's whole list).  Results are the same either way;
- * it pays off on graphs where ties are common, such as Euclidean weights.
- * Default off (the list is exactly Section 3.2's need_update_list). */
-apsp_status apsp_set_direct_edge_filter(apsp_graph *g, int32_t on);
+/* Which pairs removals and edge increases re-relax (the result of every
+ * update is the same in every mode; affected_pairs / affected_rows and Cost
+ * count the chosen list):
+ *   APSP_LIST_COROLLARY3   Section 3.2's need_update_list: every pair with
+ *                          D[i][k] + D[k][j] == D[i][j] (the default);
+ *   APSP_LIST_DIRECT_EDGE  minus the pairs whose direct edge is itself a
+ *                          shortest path (W[i][j] == D[i][j]): that edge avoids
+ *                          the removed node, and an increased edge's weight is
+ *                          already the new one, so they keep their distance;
+ *   APSP_LIST_ALGORITHM12  Algorithm 12: each listed pair keeps its place only
+ *                          if Dijkstra on Algorithm 7's small graph without the
+ *                          removed node (for an increase: with the edge's new
+ *                          weight) does not reach j within its old distance --
+ *                          by Theorem theo_algo12 exactly the pairs whose
+ *                          distance grows.  Pairs whose small graph has more
+ *                          than 126 candidates stay listed (always safe).
+ * The last two pay off where ties between routes are common. */
+typedef enum { APSP_LIST_COROLLARY3 = 0, APSP_LIST_DIRECT_EDGE = 1, APSP_LIST_ALGORITHM12 = 2 } apsp_list_mode;
+apsp_status apsp_set_list_mode(apsp_graph *g, apsp_list_mode mode);
 
 /* ----- learned warm/cold cost model ---------------------------------------
  * Algorithm 5 chooses between re-running the affected rows and recomputing

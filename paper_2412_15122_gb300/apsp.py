@@ -128,7 +128,7 @@ def _load():
         "apsp_sync": [P],
         "apsp_set_dispatch": [P, I32, ctypes.c_double],
         "apsp_set_exact_list": [P, I32],
-        "apsp_set_direct_edge_filter": [P, I32],
+        "apsp_set_list_mode": [P, I32],
         "apsp_profile_enable": [P, I32],
         "apsp_profile_read": [P, ctypes.POINTER(apsp_profile_entry), I32, ctypes.POINTER(I32)],
         "apsp_profile_reset": [P],
@@ -342,8 +342,12 @@ def apsp_set_exact_list(g: int, on: bool):
     _check(_load().apsp_set_exact_list(g, 1 if on else 0), "apsp_set_exact_list")
 
 
-def apsp_set_direct_edge_filter(g: int, on: bool):
-    _check(_load().apsp_set_direct_edge_filter(g, 1 if on else 0), "apsp_set_direct_edge_filter")
+LIST_MODES = {"corollary3": 0, "direct_edge": 1, "algorithm12": 2}
+
+
+def apsp_set_list_mode(g: int, mode):
+    m = LIST_MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(_load().apsp_set_list_mode(g, m), "apsp_set_list_mode")
 
 
 def apsp_set_dispatch(g: int, mode, delta: float = 1.0):
@@ -660,8 +664,8 @@ class Graph:
     def set_dispatch(self, mode, delta: float = 1.0):
         apsp_set_dispatch(self.h, mode, delta)
 
-    def set_direct_edge_filter(self, on: bool = True):
-        apsp_set_direct_edge_filter(self.h, on)
+    def set_list_mode(self, mode):
+        apsp_set_list_mode(self.h, mode)
 
     def set_exact_list(self, on: bool = True):
         apsp_set_exact_list(self.h, on)

@@ -95,7 +95,8 @@ struct apsp_graph {
     float delta = 1.0f;
     bool has_model = false;
     int32_t *grown_flag = nullptr;   // set when Algorithm 12's list is measured (apsp_set_exact_list)
-    int direct_filter = 0;           // apsp_set_direct_edge_filter
+    int list_mode = APSP_LIST_COROLLARY3;   // apsp_set_list_mode
+    uint32_t *umask = nullptr;              // list mode APSP_LIST_ALGORITHM12: per-unit surviving masks
 
     apsp_stats last{};
     LaunchCtx lc;
@@ -339,7 +340,8 @@ template <typename T> RepairCfg repair_cfg(apsp_graph *g, int n_before, float ty
     c.feat_type = type_feat;
     c.feat_dw = dw;
     c.grown_flag = g->grown_flag;
-    c.direct_filter = g->direct_filter;
+    c.list_mode = g->list_mode;
+    c.umask = g->umask;
     return c;
 }
 
@@ -999,9 +1001,14 @@ apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta) {
     return APSP_OK;
 }
 
-apsp_status apsp_set_direct_edge_filter(apsp_graph *g, int32_t on) {
-    if (!g) return APSP_E_ARG;
-    g->direct_filter = on ? 1 : 0;
+apsp_status apsp_set_list_mode(apsp_graph *g, apsp_list_mode mode) {
+    if (!g || mode < APSP_LIST_COROLLARY3 || mode > APSP_LIST_ALGORITHM12) return APSP_E_ARG;
+    if (mode == APSP_LIST_ALGORITHM12 && !g->umask) {
+        const int64_t hunit_cap = g->ld * ((g->ld + 1023) / 1024);
+        g->umask = (uint32_t *)dalloc(g, (size_t)hunit_cap * 32 * sizeof(uint32_t));
+        if (!g->umask) return APSP_E_NOMEM;
+    }
+    g->list_mode = mode;
     return APSP_OK;
 }
 

@@ -769,8 +769,11 @@ __global__ void __launch_bounds__(256, 2) k_det_recount(Dev<T> d, int kind, int 
     }
 }
 
-template <typename T, bool TWO, bool FILTER>
-__global__ void __launch_bounds__(256, FILTER ? 2 : 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new) {
+// FILTER: 0 the exact mask (Corollary 3), 1 minus direct-edge pairs, 2 the
+// mask that k_det_alg12 left in umask for this unit.
+template <typename T, bool TWO, int FILTER>
+__global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new,
+                                                                      const uint32_t *umask) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     __shared__ int32_t hbuf[8][32 * SWEEP_B * 4];
@@ -807,8 +810,13 @@ __global__ void __launch_bounds__(256, FILTER ? 2 : 4) k_det_write(Dev<T> d, int
         const T s1 = kind == 0 ? xi : M::add(xi, w_old);
         const T s2 = M::add(x2i, w_old);
         const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
-        unsigned mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
-        if (FILTER) mask = det_filter_direct<T>(d, mask, v, i, c0);
+        unsigned mask;
+        if (FILTER == 2) {
+            mask = __ldcg(umask + (int64_t)u * 32 + lane);
+        } else {
+            mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
+            if (FILTER == 1) mask = det_filter_direct<T>(d, mask, v, i, c0);
+        }
         int tot;
         int off = warp_exclusive_scan(__popc(mask), &tot);
         __syncwarp();   // the previous unit's buffer reads are done
@@ -1038,7 +1046,8 @@ struct RepairCfg {
     float feat_type;     // update-type feature
     float feat_dw;       // relative weight change
     int32_t *grown_flag; // per-row flags (ld int32) for Algorithm 12's list; null: not measured
-    int direct_filter;   // drop listed pairs whose direct edge is a shortest path (det_filter_direct)
+    int list_mode;       // apsp_list_mode: 1 drops direct-edge pairs (det_filter_direct), 2 applies Algorithm 12 (k_det_alg12)
+    uint32_t *umask;     // list mode 2: surviving mask per flagged unit (32 words each)
 };
 
 // Algorithm 12's need_update_list, measured once the repair is done.  A

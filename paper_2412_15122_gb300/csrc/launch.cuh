@@ -81,25 +81,33 @@ template <typename T> static size_t detect_smem(const Dev<T> &d, bool two) {
 // Detection: the streaming scan over the candidate rows (with exact counts of
 // the batches it flags), then the reservation and the writes of those units.
 template <typename T, bool TWO>
-static cudaError_t run_detect_t(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, int filter,
-                                const char *name) {
+static cudaError_t run_detect_t(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new,
+                                const RepairCfg &cfg, const char *name) {
     cudaError_t e;
     const int scan_grid = TWO ? c.detect2_grid : c.detect_grid;
+    const int mode = cfg.list_mode;
     if ((e = launch(c, name, [&] { k_det_scan<T, TWO><<<scan_grid, 256, detect_smem(d, TWO), c.stream>>>(d, kind, a, w_old); })) != cudaSuccess) return e;
-    if (filter &&
+    if (mode == 1 &&
         (e = launch(c, "detect_recount", [&] { k_det_recount<T, TWO><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old); })) != cudaSuccess)
         return e;
+    if (mode == 2 &&
+        (e = launch(c, "detect_alg12", [&] {
+             k_det_alg12<T, TWO><<<c.pw_grid, PW_WARPS * 32, pw_smem_bytes<T>(), c.stream>>>(d, kind, a, w_old, cfg.umask);
+         })) != cudaSuccess)
+        return e;
     if ((e = launch(c, "detect_alloc", [&] { k_det_alloc<T><<<c.detalloc_grid, 256, 0, c.stream>>>(d); })) != cudaSuccess) return e;
-    if (filter)
-        return launch(c, "detect_write", [&] { k_det_write<T, TWO, true><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new); });
-    return launch(c, "detect_write", [&] { k_det_write<T, TWO, false><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new); });
+    if (mode == 1)
+        return launch(c, "detect_write", [&] { k_det_write<T, TWO, 1><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new, nullptr); });
+    if (mode == 2)
+        return launch(c, "detect_write", [&] { k_det_write<T, TWO, 2><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new, cfg.umask); });
+    return launch(c, "detect_write", [&] { k_det_write<T, TWO, 0><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new, nullptr); });
 }
 
 template <typename T>
-static cudaError_t run_detect(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new, int filter,
-                              const char *name) {
-    if (d.undirected && kind == 1) return run_detect_t<T, true>(c, d, kind, a, w_old, w_new, filter, name);
-    return run_detect_t<T, false>(c, d, kind, a, w_old, w_new, filter, name);
+static cudaError_t run_detect(const LaunchCtx &c, const Dev<T> &d, int kind, int a, T w_old, T w_new,
+                              const RepairCfg &cfg, const char *name) {
+    if (d.undirected && kind == 1) return run_detect_t<T, true>(c, d, kind, a, w_old, w_new, cfg, name);
+    return run_detect_t<T, false>(c, d, kind, a, w_old, w_new, cfg, name);
 }
 
 // Cooperative grids of different graphs (streams) must not be resident at
@@ -169,7 +177,7 @@ template <typename T> static cudaError_t run_grown(const LaunchCtx &c, const Dev
 template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
-    if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, cfg.direct_filter, "detect_remove")) != cudaSuccess) return e;
+    if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, cfg, "detect_remove")) != cudaSuccess) return e;
     if ((e = launch(c, "tombstone", [&] { k_tombstone<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
     if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
     return run_grown<T>(c, d, 0, (T)0, cfg);
@@ -179,7 +187,7 @@ template <typename T>
 cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_old, T w_new, const RepairCfg &cfg) {
     cudaError_t e;
     if ((e = launch(c, "increase_prepass", [&] { k_inc_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w_old, w_new); })) != cudaSuccess) return e;
-    if ((e = run_detect<T>(c, d, 1, u, w_old, w_new, cfg.direct_filter, "detect_increase")) != cudaSuccess) return e;
+    if ((e = run_detect<T>(c, d, 1, u, w_old, w_new, cfg, "detect_increase")) != cudaSuccess) return e;
     if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
     return run_grown<T>(c, d, 1, w_old, cfg);
 }
@@ -225,6 +233,8 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     c.detunit_grid = 4 * c.num_sms;
     c.detalloc_grid = (int)((ld + 255) / 256);   // a lane per row: 256 rows a CTA
     if ((e = allow_max_smem(k_path_warp<T>)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_det_alg12<T, false>)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_det_alg12<T, true>)) != cudaSuccess) return e;
     int pw_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pw_sm, k_path_warp<T>, PW_WARPS * 32, pw_smem_bytes<T>())) !=
         cudaSuccess)

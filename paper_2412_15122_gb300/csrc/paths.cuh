@@ -431,6 +431,137 @@ template <typename T> __global__ void __launch_bounds__(PW_WARPS * 32) k_path_wa
 
 template <typename T> constexpr size_t pw_smem_bytes() { return PW_WARPS * sizeof(PwWarpSmem<T>); }
 
+// ---------------------------------------------------------------------------
+// Algorithm 12 before the repair (list mode APSP_LIST_ALGORITHM12).  For a
+// pair (i, j) that Corollary 3 lists, with old distance dold: the candidates
+// t (not i, j or the removed node `excl`) with D[i][t] + D[t][j] <= dold,
+// Algorithm 7's small graph over them, and Dijkstra from i to j on it.  If it
+// reaches j within dold, a shortest path avoids the removed node (for an
+// increase, W already holds the edge's new, larger weight, so a path through
+// the edge cannot be that short) and the pair keeps its distance: it leaves
+// the list.  Returns true when the pair stays (also when the candidates
+// exceed PW_K: staying is always safe).  One warp; D must still hold the old
+// distances.
+template <typename T>
+__device__ bool alg12_keep(const Dev<T> &d, int i, int j, int excl, T dold, PwWarpSmem<T> &S) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    constexpr int B = 4;
+    const int lane = threadIdx.x & 31;
+    const int nv = d.span >> 2;
+    const V4 *ri = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+    const V4 *rj = reinterpret_cast<const V4 *>((d.DT ? d.DT : d.D) + (int64_t)j * d.ld);
+    int total = 0;
+    for (int base = 0; base < nv && total <= PW_K - 2; base += 32 * B) {
+        V4 a[B], c[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int v = base + 32 * b + lane;
+            if (v < nv) {
+                a[b] = __ldcg(ri + v);
+                c[b] = __ldcg(rj + v);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int v = base + 32 * b + lane;
+            unsigned m4 = 0;
+            if (v < nv) {
+                const int t = v << 2;
+                if (t != i && t != j && t != excl && pq_keep<T>(a[b].x, c[b].x, dold)) m4 |= 1u;
+                if (t + 1 != i && t + 1 != j && t + 1 != excl && pq_keep<T>(a[b].y, c[b].y, dold)) m4 |= 2u;
+                if (t + 2 != i && t + 2 != j && t + 2 != excl && pq_keep<T>(a[b].z, c[b].z, dold)) m4 |= 4u;
+                if (t + 3 != i && t + 3 != j && t + 3 != excl && pq_keep<T>(a[b].w, c[b].w, dold)) m4 |= 8u;
+            }
+            int wsum;
+            int pos = 1 + total + warp_exclusive_scan(__popc(m4), &wsum);
+            while (m4) {
+                const int e = __ffs(m4) - 1;
+                m4 &= m4 - 1;
+                if (pos < PW_K - 1) S.cand[pos] = (v << 2) + e;
+                ++pos;
+            }
+            total += wsum;
+        }
+    }
+    const int K = total + 2;
+    if (K > PW_K) return true;
+    __syncwarp();
+    if (lane == 0) {
+        S.cand[0] = i;
+        S.cand[K - 1] = j;
+    }
+    __syncwarp();
+    const T *small = nullptr;
+    if (K <= PW_SK) {
+        for (int e = lane; e < K * K; e += 32) {
+            const int a = e / K, b = e - a * K;
+            S.small[e] = __ldcg(d.W + (int64_t)S.cand[a] * d.ld + S.cand[b]);
+        }
+        __syncwarp();
+        small = S.small;
+    }
+    pq_dijkstra<T>(d, S.cand, K, 0, false, true, small, S.fdist, S.fpred, S.fdone);
+    __syncwarp();
+    const T dj = S.fdist[K - 1];
+    __syncwarp();   // every lane has read it before the next pair reuses the arrays
+    return !(dj <= dold);
+}
+
+// One warp per flagged (row, batch) of the detection scan, before the
+// reservation: the exact mask, then Algorithm 12's test for each of its pairs
+// (one after another, the whole warp on each).  The surviving mask is kept
+// for k_det_write and the batch's count replaced, so the reservation and the
+// writes see Algorithm 12's list.
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(PW_WARPS * 32) k_det_alg12(Dev<T> d, int kind, int a, T w_old, uint32_t *umask) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    extern __shared__ __align__(16) unsigned char pw_smem[];
+    PwWarpSmem<T> &S = reinterpret_cast<PwWarpSmem<T> *>(pw_smem)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int n_units = *(volatile const int32_t *)&d.ctl->hit_units;
+    const int nwarps = gridDim.x * PW_WARPS;
+    const int nv4 = d.span / 4;
+    for (int u = blockIdx.x * PW_WARPS + (threadIdx.x >> 5); u < n_units; u += nwarps) {
+        const int4 ue = __ldcg(d.hunits + u);
+        const int i = ue.x;
+        const int c0 = ue.y * 32 * SWEEP_B;
+        const T xi = __ldcg(d.x + i);
+        const T x2i = TWO ? __ldcg(d.x2 + i) : M::inf();
+        const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+        V4 v[SWEEP_B];
+#pragma unroll
+        for (int bb = 0; bb < SWEEP_B; ++bb) {
+            const int c4 = c0 + bb * 32 + lane;
+            if (c4 < nv4) v[bb] = __ldcg(Dr4 + c4);
+        }
+        const T s1 = kind == 0 ? xi : M::add(xi, w_old);
+        const T s2 = M::add(x2i, w_old);
+        const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
+        const unsigned mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
+        unsigned keep = mask, rem = mask;
+        while (true) {
+            const unsigned who = __ballot_sync(0xffffffffu, rem != 0u);
+            if (!who) break;
+            const int src = __ffs(who) - 1;
+            int bit = 0;
+            if (lane == src) {
+                bit = __ffs(rem) - 1;
+                rem &= rem - 1;
+            }
+            bit = __shfl_sync(0xffffffffu, bit, src);
+            const int j = 4 * (c0 + (bit >> 2) * 32 + src) + (bit & 3);
+            const T dold = __ldcg(d.D + (int64_t)i * d.ld + j);
+            const bool stays = alg12_keep<T>(d, i, j, kind == 0 ? a : -1, dold, S);
+            if (!stays && lane == src) keep &= ~(1u << bit);
+        }
+        umask[(int64_t)u * 32 + lane] = keep;
+        const int c = warp_sum(__popc(keep));
+        if (lane == 0) d.rowcnt[(int64_t)i * DET_MAXB + ue.y] = c;
+    }
+}
+
 template <typename T> constexpr size_t pq_smem_bytes() {
     return (size_t)PQ_KS * (3 * sizeof(int32_t) + 2 * sizeof(T) + 2) + (size_t)PQ_SK * PQ_SK * sizeof(T);
 }

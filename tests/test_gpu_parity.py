@@ -263,17 +263,18 @@ def _direct_edge_pairs(lst, Wx, M):
 
 @pytest.mark.parametrize("seed", range(3))
 @pytest.mark.parametrize("undirected", [False, True])
-@pytest.mark.parametrize("direct_filter", [False, True])
-def test_exact_list_matches_oracle_algorithm12(seed, undirected, direct_filter):
+@pytest.mark.parametrize("list_mode", ["corollary3", "direct_edge", "algorithm12"])
+def test_exact_list_matches_oracle_algorithm12(seed, undirected, list_mode):
     # Small integer weights (0..4) make ties common, so Corollary 3 lists many
-    # pairs whose distance does not grow; Algorithm 12's list drops them.  With
-    # the direct-edge filter the device lists Corollary 3's pairs minus those
-    # whose direct edge is a shortest path.
+    # pairs whose distance does not grow; Algorithm 12's list drops them.  The
+    # device's list is Corollary 3's, Corollary 3's minus the pairs whose direct
+    # edge is a shortest path, or Algorithm 12's, by list mode; the measured
+    # Algorithm 12 list and the matrices are the same in every mode.
     n, cap = 60, 64
     W = make_graph(n, 700 + seed, undirected=undirected, lo=0, hi=4, p_missing=0.2)
     g = G(W, cap, undirected=undirected)
     g.set_exact_list(True)
-    g.set_direct_edge_filter(direct_filter)
+    g.set_list_mode(list_mode)
     mir = Mirror(W, cap, undirected)
     assert g.stats()["grown_pairs"] == -1            # init: not a removal or increase
     for t in range(4):
@@ -286,8 +287,11 @@ def test_exact_list_matches_oracle_algorithm12(seed, undirected, direct_filter):
         g.remove_node(k)
         mir.remove(k)
         st = g.stats()
-        if direct_filter:
+        if list_mode == "direct_edge":
             assert st["affected_pairs"] == _direct_edge_pairs(cor3, Wx, M)
+        elif list_mode == "algorithm12":   # the device list is Algorithm 12's (n < 126: no pair stays unchecked)
+            assert st["affected_pairs"] == sum(len(v) for v in alg12.values())
+            assert st["affected_rows"] == sum(1 for v in alg12.values() if v)
         else:
             assert st["affected_pairs"] == sum(len(v) for v in cor3.values())
         assert st["grown_pairs"] == sum(len(v) for v in alg12.values())
@@ -310,8 +314,10 @@ def test_exact_list_matches_oracle_algorithm12(seed, undirected, direct_filter):
     after = mir.expected(cap)
     st = g.stats()
     Wx = O.exact(mir.W, mir.alive)                   # the new weight: the changed edge is never dropped
-    if direct_filter:
+    if list_mode == "direct_edge":
         assert st["affected_pairs"] == sum(1 for (i, j) in cand if Wx[i, j] != before[i, j])
+    elif list_mode == "algorithm12":
+        assert st["affected_pairs"] == st["grown_pairs"]
     else:
         assert st["affected_pairs"] == len(cand)
     grown = (after > before) & np.outer(mir.alive, mir.alive)

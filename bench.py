@@ -44,6 +44,26 @@ SWEEP_KERNELS = ("insert_reduce", "insert_relax", "detect_remove")
 SWEEP_TRAFFIC = {"insert_reduce": 272.19e6, "insert_relax": 274.83e6, "detect_remove": 274.49e6}
 
 
+def rank_seed(rank: int) -> int:
+    """Each replica (one process per GPU) updates its own graph."""
+    return SEED + 1000 * rank
+
+
+def job_ms(ms: float, dist=None, device="cuda") -> float:
+    """The job's time is its slowest rank's: max over ranks."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(updates_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job updates/s: the updates of all ranks over the slowest rank's time."""
+    return updates_per_rank * world / (ms / 1000.0)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -838,7 +858,7 @@ def main():
     from paper_2412_15122_gb300 import apsp as A
     build.build()
 
-    seed = SEED + 1000 * rank
+    seed = rank_seed(rank)
     total = (args.warmup + args.steps) * args.updates
     W, ops = plan_ops(total, seed)
     ops_value = ops_e2e = ops          # the same workload, replayed on a fresh graph for e2e
@@ -908,12 +928,9 @@ def main():
         return ms, nl, prof, cold, span, clk
 
     ms, gpu_launches, _, cold_ms, span, clk = device_pass(profile=False, want_clocks=True)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_ms(ms, dist)
     n_updates = args.steps * U * world
-    value = n_updates / (ms / 1000.0)
+    value = job_value(args.steps * U, world, ms)
     prof_ms, _, prof, _, _, _ = device_pass(profile=True, want_clocks=False)
 
     # ---- statistics of the workload (untimed, one wait per update) -----------
@@ -970,11 +987,8 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     wall_ms = (time.perf_counter() - t0) * 1000
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = n_updates / (e2e_ms / 1000.0)
+    e2e_ms = job_ms(e2e_ms, dist)
+    e2e_value = job_value(args.steps * U, world, e2e_ms)
     g.close()
 
     # ---- roofline of the dominant sweep kernel --------------------------------

@@ -434,6 +434,11 @@ apsp_status apsp_profile_reset(apsp_graph *g);
  * and touches no memory: the ceiling against which the cold path's n^3 steps
  * are reported.  Takes a few milliseconds; waits for the device. */
 apsp_status apsp_probe_addmin_rate(apsp_dtype dtype, double *pair_ops_per_s);
+/* Measures the L2 read bandwidth of the current CUDA device (GB/s): 16-byte
+ * coalesced loads from a warm buffer of a quarter of L2, 8 in flight per
+ * thread.  The ceiling of the first re-relaxation pass, whose reads are
+ * served by L2.  Takes a few milliseconds; waits for the device. */
+apsp_status apsp_probe_l2_read_gbs(double *gbs);
 
 /* ----- insertion without allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that

@@ -120,6 +120,7 @@ def _load():
         "apsp_query_path": [P, I32, I32, P, I32, ctypes.POINTER(I32)],
         "apsp_query_all_paths": [P, I32, I32, P, I64, P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64)],
         "apsp_probe_addmin_rate": [I32, ctypes.POINTER(ctypes.c_double)],
+        "apsp_probe_l2_read_gbs": [ctypes.POINTER(ctypes.c_double)],
         "apsp_copy_D": [P, P, I64, I32],
         "apsp_copy_W": [P, P, I64, I32],
         "apsp_copy_alive": [P, P],
@@ -305,6 +306,13 @@ def apsp_probe_addmin_rate(dtype: int) -> float:
     """Min-plus steps per second of the CUDA cores (register-tile probe, current device)."""
     r = ctypes.c_double()
     _check(_load().apsp_probe_addmin_rate(dtype, ctypes.byref(r)), "apsp_probe_addmin_rate")
+    return r.value
+
+
+def apsp_probe_l2_read_gbs() -> float:
+    """L2 read bandwidth of the current device in GB/s (probe kernel)."""
+    r = ctypes.c_double()
+    _check(_load().apsp_probe_l2_read_gbs(ctypes.byref(r)), "apsp_probe_l2_read_gbs")
     return r.value
 
 

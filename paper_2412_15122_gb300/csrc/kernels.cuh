@@ -858,6 +858,8 @@ __global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, 
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // an increase whose prepass found no candidate row (a non-tight edge) has nothing to scan
+    if (kind == 1 && *(volatile const int32_t *)&d.ctl->r_count == 0) return;
     const int span = d.span;
     T *ys = reinterpret_cast<T *>(smem_raw);
     T *y2s = ys + span;

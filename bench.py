@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -118,7 +119,7 @@ class Clocks:
     def __init__(self, dev: int):
         self.dev = dev
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"apsp_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -1033,7 +1034,7 @@ def main():
         l2 = A.apsp_probe_l2_read_gbs()
         p1_bytes = 4.0 * span * rm["avg_pairs"]       # a column slice of every listed pair over all x
         p1_gbs = p1_bytes / (rm["avg_warm_pass1_us"] * 1e-6) / 1e9
-        repair_roofline = {"bound": "l2", "kernel": "repair_warm, first pass (removals)", "achieved": p1_gbs,
+        repair_roofline = {"bound": "l2", "kernel": "k_repair_warm, first pass (removals)", "achieved": p1_gbs,
                            "peak": l2, "unit": "GB/s", "frac": p1_gbs / l2,
                            "peak_kind": "measured: L2 read probe (apsp_probe_l2_read_gbs)",
                            "bytes_per_removal": p1_bytes, "pass1_us_per_removal": rm["avg_warm_pass1_us"]}

@@ -428,7 +428,11 @@ typedef struct {
 apsp_status apsp_profile_read(apsp_graph *g, apsp_profile_entry *out, int32_t cap, int32_t *count);
 apsp_status apsp_profile_reset(apsp_graph *g);
 
-/* Measures, on the current CUDA device, how many min-plus steps min(a + b, c)
+/* Measurement probes (instrumentation; the paper has no counterpart): the
+ * ceilings that the cold solver and the first re-relaxation pass are reported
+ * against.
+ *
+ * Measures, on the current CUDA device, how many min-plus steps min(a + b, c)
  * of the given dtype the CUDA cores issue per second when every thread keeps
  * an 8 x 8 register tile of them (the inner loop of the cold Floyd-Warshall)
  * and touches no memory: the ceiling against which the cold path's n^3 steps

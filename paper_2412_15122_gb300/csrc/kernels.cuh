@@ -334,6 +334,24 @@ __global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d, int rows_per_ct
     }
 }
 
+// Row p = out (Corollary 1), column p = in (Corollary 2), D[p][p] = 0, the
+// weights of p, and p becomes live (entry c of each).
+template <typename T>
+__device__ __forceinline__ void insert_finish_entry(const Dev<T> &d, int p, int c) {
+    using M = MinPlus<T>;
+    const T o = c == p ? (T)0 : M::unkey(d.vout_k[c]);
+    const T in = c == p ? (T)0 : M::unkey(d.vin_k[c]);
+    d.D[(int64_t)p * d.ld + c] = o;
+    d.D[(int64_t)c * d.ld + p] = in;
+    d.W[(int64_t)p * d.ld + c] = c == p ? (T)0 : d.w_out[c];
+    d.W[(int64_t)c * d.ld + p] = c == p ? (T)0 : d.w_in[c];
+    if (d.DT) {
+        d.DT[(int64_t)c * d.ld + p] = o;
+        d.DT[(int64_t)p * d.ld + c] = in;
+    }
+    if (c == p) d.alive[p] = 1;
+}
+
 // Theorem 3 sweep: D[i][j] = min(D[i][j], in[i] + out[j]).  One warp per
 // row; out[] is staged once per CTA in shared memory.  Each lane streams 8
 // vectors at a time and only builds a 32-bit mask of the entries that
@@ -341,13 +359,16 @@ __global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d, int rows_per_ct
 // in[i] + out[j]; the row data is no longer needed).  A dead row and p
 // itself have in[] = missing, so one load decides whether a row is swept.
 // Row p and column p are never improved by the sweep (their candidates are
-// missing), so they are written afterwards by k_insert_finish.
+// missing) and row p is never read by it, so the same launch writes them
+// (insert_finish_entry) while the rows are swept.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int span = d.span;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < span; c += gridDim.x * blockDim.x)
+        insert_finish_entry<T>(d, p, c);
     // vout_k holds ordered keys whose bit patterns are the values themselves
     T *so = reinterpret_cast<T *>(smem_raw);
     V4 *so4w = reinterpret_cast<V4 *>(smem_raw);
@@ -390,26 +411,6 @@ __global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p) {
             }
         }
     }
-}
-
-// Row p = out (Corollary 1), column p = in (Corollary 2), D[p][p] = 0, the
-// weights of p, and p becomes live.
-template <typename T>
-__global__ void k_insert_finish(Dev<T> d, int p) {
-    using M = MinPlus<T>;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d.span) return;
-    const T o = c == p ? (T)0 : M::unkey(d.vout_k[c]);
-    const T in = c == p ? (T)0 : M::unkey(d.vin_k[c]);
-    d.D[(int64_t)p * d.ld + c] = o;
-    d.D[(int64_t)c * d.ld + p] = in;
-    d.W[(int64_t)p * d.ld + c] = c == p ? (T)0 : d.w_out[c];
-    d.W[(int64_t)c * d.ld + p] = c == p ? (T)0 : d.w_in[c];
-    if (d.DT) {
-        d.DT[(int64_t)c * d.ld + p] = o;
-        d.DT[(int64_t)p * d.ld + c] = in;
-    }
-    if (c == p) d.alive[p] = 1;
 }
 
 // --------------------------------------------------------------------------
@@ -771,9 +772,30 @@ __global__ void __launch_bounds__(256, 2) k_det_recount(Dev<T> d, int kind, int 
 
 // FILTER: 0 the exact mask (Corollary 3), 1 minus direct-edge pairs, 2 the
 // mask that k_det_alg12 left in umask for this unit.
+// Removal: node k's row and column become missing, slot k dead (entry t).
+template <typename T>
+__device__ __forceinline__ void tombstone_entry(const Dev<T> &d, int k, int t) {
+    const T inf = MinPlus<T>::inf();
+    d.D[(int64_t)k * d.ld + t] = inf;
+    d.D[(int64_t)t * d.ld + k] = inf;
+    d.W[(int64_t)k * d.ld + t] = inf;
+    d.W[(int64_t)t * d.ld + k] = inf;
+    if (d.DT) {
+        d.DT[(int64_t)k * d.ld + t] = inf;
+        d.DT[(int64_t)t * d.ld + k] = inf;
+    }
+    if (t == 0) d.alive[k] = 0;
+}
+
+// For a removal (kind 0) the same launch also tombstones node a: nothing
+// here reads row or column a (column a is never listed) and no listed pair
+// lies in them.
 template <typename T, bool TWO, int FILTER>
 __global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new,
                                                                       const uint32_t *umask) {
+    if (kind == 0)
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.span; t += gridDim.x * blockDim.x)
+            tombstone_entry<T>(d, a, t);
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     __shared__ int32_t hbuf[8][32 * SWEEP_B * 4];
@@ -994,23 +1016,6 @@ __global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, 
     if (nh) flush();
 }
 
-// Removal: node k's row and column become missing, slot k dead.
-template <typename T>
-__global__ void k_tombstone(Dev<T> d, int k) {
-    using M = MinPlus<T>;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= d.span) return;
-    const T inf = M::inf();
-    d.D[(int64_t)k * d.ld + t] = inf;
-    d.D[(int64_t)t * d.ld + k] = inf;
-    d.W[(int64_t)k * d.ld + t] = inf;
-    d.W[(int64_t)t * d.ld + k] = inf;
-    if (d.DT) {
-        d.DT[(int64_t)k * d.ld + t] = inf;
-        d.DT[(int64_t)t * d.ld + k] = inf;
-    }
-    if (t == 0) d.alive[k] = 0;
-}
 
 // --------------------------------------------------------------------------
 // Repair: cooperative persistent kernel that decides warm or cold on the

@@ -64,8 +64,7 @@ cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, con
     if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d, rows_per); })) != cudaSuccess) return e;
     int gr = c.relax_grid;
     size_t sm = (size_t)d.span * sizeof(int32_t);
-    if ((e = launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p); })) != cudaSuccess) return e;
-    return launch(c, "insert_finish", [&] { k_insert_finish<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, p); });
+    return launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p); });
 }
 
 template <typename T> cudaError_t run_decrease(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w) {
@@ -178,7 +177,6 @@ template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d
     cudaError_t e;
     if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
     if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, cfg, "detect_remove")) != cudaSuccess) return e;
-    if ((e = launch(c, "tombstone", [&] { k_tombstone<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
     if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
     return run_grown<T>(c, d, 0, (T)0, cfg);
 }

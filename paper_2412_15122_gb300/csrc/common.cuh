@@ -129,7 +129,7 @@ struct Ctl {
 
 constexpr int ITEM_PAIRS = 32;          // affected pairs per re-relaxation work item
 constexpr int PASS1_COLS = 1024;        // columns of x per pass-1 work unit (the swept window stays in L2)
-constexpr int YSEG = 128;               // intermediates per work unit in passes >= 2
+constexpr int YSEG = 256;               // intermediates per work unit in passes >= 2
 constexpr int MAX_PASSES = 48;          // path doubling needs <= log2(hops) + 1 passes
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
 

@@ -28,6 +28,9 @@ What each function follows:
                               Dijkstra on it; Theorem al_correct).
 * ``all_shortest_paths_alg8`` Algorithm 8 on Algorithm 7's small graph.
 * ``need_update_list_alg12``  Algorithm 12 (Theorem theo_algo12).
+* ``key_node_list``,
+  ``need_update_list_alg11``  Algorithm 10's key_node_list of one pair with
+                              Algorithm 11's shortcut; Algorithm 11.
 """
 from __future__ import annotations
 
@@ -586,6 +589,60 @@ def need_update_list_alg12(M: np.ndarray, W: np.ndarray, alive: np.ndarray, k: i
             cand = [i] + [t for t in rem if t not in (i, j) and _on_some_shortest_path(M, i, j, t)] + [j]
             dist, _ = small_dijkstra(E[np.ix_(cand, cand)], 0)
             if dist[len(cand) - 1] > M[i, j]:
+                row.append(j)
+        lst[i] = row
+    return lst
+
+
+def key_node_list(M: np.ndarray, W: np.ndarray, alive: np.ndarray, i: int, j: int) -> Optional[List[int]]:
+    """key_node_list of pair (i, j) (Algorithm 10, steps for one pair, with
+    Algorithm 11's shortcut): the nodes common to every path in Algorithm 8's
+    path set, without i and j.  Algorithm 11 takes the joins through the
+    candidates off Psi(i, j) only (it replaces {i, j} by Psi's nodes in
+    Algorithm 8's split), since a join through a node of Psi adds nothing to
+    the intersection that Psi does not.  None when j is unreachable.  The path
+    set may miss shortest paths, so the list can only be larger than the set
+    of truly essential nodes."""
+    if i == j or M[i, j] == missing(M):
+        return None
+    cand = candidate_node_list(M, alive, i, j)
+    small = exact(np.asarray(W)[np.ix_(cand, cand)])
+    K = len(cand)
+    _, pred_i = small_dijkstra(small, 0)
+    _, pred_j = small_dijkstra(np.ascontiguousarray(small.T), K - 1)
+    psi = _tree_path(pred_i, 0, K - 1)
+    on_psi = set(psi)
+    common = set(psi)
+    for t in range(1, K - 1):
+        if t in on_psi:
+            continue
+        first = _tree_path(pred_i, 0, t)
+        second = _tree_path(pred_j, K - 1, t)[::-1]
+        if not first or not second:
+            continue
+        p = first + second[1:]
+        if len(set(p)) != len(p):
+            continue
+        common &= set(p)
+    common -= {0, K - 1}
+    return sorted(cand[a] for a in common)
+
+
+def need_update_list_alg11(M: np.ndarray, W: np.ndarray, alive: np.ndarray, k: int) -> Dict[int, List[int]]:
+    """Algorithm 11's need_update_list for removing node k: among the pairs
+    with SPD(i, j) >= SPD(i, k) + SPD(k, j) (Corollary 3), those whose
+    key_node_list holds k."""
+    alive = np.asarray(alive, dtype=bool)
+    miss = missing(M)
+    rem = [int(v) for v in np.flatnonzero(alive) if v != k]
+    lst: Dict[int, List[int]] = {}
+    for i in rem:
+        row = []
+        for j in rem:
+            if j == i or M[i, j] == miss or M[i, j] < _add(M[i, k], M[k, j], miss):
+                continue
+            key = key_node_list(M, W, alive, i, j)
+            if key is not None and k in key:
                 row.append(j)
         lst[i] = row
     return lst

@@ -1,5 +1,6 @@
-"""Pins for the oracle's path queries (Algorithm 7, Algorithm 8) and for
-Algorithm 12's need_update_list, against things other than the oracle itself:
+"""Pins for the oracle's path queries (Algorithm 7, Algorithm 8), Algorithm
+10/11's key_node_list and the need_update_lists of Algorithms 11 and 12,
+against things other than the oracle itself:
 
 * every loop-free path enumerated by brute force (n <= 7): the shortest ones
   and their length;
@@ -7,6 +8,7 @@ Algorithm 12's need_update_list, against things other than the oracle itself:
   two-edge routes has exactly m shortest paths, all found by Algorithm 8);
 * the definition behind Theorem theo_algo12: the pairs whose distance grows
   when a node is removed, by brute force on the graph without that node;
+* the essential nodes of a pair (on every shortest path), by brute force;
 * planted mistakes in copies of the oracle's steps.
 """
 import numpy as np
@@ -222,4 +224,93 @@ def test_planted_alg12_without_removing_k_is_caught(oracle_lib):
                         bad.add((i, j))
             good = {(i, j) for i, js in O.need_update_list_alg12(M, W, alive, k).items() for j in js}
             caught += bad != good
+    assert caught > 0
+
+
+def essential_nodes(W, i, j):
+    """Nodes on every shortest loop-free path i -> j, without i and j (brute force)."""
+    best, _ = shortest_simple_paths(W, i, j)
+    if not best:
+        return None
+    common = set(best[0])
+    for p in best[1:]:
+        common &= set(p)
+    return common - {i, j}
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("lo", [0, 1])
+def test_key_node_list_contains_the_essential_nodes(seed, lo, oracle_lib):
+    n = 7
+    W = rand_graph(n, seed, lo=lo, hi=4, p_missing=0.2 if seed % 2 else 0.0)
+    M = O.fw(W)
+    alive = np.ones(n, dtype=bool)
+    for i in range(n):
+        for j in range(n):
+            key = O.key_node_list(M, W, alive, i, j)
+            ess = essential_nodes(W, i, j) if i != j else None
+            if i == j or M[i, j] >= O.INF:
+                assert key is None
+                continue
+            assert ess <= set(key)                       # a path set can only miss paths
+            # the listed nodes lie on the first path (Psi), which is a shortest path
+            assert set(key) <= set(O.warm_shortest_path(M, W, alive, i, j)) - {i, j}
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_key_node_list_is_the_path_interior_when_paths_are_unique(seed, oracle_lib):
+    # weights U[1, 10^6] on 7 nodes: shortest paths are unique, so the
+    # intersection is the interior of the one path
+    n = 7
+    W = synth.complete_digraph_i32(n, 1, 10**6, 500 + seed)
+    M = O.fw(W)
+    alive = np.ones(n, dtype=bool)
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            best, _ = shortest_simple_paths(W, i, j)
+            assert len(best) == 1
+            assert O.key_node_list(M, W, alive, i, j) == sorted(best[0][1:-1])
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("lo", [0, 1])
+def test_alg11_list_between_alg12_and_corollary3(seed, lo, oracle_lib):
+    n = 7
+    W = rand_graph(n, seed, lo=lo, hi=4, p_missing=0.2 if seed % 2 else 0.0)
+    M = O.fw(W)
+    alive = np.ones(n, dtype=bool)
+    for k in range(n):
+        a11 = {(i, j) for i, js in O.need_update_list_alg11(M, W, alive, k).items() for j in js}
+        a12 = {(i, j) for i, js in O.need_update_list_alg12(M, W, alive, k).items() for j in js}
+        c3 = {(i, j) for i, js in O.need_update_list(M, alive, k).items() for j in js}
+        assert a12 <= a11 <= c3
+
+
+def test_alg11_equals_alg12_when_paths_are_unique(oracle_lib):
+    n = 7
+    for seed in range(4):
+        W = synth.complete_digraph_i32(n, 1, 10**6, 600 + seed)
+        M = O.fw(W)
+        alive = np.ones(n, dtype=bool)
+        for k in range(n):
+            assert O.need_update_list_alg11(M, W, alive, k) == O.need_update_list_alg12(M, W, alive, k)
+
+
+def test_planted_key_node_list_without_intersection_is_caught(oracle_lib):
+    # Taking Psi's interior alone (no intersection with the other paths) lists
+    # nodes that some other shortest path avoids: the essential-node pin fails.
+    caught = 0
+    for seed in range(8):
+        W = rand_graph(6, seed, lo=0, hi=3)
+        M = O.fw(W)
+        alive = np.ones(6, dtype=bool)
+        for i in range(6):
+            for j in range(6):
+                if i == j or M[i, j] >= O.INF:
+                    continue
+                bad = set(O.warm_shortest_path(M, W, alive, i, j)) - {i, j}
+                ess = essential_nodes(W, i, j)
+                caught += bad != ess
     assert caught > 0

@@ -31,6 +31,8 @@ What each function follows:
 * ``key_node_list``,
   ``need_update_list_alg11``  Algorithm 10's key_node_list of one pair with
                               Algorithm 11's shortcut; Algorithm 11.
+* ``fw_minimax``, ``add_node_minimax``, ``need_update_list_minimax``
+                              the Discussion's minimax (bottleneck) variant.
 """
 from __future__ import annotations
 
@@ -645,4 +647,83 @@ def need_update_list_alg11(M: np.ndarray, W: np.ndarray, alive: np.ndarray, k: i
             if key is not None and k in key:
                 row.append(j)
         lst[i] = row
+    return lst
+
+
+# ---------------------------------------------------------------------------
+# Minimax (bottleneck) paths: the Discussion's variant.  The value of a path
+# is its largest edge weight; SPD becomes the least such value over paths.
+# ---------------------------------------------------------------------------
+
+def fw_minimax(W: np.ndarray, alive: Optional[np.ndarray] = None) -> np.ndarray:
+    """Minimax distance matrix by Floyd-Warshall in the (min, max) semiring:
+    D[i][j] = min(D[i][j], max(D[i][k], D[k][j])) for k in order."""
+    D = exact(W, alive)
+    n = D.shape[0]
+    for k in range(n):
+        D = np.minimum(D, np.maximum(D[:, k:k + 1], D[k:k + 1, :]))
+    return D
+
+
+def brute_force_minimax(W: np.ndarray, alive: Optional[np.ndarray] = None) -> np.ndarray:
+    """Minimax distances by their definition: the least largest edge over every
+    loop-free path (n <= 8)."""
+    E = exact(W, alive)
+    n = E.shape[0]
+    assert n <= 9, "brute force is exponential"
+    miss = missing(E)
+    D = np.full((n, n), miss, dtype=E.dtype)
+    live = [v for v in range(n) if E[v, v] == 0]
+    for s in live:
+        D[s, s] = 0
+        stack = [(s, E.dtype.type(0), 1 << s)]
+        while stack:
+            u, worst, seen = stack.pop()
+            for v in live:
+                if seen >> v & 1 or E[u, v] == miss:
+                    continue
+                b = max(worst, E[u, v])
+                if b < D[s, v]:
+                    D[s, v] = b
+                stack.append((v, b, seen | (1 << v)))
+    return D
+
+
+def add_node_minimax(M: np.ndarray, alive: np.ndarray, p: int, in_w: np.ndarray, out_w: np.ndarray) -> np.ndarray:
+    """Section 3.1 in the (min, max) semiring: Corollaries 1 and 2 with max in
+    place of +, then Theorem 3's min(M[i][j], max(in[i], out[j]))."""
+    alive = np.asarray(alive, dtype=bool)
+    assert not alive[p]
+    miss = missing(M)
+    live = np.flatnonzero(alive)
+    wi = np.array(np.asarray(in_w), dtype=M.dtype)
+    wo = np.array(np.asarray(out_w), dtype=M.dtype)
+    if not is_float(M):
+        wi[wi >= INF_I32] = INF
+        wo[wo >= INF_I32] = INF
+    n = M.shape[0]
+    out_row = np.full(n, miss, dtype=M.dtype)
+    in_col = np.full(n, miss, dtype=M.dtype)
+    for r in live:
+        if len(live):
+            out_row[r] = np.min(np.maximum(wo[live], M[live, r]))
+            in_col[r] = np.min(np.maximum(M[r, live], wi[live]))
+    M2 = M.copy()
+    for i in live:
+        M2[i, live] = np.minimum(M[i, live], np.maximum(in_col[i], out_row[live]))
+    M2[p, :] = out_row
+    M2[:, p] = in_col
+    M2[p, p] = 0
+    return M2
+
+
+def need_update_list_minimax(M: np.ndarray, alive: np.ndarray, k: int) -> Dict[int, List[int]]:
+    """Corollary 3's test for removing k in the (min, max) semiring: (i, j) is
+    listed unless SPD(i, j) < max(SPD(i, k), SPD(k, j))."""
+    alive = np.asarray(alive, dtype=bool)
+    miss = missing(M)
+    rem = [int(v) for v in np.flatnonzero(alive) if v != k]
+    lst: Dict[int, List[int]] = {}
+    for i in rem:
+        lst[i] = [j for j in rem if j != i and M[i, j] != miss and not (M[i, j] < max(M[i, k], M[k, j]))]
     return lst

@@ -276,7 +276,11 @@ apsp_status apsp_set_exact_list(apsp_graph *g, int32_t on);
  *                          by Theorem theo_algo12 exactly the pairs whose
  *                          distance grows.  Pairs whose small graph has more
  *                          than 126 candidates stay listed (always safe).
- * The last two pay off where ties between routes are common. */
+ * On this library's pair-parallel repair neither filter pays for itself on
+ * the workloads measured (n = 16384 undirected Euclidean updates): the
+ * direct-edge test drops 3 % of the pairs, and Algorithm 12's test, which
+ * cuts the list to under a tenth, costs about 20x the re-relaxation it
+ * spares.  They serve comparisons with the paper's Algorithm 11 / 12. */
 typedef enum { APSP_LIST_COROLLARY3 = 0, APSP_LIST_DIRECT_EDGE = 1, APSP_LIST_ALGORITHM12 = 2 } apsp_list_mode;
 apsp_status apsp_set_list_mode(apsp_graph *g, apsp_list_mode mode);
 

@@ -32,6 +32,10 @@
 // more candidates (only possible with many equal-length routes, e.g. zero
 // weights) is marked deferred and redone by a second launch of PQ_WIDE_GRID
 // CTAs whose per-CTA arrays sit in a library-owned global scratch area.
+//
+// The end of the file holds Algorithm 12's test before a repair
+// (alg12_keep, k_det_alg12), which reuses the warp tier's scan and small
+// Dijkstra with the removed node left out.
 #pragma once
 
 #include "kernels.cuh"

@@ -447,6 +447,13 @@ apsp_status apsp_probe_addmin_rate(apsp_dtype dtype, double *pair_ops_per_s);
  * thread.  The ceiling of the first re-relaxation pass, whose reads are
  * served by L2.  Takes a few milliseconds; waits for the device. */
 apsp_status apsp_probe_l2_read_gbs(double *gbs);
+/* Failure-detection self-test (no paper counterpart): launches two CTAs
+ * cooperatively that meet at the same bounded grid barrier the repair kernel
+ * uses.  With lose_cta set, one CTA leaves without arriving, so the other's
+ * wait ends only by its 2-second limit; *status_out is then APSP_E_TIMEOUT
+ * (else APSP_OK) and the device stays usable.  Nothing faults, traps or hangs.
+ * Uses the legacy default stream and waits. */
+apsp_status apsp_selftest_barrier_timeout(int32_t lose_cta, int32_t *status_out);
 
 /* ----- insertion without allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that

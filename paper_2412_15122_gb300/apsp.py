@@ -121,6 +121,7 @@ def _load():
         "apsp_query_all_paths": [P, I32, I32, P, I64, P, I32, ctypes.POINTER(I32), ctypes.POINTER(I64)],
         "apsp_probe_addmin_rate": [I32, ctypes.POINTER(ctypes.c_double)],
         "apsp_probe_l2_read_gbs": [ctypes.POINTER(ctypes.c_double)],
+        "apsp_selftest_barrier_timeout": [I32, ctypes.POINTER(I32)],
         "apsp_copy_D": [P, P, I64, I32],
         "apsp_copy_W": [P, P, I64, I32],
         "apsp_copy_alive": [P, P],
@@ -314,6 +315,14 @@ def apsp_probe_l2_read_gbs() -> float:
     r = ctypes.c_double()
     _check(_load().apsp_probe_l2_read_gbs(ctypes.byref(r)), "apsp_probe_l2_read_gbs")
     return r.value
+
+
+def apsp_selftest_barrier_timeout(lose_cta: bool) -> int:
+    """Status the bounded grid barrier reports when one CTA never arrives (or all do)."""
+    st = ctypes.c_int32()
+    _check(_load().apsp_selftest_barrier_timeout(1 if lose_cta else 0, ctypes.byref(st)),
+           "apsp_selftest_barrier_timeout")
+    return st.value
 
 
 def apsp_copy_D(g: int, dst, ld: int, on_device: bool):

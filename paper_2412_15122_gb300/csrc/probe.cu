@@ -137,7 +137,32 @@ apsp_status probe_l2(double *gbs) {
     return APSP_OK;
 }
 
+// Self-test of the bounded grid barrier that the cooperative repair kernel
+// uses: with `lose` set the last CTA leaves without arriving, so the others'
+// wait can only end by its time limit, recording ERR_TIMEOUT.
+__global__ void k_selftest_barrier(apsp::Ctl *ctl, int lose) {
+    if (lose && blockIdx.x == gridDim.x - 1) return;
+    apsp::grid_barrier(ctl, apsp::NoLeader{});
+}
+
 }  // namespace
+
+extern "C" apsp_status apsp_selftest_barrier_timeout(int32_t lose_cta, int32_t *status_out) {
+    if (!status_out) return APSP_E_ARG;
+    apsp::Ctl *ctl = nullptr;
+    if (cudaMalloc(&ctl, sizeof(apsp::Ctl)) != cudaSuccess) return APSP_E_NOMEM;
+    cudaError_t e = cudaMemset(ctl, 0, sizeof(apsp::Ctl));
+    int lose = lose_cta ? 1 : 0;
+    void *args[] = {(void *)&ctl, (void *)&lose};
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((void *)k_selftest_barrier, dim3(2), dim3(32), args, 0, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    uint32_t err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, &ctl->err, sizeof(err), cudaMemcpyDeviceToHost);
+    cudaFree(ctl);
+    if (e != cudaSuccess) return APSP_E_CUDA;
+    *status_out = (err & apsp::ERR_TIMEOUT) ? APSP_E_TIMEOUT : APSP_OK;
+    return APSP_OK;
+}
 
 extern "C" apsp_status apsp_probe_l2_read_gbs(double *gbs) {
     if (!gbs) return APSP_E_ARG;

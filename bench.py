@@ -184,7 +184,9 @@ def run_reference(args):
     if rank != 0:
         return
     W = synth.complete_digraph_i32(N, W_LO, W_HI, SEED)
-    rows = 128
+    # a bounded sample per step: about 2560 source rows over the whole timed
+    # run, at least 64 a step so the oracle's per-call setup stays amortised
+    rows = max(64, min(128, 2560 // max(1, args.steps)))
     for _ in range(args.warmup):
         cpu_oracle_rate(W, rows)
     rates, times, cores = [], [], 1

@@ -314,3 +314,37 @@ def test_planted_key_node_list_without_intersection_is_caught(oracle_lib):
                 ess = essential_nodes(W, i, j)
                 caught += bad != ess
     assert caught > 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_alg7_float_paths_are_shortest(seed, oracle_lib):
+    # lognormal fp32 weights: the float candidate test (with its slack) keeps
+    # every node of some shortest path, so the small graph reaches the optimum
+    n = 7
+    W = synth.lognormal_digraph_f32(n, 80 + seed)
+    M = O.fw(W)
+    alive = np.ones(n, dtype=bool)
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            p = O.warm_shortest_path(M, W, alive, i, j)
+            best, L = shortest_simple_paths(W.astype(np.float64), i, j)
+            assert abs(O.path_length(W, p) - L) <= 1e-12 * L
+            assert p[0] == i and p[-1] == j and len(set(p)) == len(p)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_alg12_undirected_list_is_the_pairs_that_grow(seed, oracle_lib):
+    n = 7
+    W = rand_graph(n, 120 + seed, lo=0, hi=3, undirected=True)
+    alive = np.ones(n, dtype=bool)
+    M = O.fw(W)
+    for k in range(n):
+        a2 = alive.copy()
+        a2[k] = False
+        after = O.brute_force_apsp(W, a2)
+        grow = {(i, j) for i in range(n) for j in range(n) if i != j and k not in (i, j) and after[i, j] > M[i, j]}
+        got = {(i, j) for i, js in O.need_update_list_alg12(M, W, alive, k).items() for j in js}
+        assert got == grow
+        assert all((j, i) in got for (i, j) in got)      # symmetric, like the graph

@@ -1065,6 +1065,9 @@ def main():
             "cold_fw_ms": cold_ms,
             "cold_fw_roofline": fw_roofline,
             "repair_roofline": repair_roofline,
+            "roofline_note": ("roofline: the dominant HBM-bound kernel (a full streaming pass over D); the kernel with "
+                              "the most total time is the warm repair, whose first pass is served by L2 and is "
+                              "reported against the measured L2 read bandwidth in repair_roofline"),
             "profiled_pass_ms": prof_ms,
             "update_stats": stats,
             "warm_updates_per_cold_fw": value * cold_ms / 1000.0,

@@ -594,6 +594,64 @@ def run_batch_study(args):
     print(json.dumps(out))
 
 
+def run_ratio_study(args):
+    """Experiments I and II of the paper on the GPU: on directed complete
+    graphs (int32 U[1, 1e6]) of N = 1000, 2000, 3000, 5000 nodes, the time of a
+    warm-start update divided by a cold Floyd-Warshall of the updated graph,
+    r = APSP_warm / APSP_cold (Eq. (equ:ratioo)); 20 random node removals
+    (Experiment I) and 20 random edge modifications to a new U[1, 1e6] weight
+    (Experiment II) per size, each timed alone with CUDA events."""
+    import torch
+    from paper_2412_15122_gb300 import Graph, build
+    build.build()
+    out = {"study": "warm/cold ratios (Experiments I and II)",
+           "workload": "directed complete graphs, int32 U[1,1e6]; random node removal / random edge to a new U[1,1e6] weight",
+           "sizes": {}}
+    stream = torch.cuda.Stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1)
+
+    for n in (1000, 2000, 3000, 5000):
+        W = synth.complete_digraph_i32(n, W_LO, W_HI, 900 + n)
+        g = Graph(W, n + 32, stream=stream)
+        g.sync()
+        for _ in range(3):   # warm-up of every kernel
+            g.recompute()
+        g.sync()
+        reps = args.study_reps
+        ks = synth.uniform_int(901, n, reps, 0, n - 1)
+        rm, ed = [], []
+        alive = np.ones(n, dtype=bool)
+        for t in range(reps):
+            live = np.flatnonzero(alive)
+            k = int(live[ks[t] % len(live)])
+            warm = timed(lambda: g.remove_node(k))
+            alive[k] = False
+            cold = timed(g.recompute)
+            rm.append(warm / cold)
+        uv = synth.uniform_int(902, n, 2 * reps, 0, n - 1)
+        nw = synth.uniform_int(903, n, reps, W_LO, W_HI)
+        for t in range(reps):
+            live = np.flatnonzero(alive)
+            u, v = int(live[uv[2 * t] % len(live)]), int(live[uv[2 * t + 1] % len(live)])
+            if u == v:
+                v = int(live[(uv[2 * t + 1] + 1) % len(live)])
+            warm = timed(lambda: g.update_edge(u, v, int(nw[t])))
+            cold = timed(g.recompute)
+            ed.append(warm / cold)
+        g.close()
+        out["sizes"][str(n)] = {"removal_ratio_mean": float(np.mean(rm)), "removal_ratio_sd": float(np.std(rm)),
+                                "edge_ratio_mean": float(np.mean(ed)), "edge_ratio_sd": float(np.std(ed)),
+                                "reps": reps}
+    print(json.dumps(out))
+
+
 def run_path_study(args):
     """Warm-start path queries (Algorithm 7) on directed complete graphs with
     int32 weights U[1, 1e6]: uniform random pairs, answered in batches through
@@ -834,7 +892,8 @@ def main():
     ap.add_argument("--serve-per-size", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--study-queries", type=int, default=4096)
-    ap.add_argument("--study", choices=["dispatch", "batch", "serve", "paths"],
+    ap.add_argument("--study-reps", type=int, default=20)
+    ap.add_argument("--study", choices=["dispatch", "batch", "serve", "paths", "ratios"],
                     help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
                          "always-warm and always-cold on n=16384 undirected Euclidean updates")
     ap.add_argument("--study-updates", type=int, default=100)
@@ -854,6 +913,8 @@ def main():
         return run_serve_study(args)
     if args.study == "paths":
         return run_path_study(args)
+    if args.study == "ratios":
+        return run_ratio_study(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

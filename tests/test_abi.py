@@ -62,3 +62,67 @@ def test_init_rejects_bad_arguments_without_touching_the_device(lib):
     # capacity < n and capacity above the maximum are argument errors
     assert lib.apsp_init(ctypes.byref(h), None, 4, 2, 0, 0, None, None) in (1, 6)
     assert lib.apsp_init(None, None, 0, 1, 0, 0, None, None) == 1
+
+
+def _header_constants():
+    """#define values and enumerator values of include/apsp.h."""
+    text = open(os.path.join(ROOT, "include", "apsp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    vals = {}
+    for m in re.finditer(r"#define\s+(APSP_\w+)\s+(0x[0-9A-Fa-f]+|\d+)", text):
+        vals[m.group(1)] = int(m.group(2), 0)
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for m in re.finditer(r"(APSP_\w+)\s*=\s*(\d+)u?", body):
+            vals[m.group(1)] = int(m.group(2))
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    from paper_2412_15122_gb300 import apsp
+    h = _header_constants()
+    assert h["APSP_INF_I32"] == apsp.APSP_INF_I32
+    assert h["APSP_MAX_CAPACITY"] == apsp.APSP_MAX_CAPACITY
+    assert h["APSP_MODEL_NPARAM"] == apsp.MODEL_NPARAM and h["APSP_MODEL_NTRAIN"] == apsp.MODEL_NTRAIN
+    assert (h["APSP_I32"], h["APSP_F32"]) == (apsp.APSP_I32, apsp.APSP_F32)
+    assert (h["APSP_UNDIRECTED"], h["APSP_D_GIVEN"], h["APSP_DEVICE_INPUT"]) == \
+        (apsp.APSP_UNDIRECTED, apsp.APSP_D_GIVEN, apsp.APSP_DEVICE_INPUT)
+    for code, name in apsp.STATUS.items():
+        assert h[name] == code, name
+    assert [h["APSP_DISPATCH_DELTA"], h["APSP_DISPATCH_ALWAYS_WARM"], h["APSP_DISPATCH_ALWAYS_COLD"],
+            h["APSP_DISPATCH_MODEL"]] == [apsp.DISPATCH[k] for k in ("delta", "warm", "cold", "model")]
+    assert [h["APSP_LIST_COROLLARY3"], h["APSP_LIST_DIRECT_EDGE"], h["APSP_LIST_ALGORITHM12"]] == \
+        [apsp.LIST_MODES[k] for k in ("corollary3", "direct_edge", "algorithm12")]
+    assert [h["APSP_BATCH_ADD"], h["APSP_BATCH_REMOVE"], h["APSP_BATCH_EDGE"], h["APSP_BATCH_QUERY"]] == \
+        [apsp.BATCH_OPS[k] for k in ("add", "remove", "edge", "query")]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # sizes and field offsets of the C structs, as a C compiler lays them out
+    # from include/apsp.h, equal those of the ctypes mirrors in the binding
+    import shutil
+    import subprocess
+    from paper_2412_15122_gb300 import apsp
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    structs = {"apsp_stats": apsp.apsp_stats, "apsp_info": apsp.apsp_info, "apsp_batch_item": apsp.apsp_batch_item,
+               "apsp_request": apsp.apsp_request, "apsp_request_result": apsp.apsp_request_result,
+               "apsp_serve_config": apsp.apsp_serve_config, "apsp_profile_entry": apsp.apsp_profile_entry,
+               "apsp_batch_info": apsp.apsp_batch_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "apsp.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"

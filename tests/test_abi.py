@@ -126,3 +126,12 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    # no silent fallback: a missing CUDA library is an error, not a CPU path
+    from paper_2412_15122_gb300 import apsp
+    monkeypatch.setattr(apsp, "_lib", None)
+    monkeypatch.setattr(apsp, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libapsp_gb300.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        apsp.lib()

@@ -201,7 +201,7 @@ apsp_status apsp_query_batch(apsp_graph *g, const int32_t *uv, int32_t count, vo
  * graph of the weights among the candidates.  Ties: the next settled node is
  * the one of least distance and lowest candidate index; a predecessor changes
  * only on a strict improvement.  The float candidate test keeps t within a
- * relative slack of 2^-16 (extra candidates only enlarge the small graph).
+ * relative slack of 2^-8 (extra candidates only enlarge the small graph).
  * Result: the slots of one shortest path u, ..., v; [u] when u == v; empty
  * (length 0) when v is unreachable.  All buffers are host memory owned by the
  * caller; the calls wait for the GPU.  Errors: APSP_E_NODE for a dead or
@@ -243,6 +243,17 @@ apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *stats);
 /* Wait for all work on the handle's stream; returns any deferred device error. */
 apsp_status apsp_sync(apsp_graph *g);
 
+/* The list of (i, j) pairs that the last update re-relaxed or handed to the
+ * cold path: for a removal of k, the need_update_list of Section 3.2 (every
+ * pair of live i, j other than k with D[i][k] + D[k][j] == D[i][j], Corollary
+ * 3), for a tight edge increase the pairs whose every shortest path may use
+ * the edge; filtered as apsp_set_list_mode chose.  ij receives 2 * *count
+ * int32 (i, j, i, j, ...) in no particular order; *count = 0 after any other
+ * update.  With ij NULL only *count is written; cap (pairs) below *count
+ * gives APSP_E_ARG; a list that overflowed the scratch gives
+ * APSP_E_CAPACITY.  Host memory; waits. */
+apsp_status apsp_copy_last_list(apsp_graph *g, int32_t *ij, int64_t cap, int64_t *count);
+
 /* ----- dispatch ----------------------------------------------------------- */
 
 /* Choose how removals and edge increases pick warm or cold (default:
@@ -256,7 +267,7 @@ apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta);
  * With `on`, each removal / increase also counts that list after its repair
  * (one extra kernel over the listed pairs, comparing each final distance with
  * its old tight sum) and apsp_last_stats reports grown_pairs / grown_rows /
- * grown_cost.  int32: exact; fp32: "grew" beyond the 2^-16 tightness slack.
+ * grown_cost.  int32: exact; fp32: "grew" beyond the 2^-8 tightness slack.
  * The result of every update is the same either way. */
 apsp_status apsp_set_exact_list(apsp_graph *g, int32_t on);
 
@@ -461,23 +472,29 @@ apsp_status apsp_selftest_barrier_timeout(int32_t lose_cta, int32_t *status_out)
  * must not block on cudaMalloc, which synchronises the device; a framework
  * that owns all device memory through its own pool; a fixed memory budget).
  *
- * Adds node p to a caller-owned APSP matrix D in place, as apsp_add_node does
- * (Section 3.1): D (device, 16-byte aligned, leading dimension ld elements, a
- * multiple of 4 and >= n_slots) holds on entry the APSP matrix of the live
- * slots among the first n_slots (row and column p are ignored); on return it
- * also holds row and column p.  alive (device, n_slots int32: 1 = live, p must
- * be 0 and is not changed), in_w / out_w (device, n_slots weights t -> p and
- * p -> t) are only read.  n_slots must be a multiple of 4 in
- * [4, APSP_NOALLOC_MAX_SLOTS] (APSP_E_CAPACITY above the maximum, APSP_E_ARG
- * otherwise); negative or NaN weights are read as missing edges.
+ * Adds node p to a caller-owned APSP matrix D in place and gives the matrix
+ * apsp_add_node gives: D (device, 16-byte aligned, leading dimension ld
+ * elements, a multiple of 4 and >= n_slots) holds on entry the APSP matrix of
+ * the live slots among the first n_slots; on return it also holds row and
+ * column p.  Only entries whose row and column are both live and not p are
+ * read: row and column p, the rows and columns of dead slots and the padding
+ * beyond n_slots may hold anything (int32 values >= APSP_INF_I32 read as
+ * missing).  Row p is written over all n_slots columns (missing at dead
+ * slots) and column p at live rows; no other entry of a dead slot changes.
+ * alive (device, n_slots int32: 1 = live, p must be 0 and is not changed),
+ * in_w / out_w (device, n_slots weights t -> p and p -> t) are only read.
+ * n_slots must be a multiple of 4 in [4, APSP_NOALLOC_MAX_SLOTS]
+ * (APSP_E_CAPACITY above the maximum, APSP_E_ARG otherwise); negative or NaN
+ * weights are read as missing edges.
  *
  * Scratch lives in one fixed library-owned device array of
  * 4 * APSP_NOALLOC_MAX_SLOTS * 4 bytes (256 KiB) that every GPU loading the
  * library holds until the process exits; the call allocates nothing and does
- * not wait for the GPU.  The first call on a device looks up the array's
- * device address, so make it before any CUDA stream capture.  All calls share
- * the array (each re-initialises it): calls whose work overlaps on the GPU
- * race and must be serialised by the caller. */
+ * not wait for the GPU.  Each call looks up the array's device address on the
+ * current device; the first call on a device (or the first after its context
+ * was reset) loads the library's device code, so make it before any CUDA
+ * stream capture.  All calls share the array (each re-initialises it): calls
+ * whose work overlaps on the GPU race and must be serialised by the caller. */
 #define APSP_NOALLOC_MAX_SLOTS 16384
 apsp_status apsp_add_node_noalloc(void *D, int64_t ld, int32_t n_slots, const int32_t *alive,
                                   apsp_dtype dtype, const void *in_w, const void *out_w,

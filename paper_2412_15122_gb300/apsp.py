@@ -127,6 +127,7 @@ def _load():
         "apsp_copy_alive": [P, P],
         "apsp_info_get": [P, ctypes.POINTER(apsp_info)],
         "apsp_last_stats": [P, ctypes.POINTER(apsp_stats)],
+        "apsp_copy_last_list": [P, P, I64, ctypes.POINTER(I64)],
         "apsp_sync": [P],
         "apsp_set_dispatch": [P, I32, ctypes.c_double],
         "apsp_set_exact_list": [P, I32],
@@ -349,6 +350,15 @@ def apsp_last_stats(g: int) -> dict:
     s = apsp_stats()
     _check(_load().apsp_last_stats(g, ctypes.byref(s)), "apsp_last_stats")
     return s.as_dict()
+
+
+def apsp_copy_last_list(g: int) -> np.ndarray:
+    """(count, 2) int32 array of the (i, j) pairs the last update listed."""
+    cnt = ctypes.c_int64(0)
+    _check(_load().apsp_copy_last_list(g, None, 0, ctypes.byref(cnt)), "apsp_copy_last_list")
+    out = np.empty((max(cnt.value, 1), 2), dtype=np.int32)
+    _check(_load().apsp_copy_last_list(g, out.ctypes.data, cnt.value, ctypes.byref(cnt)), "apsp_copy_last_list")
+    return out[: cnt.value]
 
 
 def apsp_sync(g: int):
@@ -674,6 +684,9 @@ class Graph:
 
     def stats(self) -> dict:
         return apsp_last_stats(self.h)
+
+    def last_list(self) -> np.ndarray:
+        return apsp_copy_last_list(self.h)
 
     def sync(self):
         apsp_sync(self.h)

@@ -119,6 +119,7 @@ template <typename T> __device__ __forceinline__ T b_dot_min(const BG<T> &g, int
 // nothing; returns false when the pass cap is reached.
 template <typename T>
 __device__ bool b_relax(const BG<T> &g, const uint32_t *mask, int words, int span, const int32_t *rows, int nrows) {
+    using M = MinPlus<T>;
     __shared__ int changed_s;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int pass = 0; pass < MAX_PASSES; ++pass) {
@@ -136,7 +137,7 @@ __device__ bool b_relax(const BG<T> &g, const uint32_t *mask, int words, int spa
                         const int j = (w0 + src) * 32 + __ffs(m) - 1;
                         m &= m - 1;
                         const T cand = b_dot_min(g, i, j, span);
-                        if (lane == 0 && cand < __ldcg(&g.d(i, j))) {
+                        if (lane == 0 && M::lowers(cand, __ldcg(&g.d(i, j)))) {
                             g.set(i, j, cand);
                             changed = true;
                         }

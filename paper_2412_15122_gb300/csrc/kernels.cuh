@@ -1289,7 +1289,7 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
                 }
             }
             const T best = acc[0];
-            const bool lower = mine && best < cur;
+            const bool lower = mine && M::lowers(best, cur);
             if (mine && (pass == 2 || lower)) {
                 const int32_t key = M::key(M::mn(best, cur));
                 atomicMin(reinterpret_cast<int32_t *>(d.D + (int64_t)i * ld + j), key);

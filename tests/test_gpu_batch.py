@@ -155,9 +155,17 @@ def test_batch_then_single_calls_continue(lib):
     b = Batch()
     b.run([g], [(0, "remove", 3), (0, "edge", 4, 5, 1.0)])
     g.remove_node(10)   # the single-graph path sees the batch's state
-    Wm = g.W()
-    alive = g.alive().astype(bool)
+    # the test's own copy of the weights after the three updates
+    Wm = np.full((80, 80), synth.INF_I32, np.int32)
+    Wm[:64, :64] = W
+    alive = np.zeros(80, bool)
+    alive[:64] = True
+    for k in (3, 10):
+        alive[k] = False
+        Wm[k, :] = Wm[:, k] = synth.INF_I32
+    Wm[4, 5] = 1
     m = g.info()["n_slots"]
+    assert np.array_equal(g.alive()[:m].astype(bool), alive[:m])
     live = np.flatnonzero(alive[:m])
     ref = O.to_i32(O.fw(Wm[:m, :m], alive[:m]))
     np.testing.assert_array_equal(g.D()[np.ix_(live, live)], ref[np.ix_(live, live)])

@@ -239,21 +239,58 @@ def test_worked_example_need_update_list_on_gpu():
         g.close()
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_affected_set_matches_oracle_need_update_list(seed):
-    # GPU detection lists exactly the need_update_list of Section 3.2.
+def pair_set(lst):
+    """{i: [j, ...]} (the oracle's lists) -> set of (i, j)."""
+    return {(int(i), int(j)) for i, js in lst.items() for j in js}
+
+
+def device_pairs(g):
+    """The device's list of the last update as a set; no pair listed twice."""
+    ij = g.last_list()
+    s = {(int(a), int(b)) for a, b in ij}
+    assert len(s) == len(ij), "a pair is listed twice"
+    return s
+
+
+@pytest.mark.parametrize("case", ["uniform1", "uniform2", "uniform3", "euclid", "euclid_fp"])
+def test_affected_set_matches_oracle_need_update_list(case):
+    # The device detection lists exactly the need_update_list of Section 3.2,
+    # pair by pair: removals on a directed uniform graph and on a tie-heavy
+    # undirected Euclidean graph (rounded distances, weights <= 40), three
+    # removals in a row each.
     n = 180
-    W = synth.complete_digraph_i32(n, 1, 100, seed)
-    M = O.fw(W)
-    alive = np.ones(n, dtype=bool)
-    k = int(synth.uniform_int(seed, 5, 1, 0, n - 1)[0])
-    kept = O.need_update_list(M, alive, k)
-    g = G(W, n)
+    und = case.startswith("euclid")
+    if und:
+        W, _ = synth.euclidean_undirected_i32(n, 31, scale=40.0)
+    else:
+        W = synth.complete_digraph_i32(n, 1, 100, int(case[-1]))
+    if case == "euclid_fp":
+        W = np.where(W >= synth.INF_I32, np.inf, W).astype(np.float32) * np.float32(0.25)
+    g = G(W, n, undirected=und)
     g.set_dispatch("warm")
-    g.remove_node(k)
-    st = g.stats()
-    assert st["affected_pairs"] == sum(len(v) for v in kept.values())
-    assert st["affected_rows"] == sum(1 for v in kept.values() if v)
+    mir = Mirror(W, n, und)
+    for t in range(3):
+        live = mir.live()
+        M = mir.expected(n)
+        k = int(live[synth.uniform_int(len(case), 5 + t, 1, 0, len(live) - 1)[0]])
+        kept = O.need_update_list(M, mir.alive, k)
+        g.remove_node(k)
+        mir.remove(k)
+        st = g.stats()
+        want = pair_set(kept)
+        if case == "euclid_fp":
+            # fp32 lists by the conservative slack test: a superset of the
+            # exact list, its extra pairs tight within the 2^-8 slack
+            got = device_pairs(g)
+            assert want <= got
+            for (i, j) in got - want:
+                via, d = M[i, k] + M[k, j], M[i, j]
+                assert via <= d * (1 + 2.0 ** -7), (i, j, via, d)
+        else:
+            assert device_pairs(g) == want
+            assert st["affected_rows"] == sum(1 for v in kept.values() if v)
+        assert st["affected_pairs"] == len(g.last_list())
+        assert_same(g, mir, f"{case} remove {k}")
     g.close()
 
 
@@ -287,13 +324,16 @@ def test_exact_list_matches_oracle_algorithm12(seed, undirected, list_mode):
         g.remove_node(k)
         mir.remove(k)
         st = g.stats()
+        got = device_pairs(g)
         if list_mode == "direct_edge":
+            assert got == {(i, j) for (i, j) in pair_set(cor3) if Wx[i, j] != M[i, j]}
             assert st["affected_pairs"] == _direct_edge_pairs(cor3, Wx, M)
         elif list_mode == "algorithm12":   # the device list is Algorithm 12's (n < 126: no pair stays unchecked)
-            assert st["affected_pairs"] == sum(len(v) for v in alg12.values())
+            assert got == pair_set(alg12)
             assert st["affected_rows"] == sum(1 for v in alg12.values() if v)
         else:
-            assert st["affected_pairs"] == sum(len(v) for v in cor3.values())
+            assert got == pair_set(cor3)
+        assert st["affected_pairs"] == len(got)
         assert st["grown_pairs"] == sum(len(v) for v in alg12.values())
         assert st["grown_rows"] == sum(1 for v in alg12.values() if v)
         N = len(live)
@@ -314,14 +354,17 @@ def test_exact_list_matches_oracle_algorithm12(seed, undirected, list_mode):
     after = mir.expected(cap)
     st = g.stats()
     Wx = O.exact(mir.W, mir.alive)                   # the new weight: the changed edge is never dropped
-    if list_mode == "direct_edge":
-        assert st["affected_pairs"] == sum(1 for (i, j) in cand if Wx[i, j] != before[i, j])
-    elif list_mode == "algorithm12":
-        assert st["affected_pairs"] == st["grown_pairs"]
-    else:
-        assert st["affected_pairs"] == len(cand)
     grown = (after > before) & np.outer(mir.alive, mir.alive)
     np.fill_diagonal(grown, False)
+    got = device_pairs(g)
+    cand_set = {(int(i), int(j)) for (i, j) in cand}
+    if list_mode == "direct_edge":
+        assert got == {(i, j) for (i, j) in cand_set if Wx[i, j] != before[i, j]}
+    elif list_mode == "algorithm12":
+        assert got == {(int(i), int(j)) for i, j in np.argwhere(grown)}
+    else:
+        assert got == cand_set
+    assert st["affected_pairs"] == len(got)
     assert st["grown_pairs"] == int(grown.sum())
     assert st["grown_rows"] == int(grown.any(1).sum())
     assert_same(g, mir, "increase")
@@ -495,18 +538,20 @@ def test_graphs_of_different_sizes_coexist():
     build.build()
     Wb = synth.complete_digraph_i32(700, 1, 1000, 71)
     big = Graph(Wb, 720)
+    mir = Mirror(Wb, 720)                            # the test's own copy of the weights
     small = Graph(synth.complete_digraph_i32(40, 1, 1000, 72), 48)
     big.remove_node(5)
+    mir.remove(5)
     big.update_edge(3, 9, 1)
+    mir.edge(3, 9, 1)
     big.update_edge(10, 11, 4000)
-    p = big.add_node(synth.uniform_int(73, 1, 720, 1, 1000).astype(np.int32),
-                     synth.uniform_int(73, 2, 720, 1, 1000).astype(np.int32))
+    mir.edge(10, 11, 4000)
+    iw = synth.uniform_int(73, 1, 720, 1, 1000).astype(np.int32)
+    ow = synth.uniform_int(73, 2, 720, 1, 1000).astype(np.int32)
+    p = big.add_node(iw, ow)
+    assert p == mir.add(iw, ow)
     small.remove_node(3)
-    m = big.info()["n_slots"]
-    alive = big.alive().astype(bool)
-    live = np.flatnonzero(alive)
-    ref = O.to_i32(O.fw(big.W()[:m, :m], alive[:m]))
-    np.testing.assert_array_equal(big.D()[np.ix_(live, live)], ref[np.ix_(live, live)])
-    assert alive[p]
+    assert np.array_equal(big.alive().astype(bool), mir.alive[:big.info()["n_slots"]])
+    assert_same(big, mir, "big graph beside a small one")
     big.close()
     small.close()

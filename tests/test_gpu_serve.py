@@ -1,10 +1,16 @@
-"""Serving loop: requests of several graphs interleaved in time; each graph
-must end exactly as if its requests had been applied alone, and every query
-must see exactly the updates that arrived before it."""
+"""Serving loop: requests of several graphs interleaved in time.
+
+Every graph must end with the APSP matrix of its own weights after all of its
+requests (checked against the oracle on the test's own weight mirror), every
+query must return the oracle's distance in the graph as it stood when the
+query arrived, and each graph must end exactly as if its requests had been
+applied alone.
+"""
 import numpy as np
 import pytest
 
 import synth
+from oracle import apsp as O
 
 pytestmark = pytest.mark.gpu
 
@@ -16,25 +22,34 @@ def lib():
     return apsp
 
 
-def _trace(sizes, caps, count, seed):
-    """Concrete requests (with slots predicted by the lowest-free-slot rule)
-    and the per-graph initial weights."""
-    Ws = [synth.complete_digraph_i32(n, 1, 1000, seed + k) for k, n in enumerate(sizes)]
-    Wm, alive = [], []
-    for W, n, cap in zip(Ws, sizes, caps):
-        m = np.full((cap, cap), synth.INF_I32, np.int32)
-        m[:n, :n] = W
-        a = np.zeros(cap, bool)
-        a[:n] = True
-        Wm.append(m)
-        alive.append(a)
+class _Mirror:
+    """Oracle-side weights of one graph in slot space."""
+
+    def __init__(self, W, cap):
+        n = W.shape[0]
+        self.W = np.full((cap, cap), synth.INF_I32, np.int32)
+        self.W[:n, :n] = W
+        self.alive = np.zeros(cap, bool)
+        self.alive[:n] = True
+
+    def dist_row(self, u):
+        return O.to_i32(O.dijkstra_rows(self.W, [u], self.alive))[0]
+
+
+def _trace(sizes, caps, count, seed, w_hi=1000, queries_checked=True):
+    """Concrete requests (slots predicted by the lowest-free-slot rule), the
+    per-graph initial weights, the mirrors after the whole trace, and the
+    oracle's answer to every query at its place in the trace."""
+    Ws = [synth.complete_digraph_i32(n, 1, w_hi, seed + k) for k, n in enumerate(sizes)]
+    mir = [_Mirror(W, cap) for W, cap in zip(Ws, caps)]
     pick = synth.uniform_int(seed, 1, count, 0, len(sizes) - 1)
     kind = synth.uniform_f64(seed, 2, count)
     r = synth.u64(seed, 3, 3 * count)
-    reqs = []
+    reqs, expect = [], {}
     for q in range(count):
         gi = int(pick[q])
-        live = np.flatnonzero(alive[gi])
+        m = mir[gi]
+        live = np.flatnonzero(m.alive)
         cap = caps[gi]
         k = kind[q]
         a_, b_ = int(r[3 * q] % np.uint64(len(live))), int(r[3 * q + 1] % np.uint64(len(live) - 1))
@@ -43,23 +58,29 @@ def _trace(sizes, caps, count, seed):
         u, v = int(live[a_]), int(live[b_])
         if k < 0.1:
             reqs.append((gi, "query", u, v))
+            if queries_checked:
+                expect[q] = int(m.dist_row(u)[v])
         elif k < 0.2 and len(live) < cap:
             iw = np.full(cap, synth.INF_I32, np.int32)
             ow = np.full(cap, synth.INF_I32, np.int32)
-            iw[live] = synth.uniform_int(seed, 1000 + 2 * q, len(live), 1, 1000)
-            ow[live] = synth.uniform_int(seed, 1001 + 2 * q, len(live), 1, 1000)
-            p = int(np.flatnonzero(~alive[gi])[0])
-            alive[gi][p] = True
+            iw[live] = synth.uniform_int(seed, 1000 + 2 * q, len(live), 1, w_hi)
+            ow[live] = synth.uniform_int(seed, 1001 + 2 * q, len(live), 1, w_hi)
+            p = O.lowest_free_slot(m.alive)
+            m.W[:, p] = iw
+            m.W[p, :] = ow
+            m.W[p, p] = 0
+            m.alive[p] = True
             reqs.append((gi, "add", iw, ow))
         elif k < 0.3 and len(live) > 8:
-            alive[gi][u] = False
+            m.alive[u] = False
+            m.W[u, :] = m.W[:, u] = synth.INF_I32
             reqs.append((gi, "remove", u))
         else:
-            w0 = int(Wm[gi][u, v])
-            w = w0 // 2 if k < 0.65 else min(w0 * 4, 1 << 20)
-            Wm[gi][u, v] = w
+            w0 = int(m.W[u, v])
+            w = w0 // 2 if k < 0.65 else min(w0 * 4, 1 << 24)
+            m.W[u, v] = w
             reqs.append((gi, "edge", u, v, float(w)))
-    return Ws, reqs
+    return Ws, reqs, mir, expect
 
 
 def _replay_alone(lib, W, cap, reqs):
@@ -80,12 +101,28 @@ def _replay_alone(lib, W, cap, reqs):
     return D, dists
 
 
+def _check_final(g, m, full=True, rows=64, seed=0):
+    """The served graph against the oracle on its own mirror: every entry
+    (full) or sampled source rows by Dijkstra."""
+    D = g.D()
+    s = D.shape[0]
+    assert np.array_equal(g.alive()[:s].astype(bool), m.alive[:s])
+    live = np.flatnonzero(m.alive[:s])
+    if full:
+        ref = O.to_i32(O.fw(m.W[:s, :s], m.alive[:s]))
+        np.testing.assert_array_equal(D[np.ix_(live, live)], ref[np.ix_(live, live)])
+    else:
+        pick = live[synth.uniform_int(seed, 9, rows, 0, len(live) - 1)]
+        ref = O.to_i32(O.dijkstra_rows(m.W[:s, :s], pick, m.alive[:s]))
+        np.testing.assert_array_equal(D[np.ix_(pick, live)], ref[:, live])
+
+
 @pytest.mark.parametrize("budget", [0.0, 1.0])
-def test_serve_matches_each_graph_alone(lib, budget):
+def test_serve_matches_oracle_and_each_graph_alone(lib, budget):
     from paper_2412_15122_gb300 import Graph
     sizes = [60, 97, 120, 300, 257, 64]
     caps = [80, 128, 128, 320, 288, 96]   # capacity <= 128: batched kernel; larger: one call per update
-    Ws, reqs = _trace(sizes, caps, 240, 9)
+    Ws, reqs, mir, expect = _trace(sizes, caps, 240, 9)
     gaps = -np.log1p(-synth.uniform_f64(9, 5, len(reqs))) * 2e-4
     arrivals = np.cumsum(gaps)
     graphs = [Graph(W, cap) for W, cap in zip(Ws, caps)]
@@ -97,7 +134,11 @@ def test_serve_matches_each_graph_alone(lib, budget):
         # one graph per wave: a wave never mixes graphs
         for w in np.unique(res["wave"]):
             assert len({reqs[q][0] for q in np.flatnonzero(res["wave"] == w)}) == 1
+    assert expect, "the trace holds queries"
+    for q, d in expect.items():
+        assert res["dist"][q] == d, (q, reqs[q])
     for gi, (W, cap) in enumerate(zip(Ws, caps)):
+        _check_final(graphs[gi], mir[gi])
         mine = [(q, it) for q, it in enumerate(reqs) if it[0] == gi]
         D_alone, dists = _replay_alone(lib, W, cap, mine)
         np.testing.assert_array_equal(graphs[gi].D(), D_alone)
@@ -107,4 +148,26 @@ def test_serve_matches_each_graph_alone(lib, budget):
             if it[1] == "add":
                 assert res["new_id"][q] >= 0
     for g in graphs:
+        g.close()
+
+
+def test_serve_at_full_graph_sizes(lib):
+    # Resident graphs of the serving workload's sizes (n = 1024, 2048, 4096,
+    # 8192, int32 U[1, 1e6]) with Poisson arrivals: the two smaller graphs go
+    # through the batched kernel, the larger ones one call per update.  Queries
+    # are checked against the oracle's Dijkstra at their place in the trace;
+    # final matrices in full at n <= 2048, by 64 sampled rows above.
+    from paper_2412_15122_gb300 import Graph
+    sizes = [1024, 2048, 4096, 8192]
+    caps = [n + 32 for n in sizes]
+    Ws, reqs, mir, expect = _trace(sizes, caps, 48, 77, w_hi=1_000_000)
+    gaps = -np.log1p(-synth.uniform_f64(77, 5, len(reqs))) * 5e-4
+    arrivals = np.cumsum(gaps)
+    graphs = [Graph(W, cap) for W, cap in zip(Ws, caps)]
+    res = lib.apsp_serve([g.h for g in graphs], reqs, arrivals, small_max_slots=2048 + 32)
+    assert (res["status"] == 0).all()
+    for q, d in expect.items():
+        assert res["dist"][q] == d, (q, reqs[q])
+    for gi, g in enumerate(graphs):
+        _check_final(g, mir[gi], full=sizes[gi] <= 2048, seed=gi)
         g.close()

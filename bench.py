@@ -40,9 +40,12 @@ METRIC = "warm-start APSP updates/s at n=8192 vs GPU cold FW; sweep HBM GB/s vs 
 UNIT = "updates/s"
 WORKLOAD = "n=8192 directed complete graph, int32 weights U[1,1e6], mixed updates 25% add / 25% remove / 25% decrease (w/2) / 25% increase (4w), uniform targets, one call per update"
 SWEEP_KERNELS = ("insert_reduce", "insert_relax", "detect_remove")
-# DRAM bytes (read + write) per launch of each sweep, from the ncu captures
-# summarised in profiles/traffic_sweeps_n8192.md (mean of two launches)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# sweep at this workload, from an ncu capture of the same kernels taken in a
+# separate run (mean of two launches); a sweep whose code changes must be
+# captured again before its figure is used
 SWEEP_TRAFFIC = {"insert_reduce": 272.19e6, "insert_relax": 274.83e6, "detect_remove": 274.49e6}
+TRAFFIC_SOURCE = "ncu capture of the same kernel on this workload, separate run (not this run)"
 
 
 def rank_seed(rank: int) -> int:
@@ -73,16 +76,19 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def plan_ops(total: int, seed: int):
+def plan_ops(total: int, seed: int, tight: bool = False, W=None):
     """Concrete op list (slot ids and weights) from the seeded update stream,
     simulating slot assignment (lowest free slot) and the weight mirror on the
-    host, so no per-update host work happens inside the timed region."""
-    W = synth.complete_digraph_i32(N, W_LO, W_HI, seed)
+    host, so no per-update host work happens inside the timed region.  With
+    `tight`, every edge update takes the lightest out-edge of its source (a
+    shortest path, so increases are never trivial and decreases sweep)."""
+    if W is None:
+        W = synth.complete_digraph_i32(N, W_LO, W_HI, seed)
     alive = np.zeros(CAP, dtype=bool)
     alive[:N] = True
     Wm = np.full((CAP, CAP), synth.INF_I32, dtype=np.int32)
     Wm[:N, :N] = W
-    ups = synth.mixed_updates(N, total, seed, capacity=CAP, w_lo=W_LO, w_hi=W_HI, cap=1 << 26)
+    ups = synth.mixed_updates(N, total, seed, capacity=CAP, w_lo=W_LO, w_hi=W_HI, cap=1 << 26, tight=tight)
     ops = []
     for up in ups:
         live = np.flatnonzero(alive)
@@ -106,11 +112,75 @@ def plan_ops(total: int, seed: int):
             ops.append(("remove", k))
         else:
             u, v = int(live[up.a]), int(live[up.b])
+            if up.tight:
+                row = np.where(alive, Wm[u].astype(np.int64), synth.INF_I32)
+                row[u] = synth.INF_I32
+                v = int(np.argmin(row))
             w0 = int(Wm[u, v])
             w = w0 // 2 if up.kind == synth.DECREASE else min(w0 * 4, up.cap)
             Wm[u, v] = w
             ops.append((up.kind, u, v, w))
     return W, ops
+
+
+def step_queries(ops, U: int, steps, qpairs):
+    """Per step, the pair-query batch issued after the step's updates: the
+    pairs `qpairs` taken modulo the live slots as the host's own simulation of
+    the lowest-free-slot rule sees them (no device read needed)."""
+    alive = np.zeros(CAP, dtype=bool)
+    alive[:N] = True
+    out = {}
+    last = max(steps) + 1
+    for s in range(last):
+        for op in ops[s * U:(s + 1) * U]:
+            if op[0] == "add":
+                alive[int(np.flatnonzero(~alive)[0])] = True
+            elif op[0] == "remove":
+                alive[op[1]] = False
+        if s in steps:
+            live = np.flatnonzero(alive)
+            out[s] = live[qpairs % len(live)].astype(np.int32)
+    return out
+
+
+def fw_cpu_timings(sizes_all=(256, 1024, 2048, 4096), sizes_one=(256, 1024, 2048)):
+    """The oracle's Floyd-Warshall (C, OpenMP over rows) on the host cores, all
+    threads and one thread, in a child process per setting (the thread count
+    is fixed when OpenMP starts); best of 3 below n = 2048, one run above."""
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import synth
+from oracle import apsp as O
+out = {}
+for n in %r:
+    W = synth.complete_digraph_i32(n, 1, 10**6, 2)
+    best = None
+    for _ in range(3 if n < 2048 else 1):
+        t = time.perf_counter(); O.fw(W); dt = time.perf_counter() - t
+        best = dt if best is None else min(best, dt)
+    out[n] = best
+print(json.dumps({"threads": O.num_threads(), "s": out}))
+"""
+    res = {}
+    for label, sizes, env_threads in (("all_cores", sizes_all, None), ("one_thread", sizes_one, "1")):
+        env = dict(os.environ)
+        if env_threads:
+            env["OMP_NUM_THREADS"] = env_threads
+        r = subprocess.run([sys.executable, "-c", code % (ROOT, list(sizes))], capture_output=True, text=True,
+                           env=env, timeout=600)
+        if r.returncode != 0:
+            res[label] = {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+            continue
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        res[label] = {"threads": d["threads"], "seconds": {str(k): round(v, 4) for k, v in d["s"].items()}}
+    one = res.get("one_thread", {}).get("seconds", {})
+    if "2048" in one:
+        res["one_thread"]["extrapolated_n3"] = {"4096": round(one["2048"] * 8, 2), "8192": round(one["2048"] * 64, 1)}
+    allc = res.get("all_cores", {}).get("seconds", {})
+    if "4096" in allc:
+        res["all_cores"]["extrapolated_n3"] = {"8192": round(allc["4096"] * 8, 2)}
+    return res
 
 
 class Clocks:
@@ -876,6 +946,78 @@ def run_serve_study(args):
         "alone_vs_mix_identical_n1024": same, "setup_seconds": gen_s}))
 
 
+def detailed_pass(Graph, A, W, ops, stream, profile=False):
+    """Replays `ops` on a fresh graph, one wait per update: per update type
+    the count, the library's statistics and the device time of the update
+    (CUDA events on the library's stream around its call), for all updates
+    and for the non-trivial ones (path not "trivial" / "none").  With
+    `profile`, also the per-kernel totals of the pass."""
+    import torch
+    g = Graph(W, CAP, stream=stream)
+    if profile:
+        A.apsp_profile_enable(g.h, True)
+        A.apsp_profile_reset(g.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = {}
+    for op in ops:
+        e0.record(stream)
+        issue_op(A, g, op, None)
+        e1.record(stream)
+        st = g.stats()
+        ms = e0.elapsed_time(e1)
+        k = stats.setdefault(st["op"], {"count": 0, "paths": {}, "pairs": 0, "rows": 0, "passes": 0,
+                                         "sweep_rows": 0, "max_pairs": 0, "pairs_rechecked": 0,
+                                         "warm_pass1_us": 0.0, "warm_total_us": 0.0, "device_ms": 0.0,
+                                         "nontrivial": 0, "nontrivial_ms": 0.0, "warm": 0, "warm_pairs": 0})
+        k["count"] += 1
+        k["paths"][st["path"]] = k["paths"].get(st["path"], 0) + 1
+        k["pairs"] += st["affected_pairs"]
+        k["rows"] += st["affected_rows"]
+        k["passes"] += st["passes"]
+        k["sweep_rows"] += st["sweep_rows"]
+        k["pairs_rechecked"] += st["pairs_rechecked"]
+        k["warm_pass1_us"] += st["warm_pass1_us"]
+        k["warm_total_us"] += st["warm_total_us"]
+        k["max_pairs"] = max(k["max_pairs"], st["affected_pairs"])
+        k["device_ms"] += ms
+        if st["path"] not in ("trivial", "none"):
+            k["nontrivial"] += 1
+            k["nontrivial_ms"] += ms
+        if st["path"] == "warm":
+            k["warm"] += 1
+            k["warm_pairs"] += st["affected_pairs"]
+    prof = A.apsp_profile_read(g.h) if profile else {}
+    span = g.info()["n_slots"]
+    g.close()
+    for k in stats.values():
+        c = max(1, k["count"])
+        for f in ("pairs", "rows", "passes", "sweep_rows", "pairs_rechecked"):
+            k["avg_" + f] = round(k.pop(f) / c, 2)
+        w = max(1, k["warm"])
+        k["avg_warm_pass1_us"] = round(k.pop("warm_pass1_us") / w, 2)
+        k["avg_warm_total_us"] = round(k.pop("warm_total_us") / w, 2)
+        k["avg_warm_pairs"] = round(k.pop("warm_pairs") / w, 1)
+        k["device_ms"] = round(k["device_ms"], 3)
+        k["updates_per_s"] = round(k["count"] / (k["device_ms"] / 1000.0), 1) if k["device_ms"] > 0 else None
+        k["nontrivial_ms"] = round(k["nontrivial_ms"], 3)
+        k["nontrivial_updates_per_s"] = (round(k["nontrivial"] / (k["nontrivial_ms"] / 1000.0), 1)
+                                         if k["nontrivial_ms"] > 0 else None)
+    return stats, prof, span
+
+
+def issue_op(A, g, op, device_vecs):
+    """One library call for one planned update."""
+    if op[0] == "add":
+        if device_vecs is not None:
+            A.apsp_add_node_device(g.h, device_vecs[id(op)][0], device_vecs[id(op)][1])
+        else:
+            A.apsp_add_node(g.h, op[1], op[2])
+    elif op[0] == "remove":
+        A.apsp_remove_node(g.h, op[1])
+    else:
+        A.apsp_update_edge(g.h, op[1], op[2], op[3], A.APSP_I32)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -886,6 +1028,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--no-stats", action="store_true")
+    ap.add_argument("--tight-updates", type=int, default=1000, help="updates of the tight-edge mix (0: skip)")
+    ap.add_argument("--no-fw-cpu", action="store_true", help="skip the host Floyd-Warshall timings")
     ap.add_argument("--case", choices=["removals", "inserts", "paths"],
                     help="run a small fixed case of the workload (for profiler captures) and exit")
     ap.add_argument("--study-graphs", type=int, default=512)
@@ -938,15 +1082,7 @@ def main():
     hbm, peak_kind = peaks()
 
     def issue(g, op, device_vecs):
-        if op[0] == "add":
-            if device_vecs is not None:
-                A.apsp_add_node_device(g.h, device_vecs[id(op)][0], device_vecs[id(op)][1])
-            else:
-                A.apsp_add_node(g.h, op[1], op[2])
-        elif op[0] == "remove":
-            A.apsp_remove_node(g.h, op[1])
-        else:
-            A.apsp_update_edge(g.h, op[1], op[2], op[3], A.APSP_I32)
+        issue_op(A, g, op, device_vecs)
 
     def barrier():
         torch.cuda.synchronize()
@@ -1008,28 +1144,45 @@ def main():
     # ---- statistics of the workload (untimed, one wait per update) -----------
     stats = {}
     if rank == 0 and not args.no_stats:
-        g = Graph(W, CAP, stream=stream)
-        for op in ops_value[: (args.warmup + args.steps) * U]:
-            issue(g, op, dvec)
-            st = g.stats()
-            k = stats.setdefault(st["op"], {"count": 0, "paths": {}, "pairs": 0, "rows": 0, "passes": 0,
-                                             "sweep_rows": 0, "max_pairs": 0, "pairs_rechecked": 0,
-                                             "warm_pass1_us": 0.0, "warm_total_us": 0.0})
-            k["count"] += 1
-            k["paths"][st["path"]] = k["paths"].get(st["path"], 0) + 1
-            k["pairs"] += st["affected_pairs"]
-            k["rows"] += st["affected_rows"]
-            k["passes"] += st["passes"]
-            k["sweep_rows"] += st["sweep_rows"]
-            k["pairs_rechecked"] += st["pairs_rechecked"]
-            k["warm_pass1_us"] += st["warm_pass1_us"]
-            k["warm_total_us"] += st["warm_total_us"]
-            k["max_pairs"] = max(k["max_pairs"], st["affected_pairs"])
-        g.close()
-        for k in stats.values():
-            c = max(1, k["count"])
-            for f in ("pairs", "rows", "passes", "sweep_rows", "pairs_rechecked", "warm_pass1_us", "warm_total_us"):
-                k["avg_" + f] = round(k.pop(f) / c, 2)
+        stats, _, _ = detailed_pass(Graph, A, W, ops_value[: (args.warmup + args.steps) * U], stream)
+
+    # ---- the tight-edge mix: every edge update on a shortest path -------------
+    tight = None
+    if rank == 0 and not args.no_stats and args.tight_updates > 0:
+        _, tops = plan_ops(args.tight_updates, seed + 7, tight=True, W=W)
+        gt = Graph(W, CAP, stream=stream)
+        torch.cuda.synchronize()
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        for op in tops:
+            issue(gt, op, None)
+        t1e.record(stream)
+        gt.sync()
+        tight_ms = t0e.elapsed_time(t1e)
+        gt.close()
+        tstats, tprof, tspan = detailed_pass(Graph, A, W, tops, stream, profile=True)
+        tight = {"workload": f"the same graph and mix, {args.tight_updates} updates, every edge update on the "
+                             "lightest out-edge of a uniform node (a shortest path: increases are never trivial)",
+                 "value": args.tight_updates / (tight_ms / 1000.0), "unit": UNIT, "ms": tight_ms,
+                 "per_type": tstats,
+                 "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in sorted(tprof.items())}}
+        dec = tstats.get("decrease")
+        if dec and "decrease_sweep" in tprof and tprof["decrease_sweep"][1] > 0:
+            nl, tot = tprof["decrease_sweep"]
+            b = 4.0 * tspan * dec["avg_sweep_rows"] * dec["count"]      # rows swept x one row of D each
+            tight["decrease_sweep_roofline"] = {"bound": "hbm", "achieved": b / (tot / 1000.0) / 1e9, "peak": hbm,
+                                                "unit": "GB/s", "frac": b / (tot / 1000.0) / 1e9 / hbm,
+                                                "bytes_per_launch": b / max(1, nl), "launches": nl,
+                                                "avg_launch_us": 1000.0 * tot / max(1, nl)}
+        inc = tstats.get("increase")
+        if inc and inc.get("avg_warm_pass1_us", 0) > 0:
+            l2 = A.apsp_probe_l2_read_gbs()
+            b = 4.0 * tspan * inc["avg_warm_pairs"]
+            tight["increase_repair_roofline"] = {
+                "bound": "l2", "kernel": "k_repair_warm, first pass (tight increases)",
+                "achieved": b / (inc["avg_warm_pass1_us"] * 1e-6) / 1e9, "peak": l2, "unit": "GB/s",
+                "frac": b / (inc["avg_warm_pass1_us"] * 1e-6) / 1e9 / l2, "bytes_per_increase": b,
+                "pass1_us_per_increase": inc["avg_warm_pass1_us"], "warm_total_us": inc["avg_warm_total_us"]}
     del dvec
 
     # ---- e2e: host buffers through the C ABI ---------------------------------
@@ -1040,7 +1193,8 @@ def main():
         for op in ops_e2e[s * U:(s + 1) * U]:
             issue(g, op, None)
     g.sync()
-    alive = g.alive()
+    # the query pairs of every step, from the host's own slot simulation
+    quv = step_queries(ops_e2e, U, set(range(args.warmup, args.warmup + args.steps)), qpairs)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
@@ -1051,8 +1205,8 @@ def main():
             issue(g, op, None)
             if op[0] == "add":
                 h2d += op[1].nbytes + op[2].nbytes
-        live = np.flatnonzero(g.alive())
-        uv = live[qpairs % len(live)].astype(np.int32)
+        uv = quv[s]
+        h2d += uv.nbytes
         res = g.query_batch(uv)
         d2h += res.nbytes
     e1.record(stream)
@@ -1074,7 +1228,7 @@ def main():
         achieved = bytes_per_launch / (tot_ms / nl / 1000.0) / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
-                    "traffic": SWEEP_TRAFFIC.get(name), "traffic_source": "profiles/traffic_sweeps_n8192.md",
+                    "traffic": SWEEP_TRAFFIC.get(name), "traffic_source": TRAFFIC_SOURCE,
                     "bytes_per_launch": bytes_per_launch, "launches": nl,
                     "avg_launch_us": 1000 * tot_ms / nl}
 
@@ -1102,6 +1256,9 @@ def main():
                            "peak_kind": "measured: L2 read probe (apsp_probe_l2_read_gbs)",
                            "bytes_per_removal": p1_bytes, "pass1_us_per_removal": rm["avg_warm_pass1_us"]}
 
+    fw_cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_fw_cpu:
+        fw_cpu = fw_cpu_timings()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, dt = cpu_oracle_rate(W, args.cpu_rows)
@@ -1131,6 +1288,8 @@ def main():
                               "reported against the measured L2 read bandwidth in repair_roofline"),
             "profiled_pass_ms": prof_ms,
             "update_stats": stats,
+            "tight_mix": tight,
+            "fw_cpu": fw_cpu,
             "warm_updates_per_cold_fw": value * cold_ms / 1000.0,
             "top_kernel": {"name": top[0], "launches": top[1][0], "total_ms": top[1][1]},
             "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in sorted(prof.items())},

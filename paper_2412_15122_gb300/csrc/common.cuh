@@ -149,6 +149,7 @@ struct Ctl {
     unsigned long long t_start, t_pass1, t_end;  // device timestamps (ns) of the warm repair
     unsigned long long grown_pairs;  // listed pairs whose distance grew (Algorithm 12's list), when measured
     int32_t grown_rows;              // rows holding one of them
+    int32_t p1_done;                 // CTAs of the first re-relaxation pass that finished
     uint32_t err;             // sticky until the host reads it
 };
 

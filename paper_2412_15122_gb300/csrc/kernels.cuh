@@ -1093,7 +1093,7 @@ __global__ void __launch_bounds__(256) k_grown_count(Dev<T> d, int kind, T w_old
 }
 
 template <typename T>
-__device__ void repair_warm(Dev<T> &d, int n_items) {
+__device__ void repair_warm(Dev<T> &d) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     Ctl *ctl = d.ctl;
@@ -1103,84 +1103,12 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
     const T *cols = d.DT ? d.DT : d.D;   // row j of `cols` is column j of D
     const long long n_units = *(volatile const int32_t *)&ctl->unit_alloc;
 
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer_ns();
-
     const int wq = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % QUEUES) * 32;
 
-    // Pass 1: one warp per unit = (work item, window of PASS1_COLS columns
-    // of x), units ordered window-major so all warps sweep the same window.
-    // The row's slice of the window is staged in the warp's shared buffer;
-    // per pair the whole column slice is loaded at once (8 vectors a lane),
-    // reduced over the warp, and kept by lane t for pair t; one
-    // fire-and-forget atomic min per pair and unit stores it.
-    {
-        constexpr int CW = PASS1_COLS / 128;   // 16-byte vectors per lane per window
-        __shared__ V4 rowbuf[8][PASS1_COLS / 4];
-        V4 *rb = rowbuf[threadIdx.x >> 5];
-        const int nwin = (span + PASS1_COLS - 1) / PASS1_COLS;
-        const int n1 = n_items * nwin;   // items < 2^19 and windows <= 18 at the largest capacity
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&ctl->q1[wq], 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        while (true) {
-            const int u = (wq >> 5) + QUEUES * t;
-            if (u >= n1 || u < 0) break;
-            const int g = u / n_items, it = u - g * n_items;
-            if (lane == 0) t = atomicAdd(&ctl->q1[wq], 1);   // next unit, in flight meanwhile
-            const int4 item = __ldcg(d.items + it);
-            const int cnt = item.z & 0xff;
-            const int jl = lane < cnt ? __ldcg(d.pairs + item.y + lane) : 0;
-            const int x0 = g * PASS1_COLS;
-            const int nv = (min(span, x0 + PASS1_COLS) - x0) / 4;
-            const V4 *r4 = reinterpret_cast<const V4 *>(d.D + (int64_t)item.x * ld + x0);
-            __syncwarp();   // the previous unit's reads of the buffer are done
-#pragma unroll
-            for (int k = 0; k < CW; ++k)
-                if (lane + 32 * k < nv) cp_async16(rb + lane + 32 * k, r4 + lane + 32 * k);
-            T pacc = M::inf();
-            // two pairs per step: both column slices (16 vectors a lane) are
-            // in flight before either is used
-            for (int q = 0; q < cnt; q += 2) {
-                const bool two = q + 1 < cnt;
-                const int ja = __shfl_sync(0xffffffffu, jl, q);
-                const int jb = __shfl_sync(0xffffffffu, jl, two ? q + 1 : q);
-                const V4 *ca = reinterpret_cast<const V4 *>(cols + (int64_t)ja * ld + x0);
-                const V4 *cb = reinterpret_cast<const V4 *>(cols + (int64_t)jb * ld + x0);
-                V4 a[CW], b[CW];
-#pragma unroll
-                for (int k = 0; k < CW; ++k)
-                    if (lane + 32 * k < nv) {
-                        a[k] = __ldcg(ca + lane + 32 * k);
-                        if (two) b[k] = __ldcg(cb + lane + 32 * k);
-                    }
-                cp_async_wait_all();   // the row slice (in flight with the first columns)
-                __syncwarp();
-                T acc = M::inf(), acc2 = M::inf();
-#pragma unroll
-                for (int k = 0; k < CW; ++k) {
-                    if (lane + 32 * k < nv) {
-                        const V4 r = rb[lane + 32 * k];
-                        acc = M::add_min(r.x, a[k].x, acc);
-                        acc = M::add_min(r.y, a[k].y, acc);
-                        acc = M::add_min(r.z, a[k].z, acc);
-                        acc = M::add_min(r.w, a[k].w, acc);
-                        if (two) {
-                            acc2 = M::add_min(r.x, b[k].x, acc2);
-                            acc2 = M::add_min(r.y, b[k].y, acc2);
-                            acc2 = M::add_min(r.z, b[k].z, acc2);
-                            acc2 = M::add_min(r.w, b[k].w, acc2);
-                        }
-                    }
-                }
-                acc = warp_min(acc);
-                acc2 = warp_min(acc2);
-                if (lane == q) pacc = acc;
-                if (two && lane == q + 1) pacc = acc2;
-            }
-            if (lane < cnt) atomicMin(d.pmin + item.y + lane, M::key(pacc));
-            t = __shfl_sync(0xffffffffu, t, 0);
-        }
-    }
+    // Pass 1 ran in k_repair_p1 (repair_p1.cuh): pmin holds every listed
+    // pair's minimum over all x.  The control block was cleared before the
+    // update, so the state the passes below start from (no stop, no pair
+    // lowered, empty work queues) needs no barrier.
     int pass = 1;
     auto leader = [&]() {
         volatile Ctl *cv = ctl;
@@ -1189,12 +1117,8 @@ __device__ void repair_warm(Dev<T> &d, int n_items) {
         cv->changed[par ^ 1] = 0;
         for (int q = 0; q < QUEUES; ++q) cv->qn[par ^ 1][32 * q] = 0;
         cv->passes = pass;
-        const unsigned long long now = globaltimer_ns();
-        if (pass == 1) cv->t_pass1 = now;
-        cv->t_end = now;
+        cv->t_end = globaltimer_ns();
     };
-    if (!grid_barrier(ctl, leader)) return;
-
     // Passes >= 2: one warp per unit = (work item, segment of YSEG of the
     // row's listed targets y).  Lane u holds intermediates y = segment[u +
     // 32b] with D[i][y]; pairs are taken four at a time, every lane gathering
@@ -1393,31 +1317,24 @@ __device__ inline void repair_record(Ctl *ctl, int reason, float cost, float pw,
     }
 }
 
-// Warm repair (cooperative launch): restricted re-relaxation.
+// Repair (cooperative launch, after k_repair_p1): the warm / cold decision,
+// then either the re-relaxation passes >= 2 or the persistent blocked
+// Floyd-Warshall.  One kernel holds both, so an update that stays warm
+// launches no cold kernel; the first pass, which wants the shared memory for
+// its copy ring, is the separate k_repair_p1.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_repair_warm(Dev<T> d, RepairCfg cfg) {
-    float cost, pw, pc;
-    int n_items;
-    const int reason = repair_decide(d.ctl, cfg, &cost, &pw, &pc, &n_items);
-    if (reason != 0) {
-        if (reason < 0) repair_record(d.ctl, reason, cost, pw, pc);
-        return;
-    }
-    repair_record(d.ctl, reason, cost, pw, pc);
-    repair_warm<T>(d, n_items);
-}
-
-// Cold repair (cooperative launch): persistent blocked Floyd-Warshall,
-// running only when the decision says cold.
-template <typename T>
-__global__ void __launch_bounds__(256, 2) k_repair_cold(Dev<T> d, RepairCfg cfg) {
+__global__ void __launch_bounds__(256, 2) k_repair_main(Dev<T> d, RepairCfg cfg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float cost, pw, pc;
     int n_items;
     const int reason = repair_decide(d.ctl, cfg, &cost, &pw, &pc, &n_items);
-    if (reason <= 0) return;
     repair_record(d.ctl, reason, cost, pw, pc);
-    repair_cold<T>(d, smem_raw);
+    if (reason < 0) return;
+    if (reason > 0) {
+        repair_cold<T>(d, smem_raw);
+        return;
+    }
+    repair_warm<T>(d);
 }
 
 }  // namespace apsp

@@ -139,23 +139,22 @@ template <typename F> static cudaError_t coop_launch(cudaStream_t stream, F &&la
     return cudaEventRecord(cc.last[dev], stream);
 }
 
-// Both repair kernels are launched; the one whose path the device-side
-// decision did not choose returns at once.
+// The repair: the first re-relaxation pass (k_repair_p1, a plain launch that
+// returns at once unless the device-side decision is warm), then the cooperative
+// k_repair_main, which makes the same decision and runs either the later
+// passes or the cold Floyd-Warshall.
 template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d, const RepairCfg &cfg) {
+    cudaError_t e = launch(c, "repair_p1", [&] {
+        k_repair_p1<T><<<c.p1_grid, 256, 0, c.stream>>>(d, cfg);
+    });
+    if (e != cudaSuccess) return e;
     Dev<T> dd = d;
     RepairCfg cc = cfg;
     void *args[] = {(void *)&dd, (void *)&cc};
     cudaError_t le = cudaSuccess;
-    cudaError_t e = launch(c, "repair_warm", [&] {
+    e = launch(c, "repair_main", [&] {
         le = coop_launch(c.stream, [&] {
-            return cudaLaunchCooperativeKernel((void *)k_repair_warm<T>, dim3(c.warm_grid), dim3(256), args, 0, c.stream);
-        });
-    });
-    if (le != cudaSuccess) return le;
-    if (e != cudaSuccess) return e;
-    e = launch(c, "repair_cold", [&] {
-        le = coop_launch(c.stream, [&] {
-            return cudaLaunchCooperativeKernel((void *)k_repair_cold<T>, dim3(c.repair_grid), dim3(256), args,
+            return cudaLaunchCooperativeKernel((void *)k_repair_main<T>, dim3(c.repair_grid), dim3(256), args,
                                                c.repair_smem, c.stream);
         });
     });
@@ -211,15 +210,15 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     size_t row = (size_t)ld * sizeof(T);
     size_t fw = sizeof(FwSmem<T>) > sizeof(FwDiagSmem<T>) ? sizeof(FwSmem<T>) : sizeof(FwDiagSmem<T>);
     c.repair_smem = std::max<size_t>(fw, 32 * 33 * sizeof(T));
-    if ((e = allow_max_smem(k_repair_cold<T>)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_repair_main<T>)) != cudaSuccess) return e;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_repair_cold<T>, 256, c.repair_smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_repair_main<T>, 256, c.repair_smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     c.repair_grid = per_sm * c.num_sms;
-    int warm_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&warm_sm, k_repair_warm<T>, 256, 0)) != cudaSuccess) return e;
-    if (warm_sm < 1) return cudaErrorInvalidConfiguration;
-    c.warm_grid = warm_sm * c.num_sms;
+    int p1_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1_sm, k_repair_p1<T>, 256, 0)) != cudaSuccess) return e;
+    if (p1_sm < 1) return cudaErrorInvalidConfiguration;
+    c.p1_grid = p1_sm * c.num_sms;
     if ((e = allow_max_smem(k_det_scan<T, false>)) != cudaSuccess) return e;
     int det_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&det_sm, k_det_scan<T, false>, 256, row)) != cudaSuccess) return e;

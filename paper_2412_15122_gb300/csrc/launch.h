@@ -8,6 +8,7 @@
 #include "batch.cuh"
 #include "kernels.cuh"
 #include "paths.cuh"
+#include "repair_p1.cuh"
 
 namespace apsp {
 
@@ -19,7 +20,7 @@ struct LaunchCtx {
     size_t repair_smem = 0;
     int detect_grid = 1;
     int relax_grid = 1;
-    int warm_grid = 1;
+    int p1_grid = 1;
     int detect2_grid = 1;
     int detunit_grid = 1;
     int detalloc_grid = 1;

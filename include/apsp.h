@@ -61,8 +61,18 @@ enum {
     APSP_DIRECTED = 0u,
     APSP_UNDIRECTED = 1u,     /* W must be symmetric; every update keeps D symmetric */
     APSP_D_GIVEN = 4u,        /* D_or_null holds the APSP matrix of W (trusted, not recomputed) */
-    APSP_DEVICE_INPUT = 8u    /* W / D_or_null are device pointers */
+    APSP_DEVICE_INPUT = 8u,   /* W / D_or_null are device pointers */
+    APSP_MINIMAX = 16u        /* minimax (bottleneck) distances, see below */
 };
+/* APSP_MINIMAX: the variant of the paper's Discussion in which a path's value
+ * is its largest edge weight and D[i][j] is the least such value over all
+ * paths i -> j (Floyd-Warshall, insertion, Corollary 3's list and the
+ * re-relaxation all run with max in place of +; max and min are exact, so
+ * int32 and fp32 results are both exact).  Removals and edge increases wait
+ * for the device once to read the list's size and choose warm or cold
+ * (APSP_DISPATCH_DELTA / ALWAYS_*; the cost model is not used).  Path
+ * queries, batches, serving and list modes other than Corollary 3 return
+ * APSP_E_UNSUPPORTED for such a graph. */
 
 typedef enum {
     APSP_OK = 0,

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libapsp_gb300.so")
 
 APSP_I32, APSP_F32 = 0, 1
-APSP_DIRECTED, APSP_UNDIRECTED, APSP_D_GIVEN, APSP_DEVICE_INPUT = 0, 1, 4, 8
+APSP_DIRECTED, APSP_UNDIRECTED, APSP_D_GIVEN, APSP_DEVICE_INPUT, APSP_MINIMAX = 0, 1, 4, 8, 16
 APSP_INF_I32 = 0x3FFFFFFF
 APSP_MAX_CAPACITY = 18432
 
@@ -592,14 +592,15 @@ class Graph:
     """A device-resident graph and its APSP matrix (one C handle)."""
 
     def __init__(self, W, capacity: Optional[int] = None, *, undirected: bool = False, D=None,
-                 stream=None, device_input: bool = False):
+                 stream=None, device_input: bool = False, minimax: bool = False):
         n = int(W.shape[0])
         if hasattr(W, "dtype") and str(W.dtype) in ("float32", "torch.float32"):
             self.dtype = APSP_F32
         else:
             self.dtype = APSP_I32
         flags = (APSP_UNDIRECTED if undirected else 0) | (APSP_D_GIVEN if D is not None else 0) | \
-            (APSP_DEVICE_INPUT if device_input else 0)
+            (APSP_DEVICE_INPUT if device_input else 0) | (APSP_MINIMAX if minimax else 0)
+        self.minimax = minimax
         self.capacity = int(capacity or n)
         self.undirected = undirected
         self.np_dtype = _np_dtype(self.dtype)

@@ -96,6 +96,39 @@ template <> struct MinPlus<float> {
     __device__ static float unkey(int32_t a) { return __int_as_float(a); }
 };
 
+// The (min, max) semiring of minimax (bottleneck) paths, the variant the
+// paper's Discussion names: a path's value is its largest edge weight and the
+// distance is the least such value.  "+" becomes max; max and min are exact in
+// both element types, so the tightness test needs no slack.  Same interface
+// as MinPlus for the kernels that are shared (the blocked Floyd-Warshall).
+template <typename T> struct MinMax;
+
+template <> struct MinMax<int32_t> {
+    using V4 = int4;
+    __host__ __device__ static constexpr int32_t inf() { return INF_I32; }
+    __device__ static bool finite(int32_t a) { return a < INF_I32; }
+    __device__ static int32_t add(int32_t a, int32_t b) { return max(a, b); }
+    __device__ static int32_t add_min(int32_t a, int32_t b, int32_t c) { return min(max(a, b), c); }
+    __device__ static int32_t mn(int32_t a, int32_t b) { return min(a, b); }
+    __device__ static bool lowers(int32_t a, int32_t c) { return a < c; }
+    __device__ static bool tight(int32_t via, int32_t d) { return via <= d; }
+    __device__ static int32_t key(int32_t a) { return a; }
+    __device__ static int32_t unkey(int32_t a) { return a; }
+};
+
+template <> struct MinMax<float> {
+    using V4 = float4;
+    __host__ __device__ static constexpr float inf() { return __builtin_huge_valf(); }
+    __device__ static bool finite(float a) { return a < inf(); }
+    __device__ static float add(float a, float b) { return fmaxf(a, b); }
+    __device__ static float add_min(float a, float b, float c) { return fminf(fmaxf(a, b), c); }
+    __device__ static float mn(float a, float b) { return fminf(a, b); }
+    __device__ static bool lowers(float a, float c) { return a < c; }
+    __device__ static bool tight(float via, float d) { return via <= d; }
+    __device__ static int32_t key(float a) { return __float_as_int(a); }
+    __device__ static float unkey(int32_t a) { return __int_as_float(a); }
+};
+
 template <typename V> __device__ __forceinline__ V ldcg4(const V *p) { return __ldcg(p); }
 
 // Error bits, OR-ed into Ctl::err by kernels and turned into an
@@ -115,6 +148,9 @@ constexpr int QUEUES = 16;
 
 // Per-graph control block in device memory.  Cleared (except `err`) before
 // each update; read back by the host only for statistics.
+// Passes of the minimax re-relaxation the control block can record.
+constexpr int MM_PASS_SLOTS = 64;
+
 struct Ctl {
     // produced by the prepass / detection of the current update
     int32_t r_count;          // rows in the prepass row list
@@ -150,6 +186,7 @@ struct Ctl {
     unsigned long long grown_pairs;  // listed pairs whose distance grew (Algorithm 12's list), when measured
     int32_t grown_rows;              // rows holding one of them
     int32_t p1_done;                 // CTAs of the first re-relaxation pass that finished
+    int32_t mm_changed[MM_PASS_SLOTS];  // minimax re-relaxation: pass p lowered a pair
     uint32_t err;             // sticky until the host reads it
 };
 

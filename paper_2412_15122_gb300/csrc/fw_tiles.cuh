@@ -34,11 +34,11 @@ template <typename T> struct FwDiagSmem {
     T colb[2][FW_B];
 };
 
-// C = min(C, A (x) B) on 128 x 128 tiles with leading dimension ld.
+// C = min(C, A (x) B) on 128 x 128 tiles with leading dimension ld, in the
+// semiring M (min-plus by default; min-max for bottleneck paths).
 // B may alias C (phase 2): C is only stored after the last read of B.
-template <typename T>
+template <typename T, typename M = MinPlus<T>>
 __device__ void minplus_tile(T *c, const T *a, const T *b, int64_t ld, FwSmem<T> &sm) {
-    using M = MinPlus<T>;
     using V4 = typename M::V4;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -102,9 +102,8 @@ __device__ void minplus_tile(T *c, const T *a, const T *b, int64_t ld, FwSmem<T>
 // keeps rows ty*8.. and columns tx*8.. in registers; at step k the owners of
 // row k and column k publish them to shared memory (double-buffered by the
 // parity of k, so one barrier per step suffices).
-template <typename T>
+template <typename T, typename M = MinPlus<T>>
 __device__ void fw_close_diag(T *t, int64_t ld, FwDiagSmem<T> &sm) {
-    using M = MinPlus<T>;
     using V4 = typename M::V4;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -157,30 +156,30 @@ __device__ void fw_close_diag(T *t, int64_t ld, FwDiagSmem<T> &sm) {
 
 // Tile t of phase 2 in round kb (nb blocks): t < nb-1 -> pivot-row tile,
 // else pivot-column tile.  The diagonal block is skipped.
-template <typename T>
+template <typename T, typename M = MinPlus<T>>
 __device__ void fw_phase2_tile(T *D, int64_t ld, int kb, int nb, int t, FwSmem<T> &sm) {
     const int64_t B = FW_B;
     T *diag = D + kb * B * ld + kb * B;
     if (t < nb - 1) {
         int J = t < kb ? t : t + 1;
         T *c = D + kb * B * ld + J * B;
-        minplus_tile<T>(c, diag, c, ld, sm);
+        minplus_tile<T, M>(c, diag, c, ld, sm);
     } else {
         int s = t - (nb - 1);
         int I = s < kb ? s : s + 1;
         T *c = D + I * B * ld + kb * B;
-        minplus_tile<T>(c, c, diag, ld, sm);
+        minplus_tile<T, M>(c, c, diag, ld, sm);
     }
 }
 
 // Tile t of phase 3 in round kb: (I, J) over the (nb-1)^2 off-pivot tiles.
-template <typename T>
+template <typename T, typename M = MinPlus<T>>
 __device__ void fw_phase3_tile(T *D, int64_t ld, int kb, int nb, int t, FwSmem<T> &sm) {
     const int64_t B = FW_B;
     int I = t / (nb - 1), J = t % (nb - 1);
     I += (I >= kb);
     J += (J >= kb);
-    minplus_tile<T>(D + I * B * ld + J * B, D + I * B * ld + kb * B, D + kb * B * ld + J * B, ld, sm);
+    minplus_tile<T, M>(D + I * B * ld + J * B, D + I * B * ld + kb * B, D + kb * B * ld + J * B, ld, sm);
 }
 
 }  // namespace apsp

@@ -98,6 +98,10 @@ struct apsp_graph {
     int32_t *grown_flag = nullptr;   // set when Algorithm 12's list is measured (apsp_set_exact_list)
     int list_mode = APSP_LIST_COROLLARY3;   // apsp_set_list_mode
     uint32_t *umask = nullptr;              // list mode APSP_LIST_ALGORITHM12: per-unit surviving masks
+    // minimax (bottleneck) distances: one bit per listed pair (i, j)
+    bool minimax = false;
+    uint32_t *mm_mask = nullptr;
+    int32_t mm_words = 0;
 
     apsp_stats last{};
     LaunchCtx lc;
@@ -392,6 +396,11 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->units = (int32_t *)dalloc(g, (size_t)g->unit_cap * 4);
     g->ctl = (Ctl *)dalloc(g, sizeof(Ctl));
     g->model = (float *)dalloc(g, apsp::MLP_NPARAM * sizeof(float));
+    if (g->minimax) {
+        g->mm_words = (int32_t)(ld / 32);
+        g->mm_mask = (uint32_t *)dalloc(g, (size_t)ld * g->mm_words * sizeof(uint32_t));
+        if (!g->mm_mask) return APSP_E_NOMEM;
+    }
     if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
         !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->ctl || !g->model ||
         !g->pmin || !g->pstamp || !g->rstamp || !g->units || !g->hrows || !g->hunits || !g->hralloc || !g->rowcnt ||
@@ -428,7 +437,8 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
         apsp::run_sanitize<T>(c, (T *)g->D, ld, n, 0, g->ctl);
         if ((e = apsp::run_transpose<T>(c, d)) != cudaSuccess) return cuda_status(e);
     } else if (n > 0) {
-        if ((e = apsp::run_fw<T>(c, d)) != cudaSuccess) return cuda_status(e);
+        e = g->minimax ? apsp::run_mm_fw<T>(c, d) : apsp::run_fw<T>(c, d);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     // host mirror of W
     g->alive_h.assign(g->cap, 0);
@@ -507,7 +517,8 @@ apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t
     g->hwm = std::max(g->hwm, p + 1);
     reset_ctl(g);
     Dev<T> d = dev_of<T>(g);
-    cudaError_t e = apsp::run_insert<T>(g->lc, d, din, dout, cap, p);
+    cudaError_t e = g->minimax ? apsp::run_mm_insert<T>(g->lc, d, din, dout, cap, p)
+                               : apsp::run_insert<T>(g->lc, d, din, dout, cap, p);
     if (e != cudaSuccess) return cuda_status(e);
     g->alive_h[p] = 1;
     g->n_live++;
@@ -522,10 +533,70 @@ apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t
     return APSP_OK;
 }
 
+// Minimax removal / increase after detection (minimax.cuh): reads the list's
+// counts (waits), chooses warm or cold by the dispatch mode (delta rule on
+// Cost; the cost model is not used here), then re-relaxes the listed pairs
+// pass by pass until one lowers nothing, or runs the (min, max)
+// Floyd-Warshall.  Fills the statistics of the update.
+template <typename T> apsp_status mm_repair(apsp_graph *g, int n_before) {
+    Ctl c;
+    apsp_status st = sync_ctl(g, &c);
+    if (st != APSP_OK) return st;
+    g->last.affected_pairs = (int64_t)c.n_pairs;
+    g->last.affected_rows = c.n_rows;
+    g->last.cost = n_before > 1 ? (float)c.n_rows / (float)(n_before - 1) : 0.f;
+    if (c.n_pairs == 0) {
+        g->last.path = APSP_PATH_TRIVIAL;
+        return APSP_OK;
+    }
+    const bool cold = g->mode == APSP_DISPATCH_ALWAYS_COLD ||
+                      (g->mode != APSP_DISPATCH_ALWAYS_WARM && g->last.cost > g->delta);
+    Dev<T> d = dev_of<T>(g);
+    cudaError_t e;
+    if (cold) {
+        if ((e = apsp::run_mm_fw<T>(g->lc, d)) != cudaSuccess) return cuda_status(e);
+        g->last.path = APSP_PATH_COLD;
+        g->last.cold_reason = g->mode == APSP_DISPATCH_ALWAYS_COLD ? 3 : 1;
+        return sync_ctl(g, nullptr);
+    }
+    g->last.path = APSP_PATH_WARM;
+    for (int p = 1; p < apsp::MM_PASS_SLOTS - 1; ++p) {
+        if ((e = apsp::run_mm_pass<T>(g->lc, d, g->mm_mask, g->mm_words, p)) != cudaSuccess) return cuda_status(e);
+        if (p >= 2 && (p % 2 == 0 || p == apsp::MM_PASS_SLOTS - 2)) {
+            if ((st = sync_ctl(g, &c)) != APSP_OK) return st;
+            int q = 1;
+            while (q <= p && c.mm_changed[q]) ++q;
+            if (q <= p) {   // pass q lowered nothing: the fixed point
+                g->last.passes = q;
+                return APSP_OK;
+            }
+        }
+    }
+    return APSP_E_TIMEOUT;   // no fixed point within the pass slots
+}
+
 template <typename T> apsp_status remove_impl(apsp_graph *g, int v) {
     settle_fetch<T>(g);
     if (v < 0 || v >= g->cap || !g->alive_h[v]) return APSP_E_NODE;
     reset_ctl(g);
+    if (g->minimax) {
+        const int n_before = g->n_live;
+        Dev<T> d = dev_of<T>(g);
+        cudaError_t e = apsp::run_mm_detect<T>(g->lc, d, g->mm_mask, g->mm_words, 0, v, v, (T)0, (T)0);
+        if (e != cudaSuccess) return cuda_status(e);
+        g->alive_h[v] = 0;
+        for (int t = 0; t < g->cap; ++t) {
+            mirror<T>(g, t, v) = inf_of<T>();
+            mirror<T>(g, v, t) = inf_of<T>();
+        }
+        g->n_live--;
+        g->last = apsp_stats{};
+        g->last.op = APSP_OP_REMOVE;
+        g->last.node = v;
+        g->last.node2 = -1;
+        g->last.n_live = g->n_live;
+        return mm_repair<T>(g, n_before);
+    }
     Dev<T> d = dev_of<T>(g);
     RepairCfg cfg = repair_cfg<T>(g, g->n_live, 1.0f / 3.0f, 0.0f);
     cudaError_t e = apsp::run_remove<T>(g->lc, d, v, cfg);
@@ -566,6 +637,26 @@ template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const v
     reset_ctl(g);
     Dev<T> d = dev_of<T>(g);
     cudaError_t e;
+    if (g->minimax) {
+        if (w < w_old) {
+            e = apsp::run_mm_decrease<T>(g->lc, d, u, v, w);
+            g->last.op = APSP_OP_DECREASE;
+            g->last.path = APSP_PATH_SWEEP;
+        } else {
+            e = apsp::run_mm_detect<T>(g->lc, d, g->mm_mask, g->mm_words, 1, u, v, w_old, w);
+            g->last.op = APSP_OP_INCREASE;
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        mirror<T>(g, u, v) = w;
+        if (g->undirected) mirror<T>(g, v, u) = w;
+        if (w < w_old) {
+            Ctl c;
+            apsp_status st = sync_ctl(g, &c);
+            g->last.sweep_rows = c.r_count;
+            return st;
+        }
+        return mm_repair<T>(g, g->n_live);
+    }
     if (w < w_old) {
         e = apsp::run_decrease<T>(g->lc, d, u, v, w);
         g->last.op = APSP_OP_DECREASE;
@@ -587,7 +678,7 @@ template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const v
 template <typename T> apsp_status recompute_impl(apsp_graph *g) {
     settle_fetch<T>(g);
     Dev<T> d = dev_of<T>(g);
-    cudaError_t e = apsp::run_fw<T>(g->lc, d);
+    cudaError_t e = g->minimax ? apsp::run_mm_fw<T>(g->lc, d) : apsp::run_fw<T>(g->lc, d);
     if (e != cudaSuccess) return cuda_status(e);
     g->last = apsp_stats{};
     g->last.op = APSP_OP_RECOMPUTE;
@@ -816,7 +907,7 @@ apsp_status apsp_init(apsp_graph **out, const void *W, int32_t n, int32_t capaci
     *out = nullptr;
     if (n < 0 || capacity < 1 || n > capacity || capacity > APSP_MAX_CAPACITY) return APSP_E_ARG;
     if (dtype != APSP_I32 && dtype != APSP_F32) return APSP_E_ARG;
-    if (flags & ~(uint32_t)(APSP_UNDIRECTED | APSP_D_GIVEN | APSP_DEVICE_INPUT)) return APSP_E_ARG;
+    if (flags & ~(uint32_t)(APSP_UNDIRECTED | APSP_D_GIVEN | APSP_DEVICE_INPUT | APSP_MINIMAX)) return APSP_E_ARG;
     if (n > 0 && !W) return APSP_E_ARG;
     if ((flags & APSP_D_GIVEN) && !D_or_null) return APSP_E_ARG;
     int dev = 0, ndev = 0;
@@ -825,6 +916,7 @@ apsp_status apsp_init(apsp_graph **out, const void *W, int32_t n, int32_t capaci
     g->dtype = dtype;
     g->flags = flags;
     g->undirected = (flags & APSP_UNDIRECTED) != 0;
+    g->minimax = (flags & APSP_MINIMAX) != 0;
     g->cap = capacity;
     g->ld = round_up(capacity, 128);
     g->esz = 4;
@@ -917,6 +1009,7 @@ apsp_status apsp_query_batch(apsp_graph *g, const int32_t *uv, int32_t count, vo
 apsp_status apsp_query_paths(apsp_graph *g, const int32_t *uv, int32_t count, int32_t *paths, int32_t stride,
                              int32_t *lens) {
     if (!g) return APSP_E_ARG;
+    if (g->minimax) return APSP_E_UNSUPPORTED;
     return g->dtype == APSP_F32 ? paths_impl<float>(g, uv, count, paths, stride, lens)
                                 : paths_impl<int32_t>(g, uv, count, paths, stride, lens);
 }
@@ -929,6 +1022,7 @@ apsp_status apsp_query_path(apsp_graph *g, int32_t u, int32_t v, int32_t *path, 
 apsp_status apsp_query_all_paths(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, int64_t nodes_cap,
                                  int64_t *offsets, int32_t paths_cap, int32_t *n_paths, int64_t *n_nodes) {
     if (!g) return APSP_E_ARG;
+    if (g->minimax) return APSP_E_UNSUPPORTED;
     return g->dtype == APSP_F32 ? all_paths_impl<float>(g, u, v, nodes, nodes_cap, offsets, paths_cap, n_paths, n_nodes)
                                 : all_paths_impl<int32_t>(g, u, v, nodes, nodes_cap, offsets, paths_cap, n_paths, n_nodes);
 }
@@ -977,6 +1071,7 @@ apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *s) {
     s->grown_pairs = -1;
     s->grown_rows = -1;
     s->grown_cost = -1.f;
+    if (g->minimax) return st;   // filled by the update itself
     const int op = g->last.op;
     if (op == APSP_OP_REMOVE || op == APSP_OP_INCREASE) {
         s->affected_rows = c.n_rows;
@@ -1017,6 +1112,29 @@ apsp_status apsp_copy_last_list(apsp_graph *g, int32_t *ij, int64_t cap, int64_t
     if (st != APSP_OK) return st;
     const int op = g->last.op;
     if (op != APSP_OP_REMOVE && op != APSP_OP_INCREASE) return APSP_OK;
+    if (g->minimax) {
+        const int64_t words = g->mm_words, rows = g->hwm;
+        std::vector<uint32_t> m((size_t)(rows * words));
+        if (rows > 0) {
+            cudaError_t e = cudaMemcpyAsync(m.data(), g->mm_mask, m.size() * 4, cudaMemcpyDeviceToHost, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        int64_t n = 0;
+        for (uint32_t x : m) n += __builtin_popcount(x);
+        *count = n;
+        if (!ij) return APSP_OK;
+        if (cap < n) return APSP_E_ARG;
+        int64_t q = 0;
+        for (int64_t i = 0; i < rows; ++i)
+            for (int64_t wd = 0; wd < words; ++wd)
+                for (uint32_t x = m[(size_t)(i * words + wd)]; x; x &= x - 1) {
+                    ij[2 * q] = (int32_t)i;
+                    ij[2 * q + 1] = (int32_t)(wd * 32 + __builtin_ctz(x));
+                    ++q;
+                }
+        return APSP_OK;
+    }
     if (c.overflow) return APSP_E_CAPACITY;
     const int n_items = (int)(c.alloc & 0xFFFFFFull);
     const int64_t n_pairs = (int64_t)(c.alloc >> 24);
@@ -1055,6 +1173,7 @@ apsp_status apsp_set_dispatch(apsp_graph *g, apsp_dispatch mode, double delta) {
 
 apsp_status apsp_set_list_mode(apsp_graph *g, apsp_list_mode mode) {
     if (!g || mode < APSP_LIST_COROLLARY3 || mode > APSP_LIST_ALGORITHM12) return APSP_E_ARG;
+    if (g->minimax && mode != APSP_LIST_COROLLARY3) return APSP_E_UNSUPPORTED;
     if (mode == APSP_LIST_ALGORITHM12 && !g->umask) {
         const int64_t hunit_cap = g->ld * ((g->ld + 1023) / 1024);
         g->umask = (uint32_t *)dalloc(g, (size_t)hunit_cap * 32 * sizeof(uint32_t));
@@ -1066,6 +1185,7 @@ apsp_status apsp_set_list_mode(apsp_graph *g, apsp_list_mode mode) {
 
 apsp_status apsp_set_exact_list(apsp_graph *g, int32_t on) {
     if (!g) return APSP_E_ARG;
+    if (g->minimax && on) return APSP_E_UNSUPPORTED;
     if (on && !g->grown_flag) {
         g->grown_flag = (int32_t *)dalloc(g, (size_t)g->ld * sizeof(int32_t));
         if (!g->grown_flag) return APSP_E_NOMEM;
@@ -1646,7 +1766,7 @@ apsp_status apsp_batch_run(apsp_batch *b, apsp_graph *const *graphs, int32_t n_g
     for (int gi = 0; gi < n_graphs; ++gi) {
         apsp_graph *g = graphs[gi];
         if (!g || g->dtype != dtype) return APSP_E_ARG;
-        if (g->undirected || !g->DT || g->cap > APSP_BATCH_MAX_SLOTS) return APSP_E_UNSUPPORTED;
+        if (g->undirected || !g->DT || g->minimax || g->cap > APSP_BATCH_MAX_SLOTS) return APSP_E_UNSUPPORTED;
         for (int gj = 0; gj < gi; ++gj)
             if (graphs[gj] == g) return APSP_E_ARG;
     }
@@ -1877,6 +1997,7 @@ extern "C" apsp_status apsp_serve(apsp_graph *const *graphs, int32_t n_graphs, c
     const int dtype = graphs[0] ? graphs[0]->dtype : -1;
     for (int gi = 0; gi < n_graphs; ++gi) {
         if (!graphs[gi] || graphs[gi]->dtype != dtype) return APSP_E_ARG;
+        if (graphs[gi]->minimax) return APSP_E_UNSUPPORTED;
         for (int gj = 0; gj < gi; ++gj)
             if (graphs[gj] == graphs[gi]) return APSP_E_ARG;
     }

@@ -214,19 +214,22 @@ template <typename T> __global__ void k_transpose(const T *__restrict__ D, T *__
 // Floyd-Warshall, one launch per phase (cold solver at init / recompute)
 // --------------------------------------------------------------------------
 
-template <typename T> __global__ void __launch_bounds__(FW_THREADS) k_fw_p1(T *D, int64_t ld, int kb) {
+template <typename T, typename M = MinPlus<T>>
+__global__ void __launch_bounds__(FW_THREADS) k_fw_p1(T *D, int64_t ld, int kb) {
     __shared__ FwDiagSmem<T> sm;
-    fw_close_diag<T>(D + (int64_t)kb * FW_B * ld + (int64_t)kb * FW_B, ld, sm);
+    fw_close_diag<T, M>(D + (int64_t)kb * FW_B * ld + (int64_t)kb * FW_B, ld, sm);
 }
 
-template <typename T> __global__ void __launch_bounds__(FW_THREADS, 2) k_fw_p2(T *D, int64_t ld, int kb, int nb) {
+template <typename T, typename M = MinPlus<T>>
+__global__ void __launch_bounds__(FW_THREADS, 2) k_fw_p2(T *D, int64_t ld, int kb, int nb) {
     __shared__ FwSmem<T> sm;
-    fw_phase2_tile<T>(D, ld, kb, nb, blockIdx.x, sm);
+    fw_phase2_tile<T, M>(D, ld, kb, nb, blockIdx.x, sm);
 }
 
-template <typename T> __global__ void __launch_bounds__(FW_THREADS, 2) k_fw_p3(T *D, int64_t ld, int kb, int nb) {
+template <typename T, typename M = MinPlus<T>>
+__global__ void __launch_bounds__(FW_THREADS, 2) k_fw_p3(T *D, int64_t ld, int kb, int nb) {
     __shared__ FwSmem<T> sm;
-    fw_phase3_tile<T>(D, ld, kb, nb, blockIdx.x, sm);
+    fw_phase3_tile<T, M>(D, ld, kb, nb, blockIdx.x, sm);
 }
 
 // --------------------------------------------------------------------------

@@ -288,6 +288,72 @@ template <typename T> cudaError_t batch_occupancy(size_t smem, int nt, int *per_
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<T, 256>, 256, smem);
 }
 
+// ---- minimax (bottleneck) distances: minimax.cuh --------------------------
+
+template <typename T> cudaError_t run_mm_fw(const LaunchCtx &c, const Dev<T> &d) {
+    using M = MinMax<T>;
+    const int nb = cdiv(d.span, FW_B);
+    cudaError_t e = cudaMemcpyAsync(d.D, d.W, (size_t)nb * FW_B * d.ld * sizeof(T), cudaMemcpyDeviceToDevice, c.stream);
+    if (e != cudaSuccess) return e;
+    for (int kb = 0; kb < nb; ++kb) {
+        if ((e = launch(c, "mm_fw_phase1", [&] { k_fw_p1<T, M><<<1, FW_THREADS, 0, c.stream>>>(d.D, d.ld, kb); })) != cudaSuccess) return e;
+        if (nb == 1) break;
+        if ((e = launch(c, "mm_fw_phase2", [&] { k_fw_p2<T, M><<<2 * (nb - 1), FW_THREADS, 0, c.stream>>>(d.D, d.ld, kb, nb); })) != cudaSuccess) return e;
+        if ((e = launch(c, "mm_fw_phase3", [&] { k_fw_p3<T, M><<<(nb - 1) * (nb - 1), FW_THREADS, 0, c.stream>>>(d.D, d.ld, kb, nb); })) != cudaSuccess) return e;
+    }
+    return run_transpose<T>(c, d);
+}
+
+template <typename T>
+cudaError_t run_mm_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
+    cudaError_t e;
+    if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
+    const int bands = cdiv(d.span, MM_CB);
+    int ranges = std::max(1, (3 * c.num_sms + bands - 1) / bands);
+    ranges = std::min(ranges, std::max(1, cdiv(d.span, 8)));
+    const int rows_per = cdiv(d.span, ranges);
+    const dim3 g(bands, cdiv(d.span, rows_per));
+    if ((e = launch(c, "mm_insert_reduce", [&] { k_mm_insert_reduce<T><<<g, 256, 0, c.stream>>>(d, rows_per); })) != cudaSuccess) return e;
+    if ((e = launch(c, "mm_insert_relax", [&] { k_mm_insert_relax<T><<<std::min(d.span, 4 * c.num_sms), 256, 0, c.stream>>>(d, p); })) != cudaSuccess) return e;
+    return launch(c, "mm_insert_finish", [&] { k_mm_insert_finish<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, p); });
+}
+
+template <typename T> cudaError_t run_mm_decrease(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w) {
+    cudaError_t e;
+    const int two = d.undirected ? 1 : 0;
+    if ((e = launch(c, "mm_legs", [&] { k_mm_legs<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, two, 1, w); })) != cudaSuccess) return e;
+    const int g = std::max(1, std::min(cdiv(d.span, 8), 4 * c.num_sms));
+    if (two) return launch(c, "mm_decrease", [&] { k_mm_decrease<T, true><<<g, 256, 0, c.stream>>>(d, u, v, w); });
+    return launch(c, "mm_decrease", [&] { k_mm_decrease<T, false><<<g, 256, 0, c.stream>>>(d, u, v, w); });
+}
+
+// kind 0: removal of node a (legs through a, list, then the tombstone);
+// kind 1: increase of edge (a, b) from w_old to w_new (W updated first).
+template <typename T>
+cudaError_t run_mm_detect(const LaunchCtx &c, const Dev<T> &d, uint32_t *mask, int words, int kind, int a, int b,
+                          T w_old, T w_new) {
+    cudaError_t e;
+    const bool two = kind == 1 && d.undirected;
+    const int lb = kind == 0 ? a : b;
+    if ((e = launch(c, "mm_legs", [&] {
+             k_mm_legs<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, a, lb, two ? 1 : 0, kind == 1 ? 1 : 0, w_new);
+         })) != cudaSuccess)
+        return e;
+    const int g = std::max(1, std::min(cdiv(d.span, 8), 4 * c.num_sms));
+    if (two)
+        e = launch(c, "mm_detect", [&] { k_mm_detect<T, true><<<g, 256, 0, c.stream>>>(d, mask, words, kind, a, w_old, w_new); });
+    else
+        e = launch(c, "mm_detect", [&] { k_mm_detect<T, false><<<g, 256, 0, c.stream>>>(d, mask, words, kind, a, w_old, w_new); });
+    if (e != cudaSuccess || kind != 0) return e;
+    return launch(c, "mm_tomb", [&] { k_mm_tomb<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, a); });
+}
+
+template <typename T>
+cudaError_t run_mm_pass(const LaunchCtx &c, const Dev<T> &d, const uint32_t *mask, int words, int pass) {
+    const int g = 4 * c.num_sms;
+    return launch(c, "mm_pass", [&] { k_mm_pass<T><<<g, 256, 0, c.stream>>>(d, mask, words, pass); });
+}
+
 #define APSP_INSTANTIATE(T)                                                                                   \
     template cudaError_t run_fill<T>(const LaunchCtx &, T *, T, int64_t);                                     \
     template cudaError_t run_sanitize<T>(const LaunchCtx &, T *, int64_t, int, int, Ctl *);                   \
@@ -301,6 +367,11 @@ template <typename T> cudaError_t batch_occupancy(size_t smem, int nt, int *per_
     template cudaError_t run_path_query<T>(const LaunchCtx &, const Dev<T> &, const PathQuery &, int);        \
     template cudaError_t setup_shapes<T>(LaunchCtx &, int64_t, int);                                          \
     template cudaError_t run_batch<T>(cudaStream_t, BatchHeader *, int, size_t, int);                         \
-    template cudaError_t batch_occupancy<T>(size_t, int, int *);
+    template cudaError_t batch_occupancy<T>(size_t, int, int *);                                             \
+    template cudaError_t run_mm_fw<T>(const LaunchCtx &, const Dev<T> &);                                     \
+    template cudaError_t run_mm_insert<T>(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int); \
+    template cudaError_t run_mm_decrease<T>(const LaunchCtx &, const Dev<T> &, int, int, T);                  \
+    template cudaError_t run_mm_detect<T>(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T); \
+    template cudaError_t run_mm_pass<T>(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);
 
 }  // namespace apsp

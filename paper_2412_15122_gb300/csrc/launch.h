@@ -9,6 +9,7 @@
 #include "kernels.cuh"
 #include "paths.cuh"
 #include "repair_p1.cuh"
+#include "minimax.cuh"
 
 namespace apsp {
 
@@ -41,5 +42,12 @@ template <typename T> cudaError_t run_path_query(const LaunchCtx &, const Dev<T>
 template <typename T> cudaError_t setup_shapes(LaunchCtx &, int64_t, int);
 template <typename T> cudaError_t run_batch(cudaStream_t, BatchHeader *, int, size_t, int);
 template <typename T> cudaError_t batch_occupancy(size_t, int, int *);
+// minimax (bottleneck) distances
+template <typename T> cudaError_t run_mm_fw(const LaunchCtx &, const Dev<T> &);
+template <typename T> cudaError_t run_mm_insert(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int);
+template <typename T> cudaError_t run_mm_decrease(const LaunchCtx &, const Dev<T> &, int, int, T);
+template <typename T>
+cudaError_t run_mm_detect(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T);
+template <typename T> cudaError_t run_mm_pass(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);
 
 }  // namespace apsp

@@ -84,8 +84,8 @@ def test_binding_constants_match_the_header():
     assert h["APSP_MAX_CAPACITY"] == apsp.APSP_MAX_CAPACITY
     assert h["APSP_MODEL_NPARAM"] == apsp.MODEL_NPARAM and h["APSP_MODEL_NTRAIN"] == apsp.MODEL_NTRAIN
     assert (h["APSP_I32"], h["APSP_F32"]) == (apsp.APSP_I32, apsp.APSP_F32)
-    assert (h["APSP_UNDIRECTED"], h["APSP_D_GIVEN"], h["APSP_DEVICE_INPUT"]) == \
-        (apsp.APSP_UNDIRECTED, apsp.APSP_D_GIVEN, apsp.APSP_DEVICE_INPUT)
+    assert (h["APSP_UNDIRECTED"], h["APSP_D_GIVEN"], h["APSP_DEVICE_INPUT"], h["APSP_MINIMAX"]) == \
+        (apsp.APSP_UNDIRECTED, apsp.APSP_D_GIVEN, apsp.APSP_DEVICE_INPUT, apsp.APSP_MINIMAX)
     for code, name in apsp.STATUS.items():
         assert h[name] == code, name
     assert [h["APSP_DISPATCH_DELTA"], h["APSP_DISPATCH_ALWAYS_WARM"], h["APSP_DISPATCH_ALWAYS_COLD"],

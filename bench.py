@@ -946,6 +946,79 @@ def run_serve_study(args):
         "alone_vs_mix_identical_n1024": same, "setup_seconds": gen_s}))
 
 
+def run_minimax_study(args):
+    """Minimax (bottleneck) distances: warm against cold per update.  Directed
+    complete graphs with int32 weights U[1, 1e6] (n = 1024 and 4096); the same
+    seeded removals, tight-edge increases and decreases go to two graphs, one
+    always warm and one always cold ((min, max) Floyd-Warshall); each update
+    is timed with CUDA events on the library's stream; the matrices are
+    compared after every update."""
+    import torch
+    from paper_2412_15122_gb300 import Graph, build
+    build.build()
+    stream = torch.cuda.Stream()
+    out = {}
+    for n in (1024, 4096):
+        cap = n + 32
+        W = synth.complete_digraph_i32(n, 1, 10**6, 900 + n)
+        gw = Graph(W, cap, stream=stream, minimax=True)
+        gc = Graph(W, cap, stream=stream, minimax=True)
+        gw.set_dispatch("warm")
+        gc.set_dispatch("cold")
+        Wm = np.full((cap, cap), synth.INF_I32, np.int32)
+        Wm[:n, :n] = W
+        alive = np.zeros(cap, bool)
+        alive[:n] = True
+        ups = synth.mixed_updates(n, args.study_updates, 900 + n, fractions=(0.0, 0.34, 0.33, 0.33), tight=True,
+                                  capacity=cap, stream=95)
+        rec = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for up in ups:
+            live = np.flatnonzero(alive)
+            if up.kind == synth.REMOVE:
+                k = int(live[up.a])
+                call = lambda g, k=k: g.remove_node(k)
+                alive[k] = False
+                Wm[k, :] = Wm[:, k] = synth.INF_I32
+            else:
+                u = int(live[up.a])
+                row = np.where(alive, Wm[u].astype(np.int64), synth.INF_I32)
+                row[u] = synth.INF_I32
+                v = int(np.argmin(row))
+                w = int(Wm[u, v]) // 2 if up.kind == synth.DECREASE else int(Wm[u, v]) * 4 + 1
+                call = lambda g, u=u, v=v, w=w: g.update_edge(u, v, w)
+                Wm[u, v] = w
+            times = []
+            for g in (gw, gc):
+                e0.record(stream)
+                call(g)
+                e1.record(stream)
+                g.sync()
+                times.append(e0.elapsed_time(e1))
+            st = gw.stats()
+            r = rec.setdefault(up.kind, {"count": 0, "warm_ms": 0.0, "cold_ms": 0.0, "pairs": 0, "cost": 0.0,
+                                         "passes": 0, "warm_faster": 0})
+            r["count"] += 1
+            r["warm_ms"] += times[0]
+            r["cold_ms"] += times[1]
+            r["pairs"] += st["affected_pairs"]
+            r["cost"] += st["cost"]
+            r["passes"] += st["passes"]
+            r["warm_faster"] += times[0] < times[1]
+        same = bool(np.array_equal(gw.D(), gc.D()))
+        gw.close()
+        gc.close()
+        for r in rec.values():
+            c = max(1, r["count"])
+            for f in ("warm_ms", "cold_ms", "pairs", "cost", "passes"):
+                r["avg_" + f] = round(r.pop(f) / c, 4)
+        out[str(n)] = {"per_type": rec, "warm_and_cold_identical": same}
+    print(json.dumps({"study": "minimax", "updates_per_size": args.study_updates,
+                      "workload": "directed complete graphs, int32 U[1, 1e6], minimax distances; removals, "
+                                  "lightest-out-edge increases (x4 + 1) and decreases (halved)",
+                      "results": out}))
+
+
 def detailed_pass(Graph, A, W, ops, stream, profile=False):
     """Replays `ops` on a fresh graph, one wait per update: per update type
     the count, the library's statistics and the device time of the update
@@ -1037,7 +1110,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--study-queries", type=int, default=4096)
     ap.add_argument("--study-reps", type=int, default=20)
-    ap.add_argument("--study", choices=["dispatch", "batch", "serve", "paths", "ratios"],
+    ap.add_argument("--study", choices=["dispatch", "batch", "serve", "paths", "ratios", "minimax"],
                     help="dispatch: train the warm/cold cost model and compare it with the delta rule, "
                          "always-warm and always-cold on n=16384 undirected Euclidean updates")
     ap.add_argument("--study-updates", type=int, default=100)
@@ -1059,6 +1132,8 @@ def main():
         return run_path_study(args)
     if args.study == "ratios":
         return run_ratio_study(args)
+    if args.study == "minimax":
+        return run_minimax_study(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

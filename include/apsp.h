@@ -402,18 +402,12 @@ apsp_status apsp_batch_info_get(apsp_batch *b, apsp_batch_info *info);
 apsp_status apsp_batch_tuned_width(apsp_dtype dtype, int32_t max_span, int32_t *threads);
 
 /* ----- serving loop ---------------------------------------------------------
- * Replays a trace of timed requests against resident graphs in real time with
- * continuous (wave-level) batching: arrived requests queue per graph; while
- * the GPU is busy with one wave the next arrivals queue, and when it is free
- * one wave admits every queued request whose graph fits the budget (a query
- * ends its graph's share of a wave, so it sees exactly the updates that
- * arrived before it).  In a wave, graphs with capacity <= small_max_slots are
- * updated by one persistent batched launch (apsp_batch_*), which flags each
- * graph's completion in mapped host memory as soon as its CTA finishes;
- * larger graphs run the one-call-per-update path on their own streams,
- * completion observed with events.  Per graph, requests take effect in
- * arrival order, so every graph ends exactly as if its requests had been
- * applied alone.  Requests must be sorted by arrival time. */
+ * Replays a trace of timed requests against resident graphs in real time
+ * through an online server (apsp_server_*, below): each request is submitted
+ * at its arrival time and served with the server's continuous batching.  Per
+ * graph, requests take effect in arrival order, so every graph ends exactly
+ * as if its requests had been applied alone.  Requests must be sorted by
+ * arrival time; admit_s / done_s are seconds after the start of the call. */
 #define APSP_BATCH_QUERY 3    /* request op besides apsp_batch_op: distance u -> v */
 typedef struct {
     apsp_batch_item item;     /* ADD / REMOVE / EDGE, or APSP_BATCH_QUERY with (u, v) */
@@ -429,13 +423,53 @@ typedef struct {
     int32_t pad_;
 } apsp_request_result;
 typedef struct {
-    double hbm_budget_bytes;  /* bytes of graph state (W, D, D^T) one wave may touch; 0 = unlimited
+    double hbm_budget_bytes;  /* bytes of graph state (W, D, D^T) in work at once; 0 = unlimited
                                  (a single graph larger than the budget still runs alone) */
     int32_t small_max_slots;  /* graphs of capacity <= this use the batched kernel (0: none) */
     int32_t max_wave_requests;/* 0 = unlimited */
 } apsp_serve_config;
 apsp_status apsp_serve(apsp_graph *const *graphs, int32_t n_graphs, const apsp_request *reqs, int32_t count,
                        const apsp_serve_config *cfg, apsp_request_result *results);
+
+/* ----- online server --------------------------------------------------------
+ * A server owns a worker thread that applies requests to resident graphs as
+ * they arrive, with continuous batching: every graph has a FIFO of requests;
+ * whenever a graph has no work on the GPU it takes the requests queued for it
+ * (up to and including its first query, so a query sees exactly the updates
+ * submitted before it for that graph) and they go to the GPU at once -- small
+ * graphs (capacity <= cfg.small_max_slots) together in one persistent batched
+ * launch, the others one call per update on their own streams.  A graph whose
+ * work completes is served again at once, whatever the other graphs are
+ * doing, so small graphs are not held back by a large graph's repair.  A graph
+ * is admitted only while the graph state on the GPU stays within
+ * cfg.hbm_budget_bytes (a graph larger than the budget still runs alone).
+ * Per graph, requests take effect in submission order: every graph ends as if
+ * its requests had been applied alone.  Results report the time the request
+ * went to the GPU (admit_s) and the time its completion was observed (done_s)
+ * in seconds on the server's clock (apsp_server_clock), `wave` = the dispatch
+ * round that took it.  While a server lives, the served graphs must not be
+ * used by any other call.  submit / poll / wait / clock may be called from
+ * any host thread. */
+typedef struct apsp_server apsp_server;
+/* Graphs of one dtype, not APSP_MINIMAX.  cfg is copied. */
+apsp_status apsp_server_create(apsp_server **s, apsp_graph *const *graphs, int32_t n_graphs,
+                               const apsp_serve_config *cfg);
+/* Queues one request (an apsp_batch_item whose graph indexes the server's
+ * graphs; op APSP_BATCH_ADD / REMOVE / EDGE or APSP_BATCH_QUERY with (u, v)).
+ * The weight vectors of an ADD are copied, so the caller's buffers may be
+ * reused at once.  *ticket identifies the request (0, 1, 2, ... in
+ * submission order).  An invalid request completes with its error status. */
+apsp_status apsp_server_submit(apsp_server *s, const apsp_batch_item *item, int64_t *ticket);
+/* Non-blocking: *done = 1 and *res filled once the request has completed. */
+apsp_status apsp_server_poll(apsp_server *s, int64_t ticket, apsp_request_result *res, int32_t *done);
+/* Waits up to timeout_s seconds for the request; APSP_E_BUSY if it has not
+ * completed by then. */
+apsp_status apsp_server_wait(apsp_server *s, int64_t ticket, double timeout_s, apsp_request_result *res);
+/* Seconds since the server was created (the clock of admit_s / done_s). */
+double apsp_server_clock(apsp_server *s);
+/* Completes every submitted request, then stops the worker and frees the
+ * server (the graphs stay valid). */
+apsp_status apsp_server_destroy(apsp_server *s);
 
 /* ----- instrumentation ---------------------------------------------------- */
 

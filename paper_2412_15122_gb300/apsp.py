@@ -144,6 +144,11 @@ def _load():
         "apsp_batch_tuned_width": [I32, I32, ctypes.POINTER(I32)],
         "apsp_serve": [ctypes.POINTER(P), I32, ctypes.POINTER(apsp_request), I32, ctypes.POINTER(apsp_serve_config),
                        ctypes.POINTER(apsp_request_result)],
+        "apsp_server_create": [ctypes.POINTER(P), ctypes.POINTER(P), I32, ctypes.POINTER(apsp_serve_config)],
+        "apsp_server_submit": [P, ctypes.POINTER(apsp_batch_item), ctypes.POINTER(I64)],
+        "apsp_server_poll": [P, I64, ctypes.POINTER(apsp_request_result), ctypes.POINTER(I32)],
+        "apsp_server_wait": [P, I64, ctypes.c_double, ctypes.POINTER(apsp_request_result)],
+        "apsp_server_destroy": [P],
         "apsp_set_model": [P, P],
         "apsp_model_loss_grad": [P, P, P, I32, P, P],
         "apsp_model_predict": [P, P, I32, P],
@@ -153,6 +158,8 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.apsp_server_clock.argtypes = [P]
+    lib.apsp_server_clock.restype = ctypes.c_double
     lib.apsp_launch_count.argtypes = [P]
     lib.apsp_launch_count.restype = I64
     lib.apsp_status_string.argtypes = [ctypes.c_int]
@@ -504,6 +511,82 @@ def apsp_serve(graphs: Sequence[int], requests, arrivals, hbm_budget_bytes: floa
     _check(_load().apsp_serve(hs, len(graphs), arr, n, ctypes.byref(cfg), out), "apsp_serve")
     res = {k: np.array([getattr(out[q], k) for q in range(n)]) for k in ("admit_s", "done_s", "dist", "status", "wave", "new_id")}
     return res
+
+
+def _result_dict(r) -> dict:
+    return {k: getattr(r, k) for k in ("admit_s", "done_s", "dist", "status", "wave", "new_id")}
+
+
+def apsp_server_create(graphs: Sequence[int], hbm_budget_bytes: float = 0.0, small_max_slots: int = 0,
+                       max_wave_requests: int = 0) -> int:
+    cfg = apsp_serve_config(float(hbm_budget_bytes), int(small_max_slots), int(max_wave_requests))
+    hs = (ctypes.c_void_p * len(graphs))(*graphs)
+    h = ctypes.c_void_p()
+    _check(_load().apsp_server_create(ctypes.byref(h), hs, len(graphs), ctypes.byref(cfg)), "apsp_server_create")
+    return h.value
+
+
+def apsp_server_submit(s: int, item) -> int:
+    e = apsp_batch_item()
+    keep = []
+    _fill_item(e, item, keep)
+    t = ctypes.c_int64(-1)
+    _check(_load().apsp_server_submit(s, ctypes.byref(e), ctypes.byref(t)), "apsp_server_submit")
+    return t.value
+
+
+def apsp_server_poll(s: int, ticket: int):
+    """The request's result dict once it has completed, else None."""
+    r = apsp_request_result()
+    done = ctypes.c_int32(0)
+    _check(_load().apsp_server_poll(s, ticket, ctypes.byref(r), ctypes.byref(done)), "apsp_server_poll")
+    return _result_dict(r) if done.value else None
+
+
+def apsp_server_wait(s: int, ticket: int, timeout_s: float = 60.0) -> dict:
+    r = apsp_request_result()
+    _check(_load().apsp_server_wait(s, ticket, float(timeout_s), ctypes.byref(r)), "apsp_server_wait")
+    return _result_dict(r)
+
+
+def apsp_server_clock(s: int) -> float:
+    return float(_load().apsp_server_clock(s))
+
+
+def apsp_server_destroy(s: int):
+    _check(_load().apsp_server_destroy(s), "apsp_server_destroy")
+
+
+class Server:
+    """Online server over resident graphs (apsp_server_*): submit requests as
+    they arrive, poll or wait for their results.  Requests are the items of
+    apsp_batch_run plus ("query", u, v), each starting with its graph index."""
+
+    def __init__(self, graphs, hbm_budget_bytes: float = 0.0, small_max_slots: int = 0, max_wave_requests: int = 0):
+        self.h = apsp_server_create([g.h for g in graphs], hbm_budget_bytes, small_max_slots, max_wave_requests)
+
+    def submit(self, item) -> int:
+        return apsp_server_submit(self.h, item)
+
+    def poll(self, ticket: int):
+        return apsp_server_poll(self.h, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> dict:
+        return apsp_server_wait(self.h, ticket, timeout_s)
+
+    def clock(self) -> float:
+        return apsp_server_clock(self.h)
+
+    def close(self):
+        if self.h:
+            apsp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

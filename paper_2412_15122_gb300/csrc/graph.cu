@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <chrono>
 #include <cstring>
+#include <condition_variable>
 #include <deque>
 #include <thread>
 #include <limits>
@@ -1790,210 +1791,266 @@ struct Clock {
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
-// One graph's share of a wave.
-struct Segment {
-    int graph;
-    std::vector<int> reqs;   // request indices, in arrival order
-    bool small = false;
-    int small_index = -1;    // index among the wave's batched graphs
-    int query = -1;          // the closing query, if any
-    cudaEvent_t ev = nullptr;
-    bool done = false;
+}  // namespace
+
+struct apsp_server {
+    struct Req {
+        apsp_batch_item item{};
+        std::vector<char> iw, ow;   // copies of an ADD's weight vectors
+        apsp_request_result res{};
+        bool done = false;
+    };
+    std::vector<apsp_graph *> graphs;
+    apsp_serve_config cfg{};
+    int dtype = APSP_I32, device = 0;
+    std::vector<char> small;
+    std::vector<double> bytes;
+    apsp_batch *b = nullptr;
+    void *qbuf = nullptr;           // pinned: the query result in flight, one element per graph
+    Clock clk;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req> reqs;           // by ticket; deque: elements never move
+    std::deque<int64_t> inbox;      // submitted, not yet taken by the worker
+    bool stop = false;
+    std::thread worker;
 };
 
-template <typename T>
-apsp_status serve_impl(apsp_graph *const *graphs, int n_graphs, const apsp_request *reqs, int count,
-                       const apsp_serve_config &cfg, apsp_request_result *res) {
-    std::vector<bool> small(n_graphs);
-    std::vector<double> bytes(n_graphs);
-    for (int gi = 0; gi < n_graphs; ++gi) {
-        apsp_graph *g = graphs[gi];
-        small[gi] = cfg.small_max_slots > 0 && g->cap <= cfg.small_max_slots && !g->undirected && g->DT &&
-                    g->cap <= APSP_BATCH_MAX_SLOTS;
-        bytes[gi] = (double)g->ld * g->ld * g->esz * (g->undirected ? 2 : 3);
-    }
-    apsp_batch *b = nullptr;
-    apsp_status st = apsp_batch_create(&b, nullptr);
-    if (st != APSP_OK) return st;
-    T *qbuf = nullptr;   // pinned query results
-    if (cudaMallocHost(&qbuf, std::max(1, count) * sizeof(T)) != cudaSuccess) {
-        apsp_batch_destroy(b);
-        return APSP_E_NOMEM;
-    }
-    for (int q = 0; q < count; ++q) {
-        res[q] = apsp_request_result{};
-        res[q].new_id = -1;
-        res[q].wave = -1;
-    }
-    std::vector<std::deque<int>> pend(n_graphs);
-    Clock clk;
-    int next = 0, finished = 0, wave = 0, rr = 0;
+namespace {
+
+// The worker: intake, completions, then one dispatch round over the graphs
+// that have no work on the GPU.
+template <typename T> void server_loop(apsp_server *s) {
+    cudaSetDevice(s->device);
+    const int G = (int)s->graphs.size();
+    struct GraphState {
+        std::deque<int64_t> pend;
+        bool busy = false, in_batch = false, bdone = false;
+        std::vector<int64_t> seg;
+        int64_t query = -1;
+        int bidx = -1;
+        cudaEvent_t ev = nullptr;
+    };
+    std::vector<GraphState> gs(G);
+    for (auto &g : gs) cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming);
     cudaEvent_t small_q_ev = nullptr;
     cudaEventCreateWithFlags(&small_q_ev, cudaEventDisableTiming);
-    while (finished < count) {
-        double now = clk.now();
-        while (next < count && reqs[next].arrival_s <= now) pend[reqs[next].item.graph].push_back(next++);
-        bool any = false;
-        for (auto &p : pend) any |= !p.empty();
-        if (!any) {
-            // idle until the next arrival (sleep for long gaps, then spin)
-            const double gap = reqs[next].arrival_s - now;
-            if (gap > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(gap - 1e-4));
-            continue;
+    T *qbuf = (T *)s->qbuf;
+    bool batch_busy = false, batch_q = false;
+    apsp_status bst = APSP_OK;
+    std::vector<int> bg;
+    double used = 0;
+    int wave = 0;
+
+    auto finish = [&](int gi, apsp_status override_st) {
+        GraphState &g = gs[gi];
+        const double t = s->clk.now();
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (int64_t q : g.seg) {
+            apsp_server::Req &r = s->reqs[(size_t)q];
+            r.res.done_s = t;
+            if (override_st != APSP_OK && r.res.status == APSP_OK) r.res.status = override_st;
+            if (r.item.op == APSP_BATCH_QUERY && r.res.status == APSP_OK) r.res.dist = (double)qbuf[gi];
+            r.done = true;
         }
-        // ---- form the wave: round-robin over graphs, within the budget
-        std::vector<Segment> segs;
-        double used = 0;
-        int taken = 0;
-        for (int k = 0; k < n_graphs; ++k) {
-            const int gi = (rr + k) % n_graphs;
-            if (pend[gi].empty()) continue;
-            if (cfg.hbm_budget_bytes > 0 && !segs.empty() && used + bytes[gi] > cfg.hbm_budget_bytes) continue;
-            if (cfg.max_wave_requests > 0 && taken >= cfg.max_wave_requests) break;
-            Segment s;
-            s.graph = gi;
-            s.small = small[gi];
-            while (!pend[gi].empty()) {
-                if (cfg.max_wave_requests > 0 && taken >= cfg.max_wave_requests) break;
-                const int q = pend[gi].front();
-                pend[gi].pop_front();
-                s.reqs.push_back(q);
-                ++taken;
-                if (reqs[q].item.op == APSP_BATCH_QUERY) {
-                    s.query = q;
-                    break;
-                }
-            }
-            used += bytes[gi];
-            segs.push_back(std::move(s));
-        }
-        rr = (rr + 1) % n_graphs;
-        const double admit = clk.now();
-        for (auto &s : segs)
-            for (int q : s.reqs) {
-                res[q].admit_s = admit;
-                res[q].wave = wave;
-            }
-        // ---- batched graphs: one persistent launch
-        std::vector<apsp_graph *> bgraphs;
-        std::vector<apsp_batch_item> bitems;
-        std::vector<int> bmap;   // batch item -> request
-        for (auto &s : segs) {
-            if (!s.small) continue;
-            s.small_index = (int)bgraphs.size();
-            bgraphs.push_back(graphs[s.graph]);
-            for (int q : s.reqs) {
-                if (reqs[q].item.op == APSP_BATCH_QUERY) continue;
-                apsp_batch_item it = reqs[q].item;
-                it.graph = s.small_index;
-                bitems.push_back(it);
-                bmap.push_back(q);
+        g.seg.clear();
+        g.busy = g.in_batch = false;
+        g.query = -1;
+        used -= s->bytes[gi];
+        s->cv_done.notify_all();
+    };
+    // the graph's requests up to and including its first query
+    auto take = [&](int gi, int &budget_left) {
+        GraphState &g = gs[gi];
+        while (!g.pend.empty() && budget_left != 0) {
+            const int64_t q = g.pend.front();
+            g.pend.pop_front();
+            g.seg.push_back(q);
+            if (budget_left > 0) --budget_left;
+            if (s->reqs[(size_t)q].item.op == APSP_BATCH_QUERY) {
+                g.query = q;
+                break;
             }
         }
-        apsp_status bst = APSP_OK;
-        std::vector<int32_t> bids(bitems.size(), -1);
-        if (!bgraphs.empty()) {
-            bst = batch_launch<T>(b, bgraphs.data(), (int)bgraphs.size(), bitems.data(), (int)bitems.size(),
-                                  bids.data(), true);
-            bool any_q = false;
-            for (auto &s : segs)
-                if (s.small && s.query >= 0 && bst == APSP_OK) {
-                    const apsp_batch_item &it = reqs[s.query].item;
-                    apsp_graph *g = graphs[s.graph];
-                    cudaMemcpyAsync(qbuf + s.query, (T *)g->D + (int64_t)it.u * g->ld + it.v, sizeof(T),
-                                    cudaMemcpyDeviceToHost, b->stream);
-                    any_q = true;
-                }
-            if (any_q) cudaEventRecord(small_q_ev, b->stream);
+    };
+    // one call per update on the graph's own stream
+    auto issue_calls = [&](int gi) {
+        GraphState &g = gs[gi];
+        apsp_graph *gr = s->graphs[gi];
+        for (int64_t q : g.seg) {
+            apsp_server::Req &r = s->reqs[(size_t)q];
+            const apsp_batch_item &it = r.item;
+            apsp_status st = APSP_OK;
+            if (it.op == APSP_BATCH_ADD) {
+                int32_t id = -1;
+                st = apsp_add_node(gr, it.in_w, it.out_w, &id);
+                r.res.new_id = id;
+            } else if (it.op == APSP_BATCH_REMOVE) {
+                st = apsp_remove_node(gr, it.u);
+            } else if (it.op == APSP_BATCH_EDGE) {
+                T w;
+                st = batch_weight<T>(it.w, &w);
+                if (st == APSP_OK) st = apsp_update_edge(gr, it.u, it.v, &w);
+            } else if (it.u < 0 || it.v < 0 || it.u >= gr->cap || it.v >= gr->cap) {
+                st = APSP_E_NODE;
+            } else {
+                settle_fetch<T>(gr);
+                cudaMemcpyAsync(qbuf + gi, (T *)gr->D + (int64_t)it.u * gr->ld + it.v, sizeof(T),
+                                cudaMemcpyDeviceToHost, gr->stream);
+            }
+            r.res.status = st;
         }
-        // ---- other graphs: the one-call-per-update path on their own streams
-        for (auto &s : segs) {
-            if (s.small) continue;
-            apsp_graph *g = graphs[s.graph];
-            for (int q : s.reqs) {
-                const apsp_batch_item &it = reqs[q].item;
-                apsp_status r = APSP_OK;
-                if (it.op == APSP_BATCH_ADD) {
-                    int32_t id = -1;
-                    r = apsp_add_node(g, it.in_w, it.out_w, &id);
-                    res[q].new_id = id;
-                } else if (it.op == APSP_BATCH_REMOVE) {
-                    r = apsp_remove_node(g, it.u);
-                } else if (it.op == APSP_BATCH_EDGE) {
-                    T w;
-                    r = batch_weight<T>(it.w, &w);
-                    if (r == APSP_OK) r = apsp_update_edge(g, it.u, it.v, &w);
+        cudaEventRecord(g.ev, gr->stream);
+        g.busy = true;
+    };
+
+    while (true) {
+        // ---- intake
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            while (!s->inbox.empty()) {
+                const int64_t q = s->inbox.front();
+                s->inbox.pop_front();
+                gs[s->reqs[(size_t)q].item.graph].pend.push_back(q);
+            }
+            if (s->stop) {
+                bool idle = !batch_busy;
+                for (auto &g : gs) idle = idle && !g.busy && g.pend.empty();
+                if (idle) break;
+            }
+        }
+        bool progress = false;
+        // ---- completions: graphs on their own streams
+        for (int gi = 0; gi < G; ++gi)
+            if (gs[gi].busy && !gs[gi].in_batch && cudaEventQuery(gs[gi].ev) == cudaSuccess) {
+                finish(gi, APSP_OK);
+                progress = true;
+            }
+        // ---- completions: the batched launch (per-graph flags in mapped memory)
+        if (batch_busy) {
+            bool all = true, q_ready = !batch_q;
+            for (int gi : bg) {
+                GraphState &g = gs[gi];
+                if (g.bdone) continue;
+                const int flag = ((volatile int32_t *)s->b->h_done)[g.bidx];
+                if (flag > 1) bst = APSP_E_TIMEOUT;
+                if (flag != 0 && g.query >= 0 && !q_ready) q_ready = cudaEventQuery(small_q_ev) == cudaSuccess;
+                if (flag != 0 && (g.query < 0 || q_ready)) {
+                    g.bdone = true;
+                    finish(gi, bst);
+                    progress = true;
                 } else {
-                    if (it.u < 0 || it.v < 0 || it.u >= g->cap || it.v >= g->cap) {
-                        r = APSP_E_NODE;
-                    } else {
-                        settle_fetch<T>(g);
-                        cudaMemcpyAsync(qbuf + q, (T *)g->D + (int64_t)it.u * g->ld + it.v, sizeof(T),
-                                        cudaMemcpyDeviceToHost, g->stream);
-                    }
+                    all = false;
                 }
-                res[q].status = r;
             }
-            cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
-            cudaEventRecord(s.ev, g->stream);
+            if (all) {
+                batch_finish(s->b);
+                batch_busy = false;
+                bg.clear();
+            }
         }
-        // ---- completions
-        int left = (int)segs.size();
-        bool small_q_done = false;
-        while (left > 0) {
-            for (auto &s : segs) {
-                if (s.done) continue;
-                bool ok = false;
-                if (s.small) {
-                    if (bst != APSP_OK) {
-                        ok = true;
-                    } else {
-                        const int flag = ((volatile int32_t *)b->h_done)[s.small_index];
-                        if (flag != 0 && s.query >= 0 && !small_q_done)
-                            small_q_done = cudaEventQuery(small_q_ev) == cudaSuccess;
-                        ok = flag != 0 && (s.query < 0 || small_q_done);
-                        if (flag > 1) bst = APSP_E_TIMEOUT;
-                    }
+        // ---- dispatch round
+        int budget_left = s->cfg.max_wave_requests > 0 ? s->cfg.max_wave_requests : -1;
+        std::vector<int> round;
+        auto fits = [&](int gi) {
+            return s->cfg.hbm_budget_bytes <= 0 || used <= 0 || used + s->bytes[gi] <= s->cfg.hbm_budget_bytes;
+        };
+        if (!batch_busy) {
+            std::vector<apsp_graph *> bgraphs;
+            std::vector<apsp_batch_item> bitems;
+            std::vector<int64_t> bmap;
+            for (int gi = 0; gi < G && budget_left != 0; ++gi) {
+                GraphState &g = gs[gi];
+                if (!s->small[gi] || g.busy || g.pend.empty() || !fits(gi)) continue;
+                take(gi, budget_left);
+                g.busy = g.in_batch = true;
+                g.bdone = false;
+                g.bidx = (int)bgraphs.size();
+                used += s->bytes[gi];
+                bgraphs.push_back(s->graphs[gi]);
+                bg.push_back(gi);
+                round.push_back(gi);
+                for (int64_t q : g.seg) {
+                    const apsp_batch_item &it = s->reqs[(size_t)q].item;
+                    if (it.op == APSP_BATCH_QUERY) continue;
+                    apsp_batch_item bi = it;
+                    bi.graph = g.bidx;
+                    bitems.push_back(bi);
+                    bmap.push_back(q);
+                }
+            }
+            if (!bgraphs.empty()) {
+                std::vector<int32_t> ids(bitems.size(), -1);
+                bst = batch_launch<T>(s->b, bgraphs.data(), (int)bgraphs.size(), bitems.data(), (int)bitems.size(),
+                                      ids.data(), true);
+                if (bst == APSP_OK) {
+                    batch_busy = true;
+                    batch_q = false;
+                    for (size_t k = 0; k < bmap.size(); ++k) s->reqs[(size_t)bmap[k]].res.new_id = ids[k];
+                    for (int gi : bg)
+                        if (gs[gi].query >= 0) {
+                            const apsp_batch_item &it = s->reqs[(size_t)gs[gi].query].item;
+                            apsp_graph *gr = s->graphs[gi];
+                            if (it.u < 0 || it.v < 0 || it.u >= gr->cap || it.v >= gr->cap) {
+                                s->reqs[(size_t)gs[gi].query].res.status = APSP_E_NODE;
+                                continue;
+                            }
+                            cudaMemcpyAsync(qbuf + gi, (T *)gr->D + (int64_t)it.u * gr->ld + it.v, sizeof(T),
+                                            cudaMemcpyDeviceToHost, s->b->stream);
+                            batch_q = true;
+                        }
+                    if (batch_q) cudaEventRecord(small_q_ev, s->b->stream);
                 } else {
-                    ok = cudaEventQuery(s.ev) == cudaSuccess;
+                    // a request the batch rejects: these graphs go one call per
+                    // update instead, so each request gets its own status
+                    for (int gi : bg) {
+                        gs[gi].in_batch = false;
+                        issue_calls(gi);
+                    }
+                    bg.clear();
+                    bst = APSP_OK;
                 }
-                if (!ok) continue;
-                const double t = clk.now();
-                for (int q : s.reqs) {
-                    res[q].done_s = t;
-                    if (s.small) res[q].status = bst;
-                    if (reqs[q].item.op == APSP_BATCH_QUERY && res[q].status == APSP_OK) res[q].dist = (double)qbuf[q];
-                    ++finished;
-                }
-                s.done = true;
-                --left;
             }
         }
-        if (!bgraphs.empty()) {
-            const apsp_status fst = batch_finish(b);
-            for (size_t k = 0; k < bmap.size(); ++k) {
-                if (fst != APSP_OK) res[bmap[k]].status = fst;
-                if (reqs[bmap[k]].item.op == APSP_BATCH_ADD) res[bmap[k]].new_id = bids[k];
-            }
+        for (int gi = 0; gi < G && budget_left != 0; ++gi) {
+            GraphState &g = gs[gi];
+            if (s->small[gi] || g.busy || g.pend.empty() || !fits(gi)) continue;
+            take(gi, budget_left);
+            used += s->bytes[gi];
+            issue_calls(gi);
+            round.push_back(gi);
         }
-        for (auto &s : segs)
-            if (s.ev) {
-                cudaEventSynchronize(s.ev);
-                cudaEventDestroy(s.ev);
-            }
-        ++wave;
+        if (!round.empty()) {
+            const double t = s->clk.now();
+            std::lock_guard<std::mutex> lock(s->mu);
+            for (int gi : round)
+                for (int64_t q : gs[gi].seg) {
+                    s->reqs[(size_t)q].res.admit_s = t;
+                    s->reqs[(size_t)q].res.wave = wave;
+                }
+            ++wave;
+            progress = true;
+        }
+        if (!progress) {
+            std::unique_lock<std::mutex> lock(s->mu);
+            bool anything_busy = batch_busy;
+            for (auto &g : gs) anything_busy = anything_busy || g.busy;
+            if (s->inbox.empty() && !s->stop)
+                s->cv_work.wait_for(lock, std::chrono::microseconds(anything_busy ? 20 : 2000));
+        }
     }
+    for (auto &g : gs) cudaEventDestroy(g.ev);
     cudaEventDestroy(small_q_ev);
-    cudaFreeHost(qbuf);
-    apsp_batch_destroy(b);
-    return APSP_OK;
 }
 
 }  // namespace
 
-extern "C" apsp_status apsp_serve(apsp_graph *const *graphs, int32_t n_graphs, const apsp_request *reqs,
-                                  int32_t count, const apsp_serve_config *cfg, apsp_request_result *results) {
-    if (!graphs || n_graphs <= 0 || count < 0 || (count > 0 && (!reqs || !results)) || !cfg) return APSP_E_ARG;
+extern "C" {
+
+apsp_status apsp_server_create(apsp_server **out, apsp_graph *const *graphs, int32_t n_graphs,
+                               const apsp_serve_config *cfg) {
+    if (!out || !graphs || n_graphs <= 0 || !cfg) return APSP_E_ARG;
+    *out = nullptr;
     const int dtype = graphs[0] ? graphs[0]->dtype : -1;
     for (int gi = 0; gi < n_graphs; ++gi) {
         if (!graphs[gi] || graphs[gi]->dtype != dtype) return APSP_E_ARG;
@@ -2001,11 +2058,123 @@ extern "C" apsp_status apsp_serve(apsp_graph *const *graphs, int32_t n_graphs, c
         for (int gj = 0; gj < gi; ++gj)
             if (graphs[gj] == graphs[gi]) return APSP_E_ARG;
     }
+    apsp_server *s = new (std::nothrow) apsp_server();
+    if (!s) return APSP_E_NOMEM;
+    s->graphs.assign(graphs, graphs + n_graphs);
+    s->cfg = *cfg;
+    s->dtype = dtype;
+    s->device = graphs[0]->device;
+    for (int gi = 0; gi < n_graphs; ++gi) {
+        apsp_graph *g = graphs[gi];
+        s->small.push_back(cfg->small_max_slots > 0 && g->cap <= cfg->small_max_slots && !g->undirected && g->DT &&
+                           g->cap <= APSP_BATCH_MAX_SLOTS);
+        s->bytes.push_back((double)g->ld * g->ld * g->esz * (g->undirected ? 2 : 3));
+    }
+    apsp_status st = apsp_batch_create(&s->b, nullptr);
+    if (st != APSP_OK) {
+        delete s;
+        return st;
+    }
+    if (cudaMallocHost(&s->qbuf, (size_t)n_graphs * 4) != cudaSuccess) {
+        apsp_batch_destroy(s->b);
+        delete s;
+        return APSP_E_NOMEM;
+    }
+    s->worker = dtype == APSP_F32 ? std::thread(server_loop<float>, s) : std::thread(server_loop<int32_t>, s);
+    *out = s;
+    return APSP_OK;
+}
+
+apsp_status apsp_server_submit(apsp_server *s, const apsp_batch_item *item, int64_t *ticket) {
+    if (!s || !item || !ticket) return APSP_E_ARG;
+    if (item->graph < 0 || item->graph >= (int)s->graphs.size() || item->op < 0 || item->op > APSP_BATCH_QUERY)
+        return APSP_E_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stop) return APSP_E_BUSY;
+    s->reqs.emplace_back();
+    apsp_server::Req &r = s->reqs.back();
+    r.item = *item;
+    r.res.new_id = -1;
+    r.res.wave = -1;
+    r.res.status = APSP_OK;
+    if (item->op == APSP_BATCH_ADD) {
+        const size_t n = (size_t)s->graphs[item->graph]->cap * 4;
+        if (item->in_w) r.iw.assign((const char *)item->in_w, (const char *)item->in_w + n);
+        if (item->out_w) r.ow.assign((const char *)item->out_w, (const char *)item->out_w + n);
+        r.item.in_w = item->in_w ? r.iw.data() : nullptr;
+        r.item.out_w = item->out_w ? r.ow.data() : nullptr;
+    }
+    *ticket = (int64_t)s->reqs.size() - 1;
+    s->inbox.push_back(*ticket);
+    s->cv_work.notify_one();
+    return APSP_OK;
+}
+
+apsp_status apsp_server_poll(apsp_server *s, int64_t ticket, apsp_request_result *res, int32_t *done) {
+    if (!s || !res || !done) return APSP_E_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (ticket < 0 || ticket >= (int64_t)s->reqs.size()) return APSP_E_ARG;
+    const apsp_server::Req &r = s->reqs[(size_t)ticket];
+    *done = r.done ? 1 : 0;
+    if (r.done) *res = r.res;
+    return APSP_OK;
+}
+
+apsp_status apsp_server_wait(apsp_server *s, int64_t ticket, double timeout_s, apsp_request_result *res) {
+    if (!s || !res) return APSP_E_ARG;
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (ticket < 0 || ticket >= (int64_t)s->reqs.size()) return APSP_E_ARG;
+    const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(std::max(0.0, timeout_s));
+    while (!s->reqs[(size_t)ticket].done)
+        if (s->cv_done.wait_until(lock, until) == std::cv_status::timeout && !s->reqs[(size_t)ticket].done)
+            return APSP_E_BUSY;
+    *res = s->reqs[(size_t)ticket].res;
+    return APSP_OK;
+}
+
+double apsp_server_clock(apsp_server *s) { return s ? s->clk.now() : -1.0; }
+
+apsp_status apsp_server_destroy(apsp_server *s) {
+    if (!s) return APSP_E_ARG;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    apsp_batch_destroy(s->b);
+    cudaFreeHost(s->qbuf);
+    delete s;
+    return APSP_OK;
+}
+
+apsp_status apsp_serve(apsp_graph *const *graphs, int32_t n_graphs, const apsp_request *reqs, int32_t count,
+                       const apsp_serve_config *cfg, apsp_request_result *results) {
+    if (!graphs || n_graphs <= 0 || count < 0 || (count > 0 && (!reqs || !results)) || !cfg) return APSP_E_ARG;
     for (int q = 0; q < count; ++q) {
         const apsp_request &r = reqs[q];
         if (r.item.graph < 0 || r.item.graph >= n_graphs || r.item.op < 0 || r.item.op > APSP_BATCH_QUERY) return APSP_E_ARG;
         if (!(r.arrival_s >= 0) || (q > 0 && r.arrival_s < reqs[q - 1].arrival_s)) return APSP_E_ARG;
     }
-    if (dtype == APSP_F32) return serve_impl<float>(graphs, n_graphs, reqs, count, *cfg, results);
-    return serve_impl<int32_t>(graphs, n_graphs, reqs, count, *cfg, results);
+    apsp_server *s = nullptr;
+    apsp_status st = apsp_server_create(&s, graphs, n_graphs, cfg);
+    if (st != APSP_OK) return st;
+    std::vector<int64_t> tickets((size_t)count, -1);
+    for (int q = 0; q < count; ++q) {
+        // submit at the arrival time (sleep through long gaps, then spin)
+        while (true) {
+            const double gap = reqs[q].arrival_s - s->clk.now();
+            if (gap <= 0) break;
+            if (gap > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(gap - 1e-4));
+        }
+        if ((st = apsp_server_submit(s, &reqs[q].item, &tickets[(size_t)q])) != APSP_OK) break;
+    }
+    for (int q = 0; q < count && st == APSP_OK; ++q) {
+        while (apsp_server_wait(s, tickets[(size_t)q], 3600.0, &results[q]) == APSP_E_BUSY) {
+        }
+    }
+    apsp_server_destroy(s);
+    return st;
 }
+
+}  // extern "C"

@@ -171,3 +171,86 @@ def test_serve_at_full_graph_sizes(lib):
     for gi, g in enumerate(graphs):
         _check_final(g, mir[gi], full=sizes[gi] <= 2048, seed=gi)
         g.close()
+
+
+def test_online_server_matches_oracle(lib):
+    # Requests submitted while the server runs (polled in between): every
+    # query equals the oracle at its place in its graph's order, every graph
+    # ends as the oracle says and as if its requests ran alone.
+    from paper_2412_15122_gb300 import Graph, Server
+    sizes = [60, 97, 300, 257]
+    caps = [80, 128, 320, 288]
+    Ws, reqs, mir, expect = _trace(sizes, caps, 200, 21)
+    graphs = [Graph(W, cap) for W, cap in zip(Ws, caps)]
+    srv = Server(graphs, small_max_slots=128)
+    tickets = []
+    for q, it in enumerate(reqs):
+        tickets.append(srv.submit(it))
+        if q % 17 == 0:
+            srv.poll(tickets[q // 2])
+    assert tickets == list(range(len(reqs)))
+    res = [srv.wait(t, 120.0) for t in tickets]
+    srv.close()
+    assert all(r["status"] == 0 for r in res)
+    assert all(r["done_s"] >= r["admit_s"] >= 0 for r in res)
+    for q, d in expect.items():
+        assert res[q]["dist"] == d, (q, reqs[q])
+    for gi, (W, cap) in enumerate(zip(Ws, caps)):
+        _check_final(graphs[gi], mir[gi])
+        mine = [(q, it) for q, it in enumerate(reqs) if it[0] == gi]
+        D_alone, dists = _replay_alone(lib, W, cap, mine)
+        np.testing.assert_array_equal(graphs[gi].D(), D_alone)
+    for g in graphs:
+        g.close()
+
+
+def test_server_serves_small_graphs_while_a_large_one_works(lib):
+    # A removal that goes cold on an n = 4096 graph (a full Floyd-Warshall)
+    # and requests for a small graph right behind it: the small graph's
+    # requests go to the GPU before the large graph's work is done.
+    from paper_2412_15122_gb300 import Graph, Server
+    Ws, reqs, mir, expect = _trace([4096, 100], [4128, 128], 1, 5)
+    big, small = Graph(Ws[0], 4128), Graph(Ws[1], 128)
+    big.set_dispatch("cold")
+    srv = Server([big, small], small_max_slots=128)
+    t_big = srv.submit((0, "remove", 7))
+    m = mir[1]
+    ts = []
+    for k in range(20):
+        u, v = 3 + k, 40 + k
+        w = int(m.W[u, v]) // 2
+        m.W[u, v] = w
+        ts.append(srv.submit((1, "edge", u, v, float(w))))
+    tq = srv.submit((1, "query", 3, 70))
+    rq = srv.wait(tq, 120.0)
+    rb = srv.wait(t_big, 120.0)
+    rs = [srv.wait(t, 120.0) for t in ts]
+    srv.close()
+    assert rb["status"] == 0 and rq["status"] == 0 and all(r["status"] == 0 for r in rs)
+    assert rq["dist"] == int(m.dist_row(3)[70])
+    assert min(r["admit_s"] for r in rs) < rb["done_s"], "the small graph waited for the large one"
+    mir[0].alive[7] = False
+    mir[0].W[7, :] = mir[0].W[:, 7] = synth.INF_I32
+    _check_final(big, mir[0], full=False)
+    _check_final(small, m)
+    big.close()
+    small.close()
+
+
+def test_server_invalid_request_gets_its_own_status(lib):
+    from paper_2412_15122_gb300 import Graph, Server
+    Ws, reqs, mir, expect = _trace([50, 60], [64, 64], 1, 8)
+    graphs = [Graph(W, 64) for W in Ws]
+    srv = Server(graphs, small_max_slots=64)
+    a = srv.submit((0, "remove", 5))
+    b = srv.submit((0, "remove", 5))          # already removed
+    c = srv.submit((1, "edge", 1, 2, 3.0))
+    d = srv.submit((0, "query", 1, 2))
+    ra, rb, rc, rd = (srv.wait(t, 60.0) for t in (a, b, c, d))
+    srv.close()
+    assert ra["status"] == 0 and rb["status"] == 2 and rc["status"] == 0 and rd["status"] == 0
+    mir[0].alive[5] = False
+    mir[0].W[5, :] = mir[0].W[:, 5] = synth.INF_I32
+    assert rd["dist"] == int(mir[0].dist_row(1)[2])
+    for g in graphs:
+        g.close()

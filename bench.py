@@ -880,7 +880,7 @@ def run_serve_study(args):
         graphs.append(Graph(W, cap))
         states.append(_ServeState(W, cap))
     gen_s = time.perf_counter() - t_gen
-    small = 2048 + 64
+    small = args.serve_small_slots
     history = [[] for _ in graphs]
     hs = [g.h for g in graphs]
 
@@ -898,7 +898,7 @@ def run_serve_study(args):
     stream = 10
     # warm-up: lets the batched kernel's width autotuner settle on this mix
     warm_rounds = 0
-    while A.apsp_batch_tuned_width(A.APSP_I32, small) == 0 and warm_rounds < 6:
+    while small > 0 and A.apsp_batch_tuned_width(A.APSP_I32, small) == 0 and warm_rounds < 6:
         reqs = _serve_requests(states, N, 5, stream)
         stream += 10
         run(reqs, np.zeros(len(reqs)))
@@ -939,8 +939,9 @@ def run_serve_study(args):
     print(json.dumps({
         "study": "serving", "graphs": len(sizes), "sizes": [1024, 2048, 4096, 8192], "per_size": args.serve_per_size,
         "mix": "70% edge updates (half halve, half x4), 20% node add/remove (half each), 10% queries; uniform graph and targets",
-        "batched_graphs": f"capacity <= {small} (n = 1024, 2048) in the persistent batched kernel, larger via one call per update",
-        "warm_up_rounds": warm_rounds, "batch_width": A.apsp_batch_tuned_width(A.APSP_I32, small),
+        "batched_graphs": f"capacity <= {small} in the persistent batched kernel (one CTA per graph), larger via one call "
+                          "per update",
+        "warm_up_rounds": warm_rounds, "batch_width": A.apsp_batch_tuned_width(A.APSP_I32, small) if small > 0 else None,
         "capacity_requests_per_s": C, "calibration": cal, "poisson_sweep_fraction_of_capacity": sweep,
         "tight_budget": {"budget_bytes": budget, "at_fraction": 0.5, **tight},
         "alone_vs_mix_identical_n1024": same, "setup_seconds": gen_s}))
@@ -1108,6 +1109,9 @@ def main():
     ap.add_argument("--study-graphs", type=int, default=512)
     ap.add_argument("--serve-per-size", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-small-slots", type=int, default=0,
+                    help="serving: graphs of capacity <= this go through the batched kernel (one CTA per graph); "
+                         "0: every graph one call per update on its own stream")
     ap.add_argument("--study-queries", type=int, default=4096)
     ap.add_argument("--study-reps", type=int, default=20)
     ap.add_argument("--study", choices=["dispatch", "batch", "serve", "paths", "ratios", "minimax"],

@@ -239,6 +239,20 @@ apsp_status apsp_query_path(apsp_graph *g, int32_t u, int32_t v, int32_t *path, 
 apsp_status apsp_query_all_paths(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, int64_t nodes_cap,
                                  int64_t *offsets, int32_t paths_cap, int32_t *n_paths, int64_t *n_nodes);
 
+/* Next hops (the hot-path plan's optional next-hop output), derived from the
+ * resident D and W when asked for rather than carried through every update:
+ * for each of the `count` live rows i = rows[r] (host int32),
+ * out[r * ld_out + j] (host, ld_out >= n_slots) receives for j < n_slots the
+ * lowest live slot t != i with W[i][t] + D[t][j] == D[i][j] (fp32: within the
+ * 2^-8 tightness slack) -- the first hop of a shortest walk i -> t ~> j --,
+ * i for j == i and -1 where j is dead or unreachable.  With positive weights
+ * following next hops from i reaches j along a shortest path; zero-weight
+ * cycles can make them loop (use apsp_query_path for paths then).  Cost per
+ * row: the row's tight out-edges times n_slots reads of D.  APSP_E_NODE for a
+ * dead or out-of-range row; APSP_E_UNSUPPORTED for APSP_MINIMAX graphs.
+ * Waits. */
+apsp_status apsp_next_hops(apsp_graph *g, const int32_t *rows, int32_t count, int32_t *out, int64_t ld_out);
+
 /* Copy the n_slots x n_slots top-left block of D (or W) to dst with leading
  * dimension ld_dst (elements); dst is device memory if dst_on_device, else
  * host.  Dead slots read as missing.  Waits. */

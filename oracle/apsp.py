@@ -434,7 +434,7 @@ def itertools_paths_min(W: np.ndarray) -> np.ndarray:
 #: Relative slack of the float candidate test (the same reading as the float
 #: tightness test): extra candidates only enlarge the small graph; a missed
 #: one could drop every shortest path from it.
-FLOAT_SLACK = 2.0 ** -16
+FLOAT_SLACK = 2.0 ** -8
 
 
 def _on_some_shortest_path(M: np.ndarray, i: int, j: int, t: int) -> bool:
@@ -648,6 +648,39 @@ def need_update_list_alg11(M: np.ndarray, W: np.ndarray, alive: np.ndarray, k: i
                 row.append(j)
         lst[i] = row
     return lst
+
+
+# ---------------------------------------------------------------------------
+# Next hops (the optional next-hop output of the hot-path plan)
+# ---------------------------------------------------------------------------
+
+def next_hop_row(M: np.ndarray, W: np.ndarray, alive: np.ndarray, i: int) -> np.ndarray:
+    """Row i of the next-hop matrix: for every live j != i with SPD(i, j)
+    finite, the lowest live t != i such that the edge i -> t followed by a
+    shortest t -> j path is a shortest i -> j walk, w(i, t) + SPD(t, j) ==
+    SPD(i, j) (fp: within the tightness slack); i for j == i; -1 where j is
+    dead or unreachable.  With positive weights this is the lowest first hop
+    of a shortest i -> j path."""
+    alive = np.asarray(alive, dtype=bool)
+    E = exact(W, alive)
+    miss = missing(M)
+    n = M.shape[0]
+    out = np.full(n, -1, dtype=np.int64)
+    if not alive[i]:
+        return out
+    out[i] = i
+    for j in np.flatnonzero(alive):
+        if j == i or M[i, j] == miss:
+            continue
+        for t in np.flatnonzero(alive):
+            if t == i or E[i, t] == miss or M[t, j] == miss:
+                continue
+            via = E[i, t] + M[t, j]
+            ok = via <= M[i, j] * (1.0 + FLOAT_SLACK) if is_float(M) else via == M[i, j]
+            if ok:
+                out[j] = t
+                break
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -128,6 +128,7 @@ def _load():
         "apsp_info_get": [P, ctypes.POINTER(apsp_info)],
         "apsp_last_stats": [P, ctypes.POINTER(apsp_stats)],
         "apsp_copy_last_list": [P, P, I64, ctypes.POINTER(I64)],
+        "apsp_next_hops": [P, P, I32, P, I64],
         "apsp_sync": [P],
         "apsp_set_dispatch": [P, I32, ctypes.c_double],
         "apsp_set_exact_list": [P, I32],
@@ -366,6 +367,15 @@ def apsp_copy_last_list(g: int) -> np.ndarray:
     out = np.empty((max(cnt.value, 1), 2), dtype=np.int32)
     _check(_load().apsp_copy_last_list(g, out.ctypes.data, cnt.value, ctypes.byref(cnt)), "apsp_copy_last_list")
     return out[: cnt.value]
+
+
+def apsp_next_hops(g: int, rows, n_slots: int) -> np.ndarray:
+    """(len(rows), n_slots) int32: next hops of the given live rows (-1: none)."""
+    rows = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1)
+    out = np.full((max(len(rows), 1), max(n_slots, 1)), -1, dtype=np.int32)
+    _check(_load().apsp_next_hops(g, rows.ctypes.data, len(rows), out.ctypes.data, max(n_slots, 1)),
+           "apsp_next_hops")
+    return out[: len(rows), :n_slots]
 
 
 def apsp_sync(g: int):
@@ -768,6 +778,9 @@ class Graph:
 
     def stats(self) -> dict:
         return apsp_last_stats(self.h)
+
+    def next_hops(self, rows) -> np.ndarray:
+        return apsp_next_hops(self.h, rows, self.info()["n_slots"])
 
     def last_list(self) -> np.ndarray:
         return apsp_copy_last_list(self.h)

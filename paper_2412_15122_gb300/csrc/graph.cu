@@ -70,6 +70,9 @@ struct apsp_graph {
     // path queries (Section 4): per-call buffers, grown on demand
     void *pq_uv = nullptr, *pq_out = nullptr, *pq_wide = nullptr;
     int64_t pq_uv_bytes = 0, pq_out_bytes = 0, pq_wide_bytes = 0;
+    // next hops: requested rows and their output, grown on demand
+    void *nh_rows = nullptr, *nh_out = nullptr;
+    int64_t nh_rows_bytes = 0, nh_out_bytes = 0;
     float *model = nullptr;
     int64_t pair_cap = 0;
     int32_t item_cap = 0;
@@ -784,6 +787,32 @@ std::vector<int32_t> pq_walk(const int32_t *pred, int K, int from, int to) {
     return w;
 }
 
+// Next hops of the requested rows, in chunks that bound the device buffer.
+template <typename T>
+apsp_status next_hops_impl(apsp_graph *g, const int32_t *rows, int32_t count, int32_t *out, int64_t ld_out) {
+    settle_fetch<T>(g);
+    const int64_t S = g->hwm;
+    const Dev<T> d = dev_of<T>(g);
+    const int64_t P = std::max<int64_t>(d.span, 1);   // device pitch: the kernel writes span columns a row
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(count, ((int64_t)1 << 26) / P));
+    if (!ensure_buf(g, &g->nh_rows, &g->nh_rows_bytes, chunk * 4) ||
+        !ensure_buf(g, &g->nh_out, &g->nh_out_bytes, chunk * P * 4))
+        return APSP_E_NOMEM;
+    for (int64_t r0 = 0; r0 < count; r0 += chunk) {
+        const int nr = (int)std::min<int64_t>(chunk, count - r0);
+        cudaError_t e = cudaMemcpyAsync(g->nh_rows, rows + r0, (size_t)nr * 4, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess)
+            e = apsp::run_next_hop<T>(g->lc, d, (const int32_t *)g->nh_rows, nr, (int32_t *)g->nh_out, P);
+        if (e == cudaSuccess && S > 0)
+            e = cudaMemcpy2DAsync(out + r0 * ld_out, (size_t)ld_out * 4, g->nh_out, (size_t)P * 4, (size_t)S * 4, nr,
+                                  cudaMemcpyDeviceToHost, g->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        apsp_status st = sync_ctl(g, nullptr);
+        if (st != APSP_OK) return st;
+    }
+    return APSP_OK;
+}
+
 template <typename T>
 apsp_status all_paths_impl(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, int64_t nodes_cap,
                            int64_t *offsets, int32_t paths_cap, int32_t *n_paths, int64_t *n_nodes) {
@@ -1026,6 +1055,16 @@ apsp_status apsp_query_all_paths(apsp_graph *g, int32_t u, int32_t v, int32_t *n
     if (g->minimax) return APSP_E_UNSUPPORTED;
     return g->dtype == APSP_F32 ? all_paths_impl<float>(g, u, v, nodes, nodes_cap, offsets, paths_cap, n_paths, n_nodes)
                                 : all_paths_impl<int32_t>(g, u, v, nodes, nodes_cap, offsets, paths_cap, n_paths, n_nodes);
+}
+
+apsp_status apsp_next_hops(apsp_graph *g, const int32_t *rows, int32_t count, int32_t *out, int64_t ld_out) {
+    if (!g || count < 0 || (count > 0 && (!rows || !out)) || ld_out < g->hwm) return APSP_E_ARG;
+    if (g->minimax) return APSP_E_UNSUPPORTED;
+    for (int32_t r = 0; r < count; ++r)
+        if (rows[r] < 0 || rows[r] >= g->cap || !g->alive_h[rows[r]]) return APSP_E_NODE;
+    if (count == 0) return APSP_OK;
+    return g->dtype == APSP_F32 ? next_hops_impl<float>(g, rows, count, out, ld_out)
+                                : next_hops_impl<int32_t>(g, rows, count, out, ld_out);
 }
 
 static apsp_status copy_mat(apsp_graph *g, const void *src, void *dst, int64_t ld_dst, int32_t on_dev) {

@@ -230,6 +230,7 @@ template <typename T> cudaError_t setup_shapes(LaunchCtx &c, int64_t ld, int und
     c.detunit_grid = 4 * c.num_sms;
     c.detalloc_grid = (int)((ld + 255) / 256);   // a lane per row: 256 rows a CTA
     if ((e = allow_max_smem(k_path_warp<T>)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_next_hop<T>)) != cudaSuccess) return e;
     if ((e = allow_max_smem(k_det_alg12<T, false>)) != cudaSuccess) return e;
     if ((e = allow_max_smem(k_det_alg12<T, true>)) != cudaSuccess) return e;
     int pw_sm = 0;
@@ -354,6 +355,15 @@ cudaError_t run_mm_pass(const LaunchCtx &c, const Dev<T> &d, const uint32_t *mas
     return launch(c, "mm_pass", [&] { k_mm_pass<T><<<g, 256, 0, c.stream>>>(d, mask, words, pass); });
 }
 
+template <typename T>
+cudaError_t run_next_hop(const LaunchCtx &c, const Dev<T> &d, const int32_t *rows, int nrows, int32_t *out,
+                         int64_t ld_out) {
+    const int g = std::max(1, std::min(nrows, 4 * c.num_sms));
+    return launch(c, "next_hop", [&] {
+        k_next_hop<T><<<g, 256, (size_t)d.span * sizeof(int32_t), c.stream>>>(d, rows, nrows, out, ld_out);
+    });
+}
+
 #define APSP_INSTANTIATE(T)                                                                                   \
     template cudaError_t run_fill<T>(const LaunchCtx &, T *, T, int64_t);                                     \
     template cudaError_t run_sanitize<T>(const LaunchCtx &, T *, int64_t, int, int, Ctl *);                   \
@@ -372,6 +382,7 @@ cudaError_t run_mm_pass(const LaunchCtx &c, const Dev<T> &d, const uint32_t *mas
     template cudaError_t run_mm_insert<T>(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int); \
     template cudaError_t run_mm_decrease<T>(const LaunchCtx &, const Dev<T> &, int, int, T);                  \
     template cudaError_t run_mm_detect<T>(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T); \
-    template cudaError_t run_mm_pass<T>(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);
+    template cudaError_t run_mm_pass<T>(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);          \
+    template cudaError_t run_next_hop<T>(const LaunchCtx &, const Dev<T> &, const int32_t *, int, int32_t *, int64_t);
 
 }  // namespace apsp

@@ -10,6 +10,7 @@
 #include "paths.cuh"
 #include "repair_p1.cuh"
 #include "minimax.cuh"
+#include "next_hop.cuh"
 
 namespace apsp {
 
@@ -49,5 +50,6 @@ template <typename T> cudaError_t run_mm_decrease(const LaunchCtx &, const Dev<T
 template <typename T>
 cudaError_t run_mm_detect(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T);
 template <typename T> cudaError_t run_mm_pass(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);
+template <typename T> cudaError_t run_next_hop(const LaunchCtx &, const Dev<T> &, const int32_t *, int, int32_t *, int64_t);
 
 }  // namespace apsp

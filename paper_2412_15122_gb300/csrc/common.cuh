@@ -252,76 +252,4 @@ __device__ bool grid_barrier(Ctl *ctl, Leader leader) {
 
 struct NoLeader { __device__ void operator()() const {} };
 
-// ---------------------------------------------------------------------------
-// TMA bulk copies (cp.async.bulk, global -> shared) completing on an mbarrier.
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Orders earlier generic-proxy accesses of shared memory before later
-// async-proxy (TMA) writes to it.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Copies `bytes` (a multiple of 16, both addresses 16-byte aligned) from global
-// to shared memory; completion is signalled on `bar` as transaction bytes.
-__device__ __forceinline__ void tma_load_1d(void *smem_dst, const void *gsrc, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(smem_dst)),
-        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for phase `parity` of `bar` with a bound: after BARRIER_TIMEOUT_NS it
-// records ERR_TIMEOUT and returns false (the caller then stops using the
-// buffer and leaves the kernel after its copies in flight have landed).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, Ctl *ctl) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
-            atomicOr(&ctl->err, ERR_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
-
-// Issues the copy of one row of `bytes` into `dst` in pieces of at most 32 KiB
-// (one elected thread).
-__device__ __forceinline__ void tma_load_row(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    mbar_arrive_expect_tx(bar, bytes);
-    for (uint32_t off = 0; off < bytes; off += 32768u) {
-        const uint32_t n = bytes - off < 32768u ? bytes - off : 32768u;
-        tma_load_1d((char *)dst + off, (const char *)src + off, n, bar);
-    }
-}
-
 }  // namespace apsp

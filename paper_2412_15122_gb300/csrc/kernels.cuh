@@ -365,7 +365,7 @@ __device__ __forceinline__ void insert_finish_entry(const Dev<T> &d, int p, int 
 // missing) and row p is never read by it, so the same launch writes them
 // (insert_finish_entry) while the rows are swept.
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p) {
+__global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p, int ranges, int rows_per) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -382,7 +382,14 @@ __global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p) {
     const V4 *so4 = reinterpret_cast<const V4 *>(so);
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < span; row += nwarps) {
+    // Row order: k_insert_reduce read every one of its `ranges` row ranges in
+    // ascending order at once, so its last rows -- the ends of all ranges --
+    // are what L2 still holds.  Take those first: k walks the ranges
+    // interleaved, from each range's end backwards.
+    const int cover = ranges * rows_per;
+    for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < cover; k += nwarps) {
+        const int row = (k % ranges) * rows_per + (rows_per - 1 - k / ranges);
+        if (row >= span) continue;
         const T vi = M::unkey(d.vin_k[row]);
         if (!M::finite(vi)) continue;
         T *Dr = d.D + (int64_t)row * d.ld;

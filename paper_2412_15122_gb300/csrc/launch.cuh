@@ -64,7 +64,8 @@ cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, con
     if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d, rows_per); })) != cudaSuccess) return e;
     int gr = c.relax_grid;
     size_t sm = (size_t)d.span * sizeof(int32_t);
-    return launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p); });
+    const int nranges = cdiv(d.span, rows_per);
+    return launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p, nranges, rows_per); });
 }
 
 template <typename T> cudaError_t run_decrease(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w) {

@@ -1,7 +1,7 @@
 // Batched execution: one persistent kernel applies a batch of updates to many
-// independent graphs.  CTAs take graphs from a device queue; a CTA applies its
-// graph's updates in order (each graph's sequence is causal, different graphs
-// are independent), with the same steps as the single-graph path:
+// independent graphs.  Each graph's updates are applied in order (a graph's
+// sequence is causal, different graphs are independent), with the same steps
+// as the single-graph path:
 //   add       Corollary 1 / Corollary 2 as row reductions over D and D^T,
 //             then the Theorem 3 sweep, then row / column p;
 //   decrease  D = min(D, D[:,u] + w + D[v,:]) on rows with D[i][u] + w < D[i][v];
@@ -12,9 +12,17 @@
 //                 D[i][j] = min over x of D[i][x] + D[x][j],
 //             in full passes until a pass lowers nothing (the fixed point of
 //             D = min(D, D (x) D) over the listed pairs is exact).
-// Graphs are directed (D and D^T kept, row-major, ld = the graph's leading
-// dimension); the host has already chosen new nodes' slots, read old edge
-// weights from its mirror and masked new-node weight vectors.
+// Who works on a graph: large graphs (the first n_team of `order`) go to
+// teams of team_size co-resident CTAs, team t taking large graphs t,
+// t + n_teams, ...; the team splits each step's rows over all its warps and
+// meets at a bounded team barrier between steps, with its scratch vectors in
+// global memory.  Every other graph goes to a single CTA (scratch in shared
+// memory, __syncthreads between steps) from a device queue, which the teams'
+// CTAs also join once their large graphs are done.  The grid is never larger
+// than the CTAs that fit on the device at once, so every team's CTAs run
+// together.  Graphs are directed (D and D^T kept, row-major, ld = the graph's
+// leading dimension); the host has already chosen new nodes' slots, read old
+// edge weights from its mirror and masked new-node weight vectors.
 #pragma once
 
 #include "kernels.cuh"
@@ -41,16 +49,83 @@ struct BatchOp {
     int32_t w_bits, w_old_bits;   // edges: new and old weight (bit patterns of T)
 };
 
+// Per team, in global memory: 4 vectors of max_span elements, the listed rows
+// (max_span), then the team's counters.
+constexpr int TEAM_INTS = 8;   // nrows, changed, barrier count, barrier generation, spare
+constexpr int TEAM_MAX = 8;    // largest team
+
 struct BatchHeader {
     BatchGraph *graphs;
     const BatchOp *ops;
     const void *vecs;
     int32_t n_graphs;
-    int32_t max_span;         // largest span of any update (sizes the shared arrays)
-    int32_t queue;            // next graph to take
-    int32_t pad_;
+    int32_t max_span;         // largest span of any update (sizes the scratch arrays)
+    int32_t queue;            // next single-CTA graph to take
+    int32_t n_team;           // order[0, n_team) go to teams
+    int32_t team_size;        // CTAs per team (1: no teams)
+    int32_t n_teams;
+    const int32_t *order;     // graph indices: large ones first
+    void *team_scratch;       // n_teams * team_stride bytes
+    int64_t team_stride;
     volatile int32_t *done;   // optional (mapped host memory): 1 + status per graph when it is finished
 };
+
+// Who works on the current graph.  SOLO: this CTA alone.  Team: CTA `rank`
+// of `size`; warps and threads are numbered across the team.
+struct Team {
+    int rank, size;
+    int32_t *ints;            // team mode: nrows, changed, barrier count, generation
+    __device__ int gw() const { return rank * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); }
+    __device__ int nw() const { return size * (int)(blockDim.x >> 5); }
+    __device__ int gt() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ int nt() const { return size * (int)blockDim.x; }
+    __device__ bool leader() const { return rank == 0 && threadIdx.x == 0; }
+};
+
+// Scratch shared by the team: shared memory for one CTA (plain loads), global
+// memory for a team (loads bypass L1, where another CTA's writes are not seen).
+template <bool TEAM, typename V> __device__ __forceinline__ V tld(const V *p) {
+    if constexpr (TEAM) return __ldcg(p);
+    else return *p;
+}
+
+// Barrier between the steps of an update.  A team's wait is bounded: after
+// BARRIER_TIMEOUT_NS the CTA records ERR_TIMEOUT in *err and returns false.
+template <bool TEAM> __device__ __forceinline__ bool team_sync(const Team &tm, int32_t *err) {
+    if constexpr (!TEAM) {
+        __syncthreads();
+        return true;
+    } else {
+        __shared__ int ok_s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            volatile int32_t *gen = tm.ints + 3;
+            const int32_t g0 = *gen;
+            __threadfence();
+            int ok = 1;
+            if (atomicAdd(tm.ints + 2, 1) == tm.size - 1) {
+                tm.ints[2] = 0;
+                __threadfence();
+                atomicAdd(tm.ints + 3, 1);
+            } else {
+                const unsigned long long t0 = globaltimer_ns();
+                unsigned spins = 0;
+                while (*gen == g0) {
+                    __nanosleep(64);
+                    if ((++spins & 1023u) == 0 && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS) {
+                        atomicOr(err, (int32_t)ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+            ok_s = ok;
+        }
+        __syncthreads();
+        return ok_s != 0;
+    }
+}
 
 template <typename T> __device__ __forceinline__ T bits_as(int32_t b) {
     if constexpr (std::is_same<T, float>::value) return __int_as_float(b);
@@ -116,18 +191,18 @@ template <typename T> __device__ __forceinline__ T b_dot_min(const BG<T> &g, int
 
 // Re-relaxes the listed pairs (bitmask rows of `words` words; the rows
 // holding any are rows[0, nrows)) in full passes until a pass lowers
-// nothing; returns false when the pass cap is reached.
-template <typename T>
-__device__ bool b_relax(const BG<T> &g, const uint32_t *mask, int words, int span, const int32_t *rows, int nrows) {
+// nothing; returns false when the pass cap is reached or a team wait gave up.
+template <typename T, bool TEAM>
+__device__ bool b_relax(const BG<T> &g, const Team &tm, int32_t *err, const uint32_t *mask, int words, int span,
+                        const int32_t *rows, int nrows, int32_t *changed_p) {
     using M = MinPlus<T>;
-    __shared__ int changed_s;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = tm.gw(), nw = tm.nw();
     for (int pass = 0; pass < MAX_PASSES; ++pass) {
-        if (threadIdx.x == 0) changed_s = 0;
-        __syncthreads();
+        if (tm.leader()) *changed_p = 0;
+        if (!team_sync<TEAM>(tm, err)) return false;
         bool changed = false;
         for (int r = wid; r < nrows; r += nw) {
-            const int i = rows[r];
+            const int i = tld<TEAM>(rows + r);
             for (int w0 = 0; w0 < words; w0 += 32) {
                 const uint32_t my = w0 + lane < words ? __ldcg(mask + (int64_t)i * words + w0 + lane) : 0u;
                 for (unsigned nz = __ballot_sync(0xffffffffu, my != 0u); nz; nz &= nz - 1) {
@@ -145,41 +220,48 @@ __device__ bool b_relax(const BG<T> &g, const uint32_t *mask, int words, int spa
                 }
             }
         }
-        if (changed) changed_s = 1;
-        __syncthreads();
-        const int any = changed_s;
-        __syncthreads();
+        if (changed) atomicExch(changed_p, 1);
+        if (!team_sync<TEAM>(tm, err)) return false;
+        const int any = tld<TEAM>(changed_p);
+        if (!team_sync<TEAM>(tm, err)) return false;
         if (!any) return true;
     }
     return false;
 }
 
 // Clears rows [0, span) of the bitmask and the listed-row count.
-__device__ __forceinline__ void b_clear_mask(uint32_t *mask, int words, int span, int *nrows_s) {
-    for (int64_t t = threadIdx.x; t < (int64_t)span * words; t += blockDim.x) mask[t] = 0u;
-    if (threadIdx.x == 0) *nrows_s = 0;
-    __syncthreads();
+template <bool TEAM>
+__device__ __forceinline__ bool b_clear_mask(const Team &tm, int32_t *err, uint32_t *mask, int words, int span,
+                                             int32_t *nrows_p) {
+    for (int64_t t = tm.gt(); t < (int64_t)span * words; t += tm.nt()) mask[t] = 0u;
+    if (tm.leader()) *nrows_p = 0;
+    return team_sync<TEAM>(tm, err);
 }
 
 // Node insertion at slot p with masked weights wi (t -> p) and wo (p -> t).
-template <typename T>
-__device__ __noinline__ void b_add(const BG<T> &g, int p, int span, const T *wi, const T *wo, T *s_in, T *s_out, T *s_wi,
-                      T *s_wo) {
+template <typename T, bool TEAM>
+__device__ __noinline__ bool b_add(const BG<T> &g, const Team &tm, int32_t *err, int p, int span, const T *wi,
+                                   const T *wo, T *s_in, T *s_out, T *s_wi, T *s_wo) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = tm.gw(), nw = tm.nw();
     const int nv4 = span / 4;
-    for (int t = threadIdx.x; t < span; t += blockDim.x) {
-        s_wi[t] = wi[t];
-        s_wo[t] = wo[t];
+    if constexpr (TEAM) {   // the host-written vectors are read where they are
+        s_wi = const_cast<T *>(wi);
+        s_wo = const_cast<T *>(wo);
+    } else {
+        for (int t = threadIdx.x; t < span; t += blockDim.x) {
+            s_wi[t] = wi[t];
+            s_wo[t] = wo[t];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const V4 *wi4 = reinterpret_cast<const V4 *>(s_wi), *wo4 = reinterpret_cast<const V4 *>(s_wo);
     // Corollary 2: D[i][p] = min_t D[i][t] + w(t -> p); Corollary 1:
     // D[p][j] = min_t w(p -> t) + D[t][j], a row reduction over D^T row j
     for (int r = wid; r < span; r += nw) {
         T a = M::inf(), b = M::inf();
-        if (g.alive[r] && r != p) {
+        if (__ldcg(g.alive + r) && r != p) {
             b_row(reinterpret_cast<const V4 *>(g.D + (int64_t)r * g.ld), nv4, [&](int c4, const V4 &v) {
                 const V4 w = wi4[c4];
                 a = M::mn(a, M::mn(M::mn(M::add(v.x, w.x), M::add(v.y, w.y)), M::mn(M::add(v.z, w.z), M::add(v.w, w.w))));
@@ -193,46 +275,43 @@ __device__ __noinline__ void b_add(const BG<T> &g, int p, int span, const T *wi,
         b = warp_min(b);
         if (lane == 0) {
             s_in[r] = a;
-            s_out[r] = b;
+            s_out[r] = r == p ? M::inf() : b;   // s_out[p] stays missing: those entries never improve
         }
     }
-    __syncthreads();
+    if (!team_sync<TEAM>(tm, err)) return false;
     // Theorem 3: D[i][j] = min(D[i][j], D[i][p] + D[p][j]) (s_out[p] and the
     // dead columns are missing, so those entries never improve)
-    if (threadIdx.x == 0) s_out[p] = M::inf();
-    __syncthreads();
     for (int i = wid; i < span; i += nw) {
-        const T vi = s_in[i];
+        const T vi = tld<TEAM>(s_in + i);
         if (i == p || !M::finite(vi)) continue;
         T *Di = g.D + (int64_t)i * g.ld;
         b_row(reinterpret_cast<const V4 *>(Di), nv4, [&](int c4, const V4 &v) {
             const T dv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const T o = s_out[4 * c4 + e];
+                const T o = tld<TEAM>(s_out + 4 * c4 + e);
                 if (M::finite(o) && vi + o < dv[e]) g.set(i, 4 * c4 + e, vi + o);
             }
         });
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < span; t += blockDim.x) {
-        const T out_t = t == p ? (T)0 : s_out[t];
-        const T in_t = t == p ? (T)0 : s_in[t];
+    if (!team_sync<TEAM>(tm, err)) return false;
+    for (int t = tm.gt(); t < span; t += tm.nt()) {
+        const T out_t = t == p ? (T)0 : tld<TEAM>(s_out + t);
+        const T in_t = t == p ? (T)0 : tld<TEAM>(s_in + t);
         g.set(p, t, out_t);
         g.set(t, p, in_t);
         g.w(p, t) = t == p ? (T)0 : s_wo[t];
         g.w(t, p) = t == p ? (T)0 : s_wi[t];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) g.alive[p] = 1;
-    __syncthreads();
+    if (tm.leader()) g.alive[p] = 1;
+    return team_sync<TEAM>(tm, err);
 }
 
 // Marks the entries j != i of row i with s + y[j] tight against D[i][j] in
 // the row's bitmask words (bit j % 32 of word j / 32); returns whether any.
 // Lane l holds 4 consecutive entries of each 128-entry block, so the bits of
 // a 32-entry word come from 8 lanes and are combined with shuffles.
-template <typename T>
+template <typename T, bool TEAM>
 __device__ __forceinline__ bool b_detect_row(const BG<T> &g, int i, T s, const T *sy, int span, uint32_t *mrow) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
@@ -244,7 +323,7 @@ __device__ __forceinline__ bool b_detect_row(const BG<T> &g, int i, T s, const T
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int j = 4 * c4 + e;
-            if (j != i && M::slack_tight(M::slack(s + sy[j], dv[e]))) m |= 1u << e;
+            if (j != i && M::slack_tight(M::slack(s + tld<TEAM>(sy + j), dv[e]))) m |= 1u << e;
         }
         // entries 4 c4 .. 4 c4 + 3 sit at bits 4 (c4 % 8) .. of word c4 / 8;
         // the row length is a multiple of 32 entries, so a word's 8 lanes
@@ -262,17 +341,19 @@ __device__ __forceinline__ bool b_detect_row(const BG<T> &g, int i, T s, const T
 }
 
 // Edge decrease (u, v) -> w.
-template <typename T> __device__ __noinline__ void b_decrease(const BG<T> &g, int u, int v, T w, int span, T *sx, T *sy) {
+template <typename T, bool TEAM>
+__device__ __noinline__ bool b_decrease(const BG<T> &g, const Team &tm, int32_t *err, int u, int v, T w, int span, T *sx,
+                                        T *sy) {
     using M = MinPlus<T>;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    const int wid = tm.gw(), nw = tm.nw();
+    for (int t = tm.gt(); t < span; t += tm.nt()) {
         sx[t] = __ldcg(&g.dt(u, t));   // D[t][u]
         sy[t] = __ldcg(&g.d(v, t));    // D[v][t]
     }
-    __syncthreads();
-    if (threadIdx.x == 0) g.w(u, v) = w;
+    if (!team_sync<TEAM>(tm, err)) return false;
+    if (tm.leader()) g.w(u, v) = w;
     for (int i = wid; i < span; i += nw) {
-        const T xi = sx[i];
+        const T xi = tld<TEAM>(sx + i);
         if (!M::finite(xi) || !(M::add(xi, w) < __ldcg(&g.dt(v, i)))) continue;   // row filter
         const T s = xi + w;
         b_row(reinterpret_cast<const typename M::V4 *>(g.D + (int64_t)i * g.ld), span / 4,
@@ -280,147 +361,175 @@ template <typename T> __device__ __noinline__ void b_decrease(const BG<T> &g, in
                   const T dv[4] = {dv4.x, dv4.y, dv4.z, dv4.w};
 #pragma unroll
                   for (int e = 0; e < 4; ++e) {
-                      const T y = sy[4 * c4 + e];
+                      const T y = tld<TEAM>(sy + 4 * c4 + e);
                       if (M::finite(y) && s + y < dv[e]) g.set(i, 4 * c4 + e, s + y);
                   }
               });
     }
-    __syncthreads();
+    return team_sync<TEAM>(tm, err);
 }
 
 // Edge increase (u, v): w_old -> w (w may be missing: a deletion).  Returns
-// false on the pass cap.
-template <typename T>
-__device__ __noinline__ bool b_increase(const BG<T> &g, int u, int v, T w_old, T w, int span, uint32_t *mask, int words, T *sx,
-                           T *sy, int32_t *rows, int *nrows_s) {
+// false on the pass cap or a team wait that gave up.
+template <typename T, bool TEAM>
+__device__ __noinline__ bool b_increase(const BG<T> &g, const Team &tm, int32_t *err, int u, int v, T w_old, T w,
+                                        int span, uint32_t *mask, int words, T *sx, T *sy, int32_t *rows,
+                                        int32_t *nrows_p, int32_t *changed_p) {
     using M = MinPlus<T>;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = tm.gw(), nw = tm.nw();
     const bool tight_edge = M::tight(w_old, __ldcg(&g.d(u, v)));
-    __syncthreads();
-    if (threadIdx.x == 0) g.w(u, v) = w;
-    if (!tight_edge) {
-        __syncthreads();
-        return true;
-    }
-    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    if (!team_sync<TEAM>(tm, err)) return false;   // every CTA has read D[u][v] before it changes
+    if (tm.leader()) g.w(u, v) = w;
+    if (!tight_edge) return team_sync<TEAM>(tm, err);
+    for (int t = tm.gt(); t < span; t += tm.nt()) {
         sx[t] = __ldcg(&g.dt(u, t));   // D[t][u]
         sy[t] = M::leg(__ldcg(&g.d(v, t)));
     }
-    b_clear_mask(mask, words, span, nrows_s);
+    if (!b_clear_mask<TEAM>(tm, err, mask, words, span, nrows_p)) return false;
     // pairs whose distance is a path through the old edge (Corollary 3 for an edge)
     for (int i = wid; i < span; i += nw) {
-        const T xi = sx[i];
-        if (!M::finite(xi) || !g.alive[i]) continue;
+        const T xi = tld<TEAM>(sx + i);
+        if (!M::finite(xi) || !__ldcg(g.alive + i)) continue;
         const T s = M::add(xi, w_old);
         if (!M::tight(s, __ldcg(&g.dt(v, i)))) continue;
-        const bool any = b_detect_row(g, i, s, sy, span, mask + (int64_t)i * words);
-        if (lane == 0 && any) rows[atomicAdd(nrows_s, 1)] = i;
+        const bool any = b_detect_row<T, TEAM>(g, i, s, sy, span, mask + (int64_t)i * words);
+        if (lane == 0 && any) rows[atomicAdd(nrows_p, 1)] = i;
     }
-    __syncthreads();
+    if (!team_sync<TEAM>(tm, err)) return false;
     // starting upper bounds: the direct edge, or the path through the edge at its new weight
-    const int nrows = *nrows_s;
+    const int nrows = tld<TEAM>(nrows_p);
     for (int r = wid; r < nrows; r += nw) {
-        const int i = rows[r];
+        const int i = tld<TEAM>(rows + r);
         for (int wd = 0; wd < words; ++wd) {
-            const uint32_t m = mask[(int64_t)i * words + wd];
+            const uint32_t m = __ldcg(mask + (int64_t)i * words + wd);
             const int j = wd * 32 + lane;
             if ((m >> lane) & 1u) {
-                const T via = M::add(M::add(sx[i], w), M::mn(sy[j], M::inf()));
+                const T via = M::add(M::add(tld<TEAM>(sx + i), w), M::mn(tld<TEAM>(sy + j), M::inf()));
                 g.set(i, j, M::mn(__ldcg(&g.w(i, j)), via));
             }
         }
     }
-    __syncthreads();
-    return b_relax(g, mask, words, span, rows, nrows);
+    if (!team_sync<TEAM>(tm, err)) return false;
+    return b_relax<T, TEAM>(g, tm, err, mask, words, span, rows, nrows, changed_p);
 }
 
-// Removal of node k.  Returns false on the pass cap.
-template <typename T>
-__device__ __noinline__ bool b_remove(const BG<T> &g, int k, int span, uint32_t *mask, int words, T *sx, T *sy, int32_t *rows,
-                         int *nrows_s) {
+// Removal of node k.  Returns false on the pass cap or a team wait that gave up.
+template <typename T, bool TEAM>
+__device__ __noinline__ bool b_remove(const BG<T> &g, const Team &tm, int32_t *err, int k, int span, uint32_t *mask,
+                                      int words, T *sx, T *sy, int32_t *rows, int32_t *nrows_p, int32_t *changed_p) {
     using M = MinPlus<T>;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = tm.gw(), nw = tm.nw();
+    for (int t = tm.gt(); t < span; t += tm.nt()) {
         sx[t] = __ldcg(&g.dt(k, t));                         // D[t][k]
         sy[t] = t == k ? unreachable_leg<T>() : M::leg(__ldcg(&g.d(k, t)));   // D[k][t]
     }
-    b_clear_mask(mask, words, span, nrows_s);
+    if (!b_clear_mask<TEAM>(tm, err, mask, words, span, nrows_p)) return false;
     // need_update_list: D[i][k] + D[k][j] == D[i][j], i != j, both != k
     for (int i = wid; i < span; i += nw) {
-        const T xi = sx[i];
-        if (i == k || !M::finite(xi) || !g.alive[i]) continue;
-        const bool any = b_detect_row(g, i, xi, sy, span, mask + (int64_t)i * words);
-        if (lane == 0 && any) rows[atomicAdd(nrows_s, 1)] = i;
+        const T xi = tld<TEAM>(sx + i);
+        if (i == k || !M::finite(xi) || !__ldcg(g.alive + i)) continue;
+        const bool any = b_detect_row<T, TEAM>(g, i, xi, sy, span, mask + (int64_t)i * words);
+        if (lane == 0 && any) rows[atomicAdd(nrows_p, 1)] = i;
     }
-    __syncthreads();
+    if (!team_sync<TEAM>(tm, err)) return false;
     // tombstone k (Section 3.2: its distances become infinite), then the
     // listed pairs restart from their direct edges
     const T inf = M::inf();
-    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    for (int t = tm.gt(); t < span; t += tm.nt()) {
         g.set(k, t, inf);
         g.set(t, k, inf);
         g.w(k, t) = inf;
         g.w(t, k) = inf;
     }
-    if (threadIdx.x == 0) g.alive[k] = 0;
-    __syncthreads();
-    const int nrows = *nrows_s;
+    if (tm.leader()) g.alive[k] = 0;
+    if (!team_sync<TEAM>(tm, err)) return false;
+    const int nrows = tld<TEAM>(nrows_p);
     for (int r = wid; r < nrows; r += nw) {
-        const int i = rows[r];
+        const int i = tld<TEAM>(rows + r);
         for (int wd = 0; wd < words; ++wd) {
-            const uint32_t m = mask[(int64_t)i * words + wd];
+            const uint32_t m = __ldcg(mask + (int64_t)i * words + wd);
             const int j = wd * 32 + lane;
             if ((m >> lane) & 1u) g.set(i, j, __ldcg(&g.w(i, j)));
         }
     }
-    __syncthreads();
-    return b_relax(g, mask, words, span, rows, nrows);
+    if (!team_sync<TEAM>(tm, err)) return false;
+    return b_relax<T, TEAM>(g, tm, err, mask, words, span, rows, nrows, changed_p);
 }
 
 // Widths (threads per CTA) the executor's autotuner chooses from.
 constexpr int BATCH_WIDTHS[3] = {128, 256, 512};
 
+// All updates of graph gi by a team (or one CTA); then the graph's status and
+// completion flag.  A pass cap reached is recorded and the next update goes
+// on; a team wait that gave up ends the graph (the team is out of step).
+template <typename T, bool TEAM>
+__device__ void b_graph(BatchHeader *hdr, int gi, const Team &tm, T *s0, T *s1, T *s2, T *s3, int32_t *srows,
+                        int32_t *nrows_p, int32_t *changed_p) {
+    BatchGraph &bg = hdr->graphs[gi];
+    BG<T> g{reinterpret_cast<T *>(bg.D), reinterpret_cast<T *>(bg.DT), reinterpret_cast<T *>(bg.W), bg.alive, bg.ld};
+    const T *vecs = reinterpret_cast<const T *>(hdr->vecs);
+    int32_t *err = &bg.status;
+    for (int q = bg.first; q < bg.first + bg.count; ++q) {
+        const BatchOp op = hdr->ops[q];
+        bool ok;
+        if (op.op == BOP_ADD) {
+            ok = b_add<T, TEAM>(g, tm, err, op.a, op.span, vecs + op.vec, vecs + op.vec + op.span, s0, s1, s2, s3);
+        } else if (op.op == BOP_DECREASE) {
+            ok = b_decrease<T, TEAM>(g, tm, err, op.a, op.b, bits_as<T>(op.w_bits), op.span, s0, s1);
+        } else if (op.op == BOP_INCREASE) {
+            ok = b_increase<T, TEAM>(g, tm, err, op.a, op.b, bits_as<T>(op.w_old_bits), bits_as<T>(op.w_bits),
+                                     op.span, bg.mask, bg.mask_words, s0, s1, srows, nrows_p, changed_p);
+        } else {
+            ok = b_remove<T, TEAM>(g, tm, err, op.a, op.span, bg.mask, bg.mask_words, s0, s1, srows, nrows_p,
+                                   changed_p);
+        }
+        if (!ok) {
+            if (__ldcg(err) & (int32_t)ERR_TIMEOUT) break;
+            if (tm.leader()) atomicOr(err, (int32_t)ERR_PASSES);
+        }
+    }
+    const bool synced = team_sync<TEAM>(tm, err);   // every CTA of the team is done with the graph
+    if (tm.leader()) {
+        const int32_t st = __ldcg(err) | (synced ? 0 : (int32_t)ERR_TIMEOUT);
+        bg.status = st;
+        if (hdr->done) {
+            __threadfence_system();   // the graph's results are written before its flag
+            hdr->done[gi] = 1 + st;
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T, int NT> __global__ void __launch_bounds__(NT, 768 / NT) k_batch(BatchHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int gi_s, nrows_s;
-    const T *vecs = reinterpret_cast<const T *>(hdr->vecs);
+    __shared__ int32_t gi_s, nrows_s, changed_s;
+    const int G = hdr->team_size;
+    const int max_span = hdr->max_span;
+    // large graphs: team t = blockIdx / G takes order[t], order[t + n_teams], ...
+    if (G > 1 && (int)blockIdx.x < hdr->n_teams * G) {
+        const int t = (int)blockIdx.x / G;
+        unsigned char *base = reinterpret_cast<unsigned char *>(hdr->team_scratch) + (int64_t)t * hdr->team_stride;
+        T *t0 = reinterpret_cast<T *>(base);
+        int32_t *trows = reinterpret_cast<int32_t *>(t0 + 4 * (int64_t)max_span);
+        int32_t *ints = trows + max_span;
+        const Team tm{(int)blockIdx.x % G, G, ints};
+        for (int k = t; k < hdr->n_team; k += hdr->n_teams)
+            b_graph<T, true>(hdr, hdr->order[k], tm, t0, t0 + max_span, t0 + 2 * max_span, t0 + 3 * max_span, trows,
+                             ints + 0, ints + 1);
+    }
+    // every other graph: one CTA each, from the queue
+    T *s0 = reinterpret_cast<T *>(smem_raw);
+    int32_t *srows = reinterpret_cast<int32_t *>(s0 + 4 * (int64_t)max_span);
+    const Team solo{0, 1, nullptr};
+    const int n_solo = hdr->n_graphs - hdr->n_team;
     while (true) {
         if (threadIdx.x == 0) gi_s = atomicAdd(&hdr->queue, 1);
         __syncthreads();
-        const int gi = gi_s;
+        const int q = gi_s;
         __syncthreads();
-        if (gi >= hdr->n_graphs) break;
-        BatchGraph &bg = hdr->graphs[gi];
-        BG<T> g{reinterpret_cast<T *>(bg.D), reinterpret_cast<T *>(bg.DT), reinterpret_cast<T *>(bg.W), bg.alive, bg.ld};
-        T *s0 = reinterpret_cast<T *>(smem_raw);
-        T *s1 = s0 + hdr->max_span;
-        T *s2 = s1 + hdr->max_span;
-        T *s3 = s2 + hdr->max_span;
-        int32_t *srows = reinterpret_cast<int32_t *>(s3 + hdr->max_span);
-        int err = 0;
-        for (int q = bg.first; q < bg.first + bg.count; ++q) {
-            const BatchOp op = hdr->ops[q];
-            bool ok = true;
-            if (op.op == BOP_ADD) {
-                b_add<T>(g, op.a, op.span, vecs + op.vec, vecs + op.vec + op.span, s0, s1, s2, s3);
-            } else if (op.op == BOP_DECREASE) {
-                b_decrease<T>(g, op.a, op.b, bits_as<T>(op.w_bits), op.span, s0, s1);
-            } else if (op.op == BOP_INCREASE) {
-                ok = b_increase<T>(g, op.a, op.b, bits_as<T>(op.w_old_bits), bits_as<T>(op.w_bits), op.span, bg.mask,
-                                   bg.mask_words, s0, s1, srows, &nrows_s);
-            } else {
-                ok = b_remove<T>(g, op.a, op.span, bg.mask, bg.mask_words, s0, s1, srows, &nrows_s);
-            }
-            if (!ok) err |= ERR_PASSES;
-        }
-        if (threadIdx.x == 0) {
-            bg.status = err;
-            if (hdr->done) {
-                __threadfence_system();   // the graph's results are written before its flag
-                hdr->done[gi] = 1 + err;
-            }
-        }
-        __syncthreads();
+        if (q >= n_solo) break;
+        b_graph<T, false>(hdr, hdr->order[hdr->n_team + q], solo, s0, s0 + max_span, s0 + 2 * max_span,
+                          s0 + 3 * max_span, srows, &nrows_s, &changed_s);
     }
 }
 

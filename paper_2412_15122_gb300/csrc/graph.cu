@@ -1306,6 +1306,9 @@ struct apsp_batch {
     size_t d_cap = 0;
     uint32_t *d_mask = nullptr;   // listed-pair bitmasks
     size_t mask_cap = 0;          // words
+    void *d_team = nullptr;       // team scratch (vectors, listed rows, counters) for large graphs
+    size_t team_cap = 0;
+    bool team_dirty = false;      // counters must be zeroed before the next launch
     // One CUDA graph per (dtype, CTA width) holding a whole launch: the
     // upload, the persistent kernel and the status read-back.  Later launches
     // of the same kind only update the three nodes' parameters (sizes,
@@ -1328,6 +1331,9 @@ struct apsp_batch {
 namespace {
 
 size_t align256(size_t a) { return (a + 255) & ~size_t(255); }
+
+// Graphs whose sweeps span at least this many slots go to teams of CTAs.
+constexpr int TEAM_MIN_SPAN = 384;
 
 template <typename T> apsp_status batch_weight(double w, T *out) {
     if (std::isnan(w)) return APSP_E_ARG;
@@ -1627,7 +1633,8 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
     const size_t o_hdr = 0, o_tab = align256(sizeof(BatchHeader));
     const size_t o_ops = o_tab + align256(table.size() * sizeof(BatchGraph));
     const size_t o_vec = o_ops + align256(std::max<size_t>(1, ops.size()) * sizeof(BatchOp));
-    const size_t total = o_vec + align256(std::max<size_t>(1, vecs.size()) * sizeof(T));
+    const size_t o_ord = o_vec + align256(std::max<size_t>(1, vecs.size()) * sizeof(T));
+    const size_t total = o_ord + align256((size_t)n_graphs * sizeof(int32_t));
     if (total > b->h_cap) {
         if (b->h_blob) cudaFreeHost(b->h_blob);
         b->h_blob = nullptr;
@@ -1680,7 +1687,53 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
     if ((e = apsp::batch_occupancy<T>(smem, nt, &per_sm)) != cudaSuccess) return cuda_status(e);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::max(1, std::min(n_graphs, std::max(1, per_sm) * sms));
+    // Teams for the large graphs when the batch has fewer graphs than CTAs
+    // that fit on the device at once (otherwise single CTAs already keep
+    // every SM busy; measured: teams cost 8 % on 512 graphs): teams of G (at
+    // most TEAM_MAX) CTAs.  The large graphs go first in the order, largest
+    // first, then the others, largest first (the longest jobs start earliest).
+    const int C = std::max(1, per_sm) * sms;
+    std::vector<int32_t> order((size_t)n_graphs);
+    for (int gi = 0; gi < n_graphs; ++gi) order[gi] = gi;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return spans[a] > spans[c]; });
+    int n_large = 0;
+    while (n_large < n_graphs && spans[order[n_large]] >= TEAM_MIN_SPAN) ++n_large;
+    int team = 1, n_teams = 0;
+    if (n_large > 0 && n_graphs < C) {   // with a graph for every CTA, single CTAs already fill the device
+        team = std::min(apsp::TEAM_MAX, std::max(2, C / n_large));
+        n_teams = std::min(n_large, C / team);
+    }
+    if (n_teams < 1) {
+        team = 1;
+        n_teams = 0;
+        n_large = 0;
+    }
+    const int grid = std::max(1, std::min(C, std::max(n_teams * team + (n_graphs - n_large), n_teams * team)));
+    const int64_t team_stride = (int64_t)align256(4 * (size_t)max_span * sizeof(T) + (size_t)max_span * 4 +
+                                                  apsp::TEAM_INTS * 4);
+    if (n_teams > 0) {
+        const size_t need = (size_t)n_teams * (size_t)team_stride;
+        if (need > b->team_cap) {
+            if (b->d_team) cudaFree(b->d_team);
+            b->d_team = nullptr;
+            b->team_cap = 0;
+            if (cudaMalloc(&b->d_team, need) != cudaSuccess) return APSP_E_NOMEM;
+            b->team_cap = need;
+            b->team_dirty = true;
+        }
+        if (b->team_dirty) {   // barrier counters start at zero
+            if (cudaMemsetAsync(b->d_team, 0, b->team_cap, b->stream) != cudaSuccess) return APSP_E_CUDA;
+            b->team_dirty = false;
+        }
+    }
+    hdr.n_team = n_large;
+    hdr.team_size = team;
+    hdr.n_teams = n_teams;
+    hdr.order = reinterpret_cast<const int32_t *>(b->d_blob + o_ord);
+    hdr.team_scratch = b->d_team;
+    hdr.team_stride = team_stride;
+    std::memcpy(b->h_blob + o_hdr, &hdr, sizeof(hdr));
+    std::memcpy(b->h_blob + o_ord, order.data(), (size_t)n_graphs * sizeof(int32_t));
     const size_t tab_bytes = table.size() * sizeof(BatchGraph);
     double work = 0.0;
     for (const BatchOp &op : ops) work += (double)op.span * op.span;
@@ -1724,7 +1777,10 @@ apsp_status batch_finish(apsp_batch *b) {
     }
     const apsp::BatchGraph *done = reinterpret_cast<const apsp::BatchGraph *>(b->h_blob + b->o_tab);
     for (int gi = 0; gi < b->n_graphs; ++gi)
-        if (done[gi].status) return APSP_E_TIMEOUT;
+        if (done[gi].status) {
+            if (done[gi].status & apsp::ERR_TIMEOUT) b->team_dirty = true;   // a team barrier may be mid-count
+            return APSP_E_TIMEOUT;
+        }
     return APSP_OK;
 }
 
@@ -1762,6 +1818,7 @@ apsp_status apsp_batch_destroy(apsp_batch *b) {
     if (b->h_blob) cudaFreeHost(b->h_blob);
     if (b->d_blob) cudaFree(b->d_blob);
     if (b->d_mask) cudaFree(b->d_mask);
+    if (b->d_team) cudaFree(b->d_team);
     if (b->h_done) cudaFreeHost(b->h_done);
     for (auto &row : b->cap)
         for (auto &cp : row) {

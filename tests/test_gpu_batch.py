@@ -242,3 +242,71 @@ def test_batch_autotuner_settles_on_a_width(lib):
     for g in graphs:
         g.close()
     b.close()
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+@pytest.mark.parametrize("width", [256, 512])
+def test_batch_teams_for_large_graphs(lib, dtype, width):
+    # Graphs of n >= 384 go to teams of CTAs (a team barrier between steps,
+    # scratch in global memory), the others to single CTAs, in one launch:
+    # results equal one call per update (int32 bit for bit, fp32 within
+    # 1e-5) and the oracle (every entry up to n = 1100, 64 sampled rows at
+    # n = 2048).  Two launches in a row on one executor (the second replays
+    # the captured graph and reuses the team scratch).
+    from paper_2412_15122_gb300 import Batch, Graph
+    sizes = [2048, 1100, 700, 400, 150, 90]
+    graphs, singles, mirrors, per = [], [], [], []
+    for gi, n in enumerate(sizes):
+        cap = n + 24
+        W, ups = _graph_and_updates(n, cap, 900 + gi, 24, dtype, gi % 2 == 0)
+        graphs.append(Graph(W, cap))
+        singles.append(Graph(W, cap))
+        inf = np.float32(np.inf) if dtype == "f32" else synth.INF_I32
+        Wm = np.full((cap, cap), inf, W.dtype)
+        Wm[:n, :n] = W
+        alive = np.zeros(cap, bool)
+        alive[:n] = True
+        per.append(_items_for(gi, ups, Wm, alive, cap, dtype))
+        mirrors.append((Wm, alive))
+    b = Batch()
+    b.set_width(width)
+    for half in (0, 1):
+        its = [it for p in per for it in p[12 * half:12 * (half + 1)]]
+        b.run(graphs, its)
+        for it in its:
+            s = singles[it[0]]
+            if it[1] == "add":
+                s.add_node(it[2], it[3])
+            elif it[1] == "remove":
+                s.remove_node(it[2])
+            else:
+                s.update_edge(it[2], it[3], it[4])
+    assert b.info()["graph_replays"] == 2
+    for gi, (g, s) in enumerate(zip(graphs, singles)):
+        Db, Ds = g.D(), s.D()
+        Wm, alive = mirrors[gi]
+        m = Db.shape[0]
+        live = np.flatnonzero(alive[:m])
+        if dtype == "i32":
+            np.testing.assert_array_equal(Db, Ds, err_msg=f"graph {gi}")
+        else:
+            fin = np.isfinite(Ds)
+            assert np.array_equal(np.isfinite(Db), fin)
+            assert (np.abs(Db[fin] - Ds[fin]) <= 1e-5 * np.abs(Ds[fin]) + 1e-6).all()
+        if sizes[gi] <= 1100:
+            ref = O.fw(Wm[:m, :m], alive[:m])[np.ix_(live, live)]
+        else:
+            pick = live[synth.uniform_int(gi, 9, 64, 0, len(live) - 1)]
+            ref = O.dijkstra_rows(Wm[:m, :m], pick, alive[:m])[:, live]
+            live_rows = pick
+        rows = live if sizes[gi] <= 1100 else live_rows
+        got = Db[np.ix_(rows, live)].astype(np.float64)
+        if dtype == "i32":
+            np.testing.assert_array_equal(got, O.to_i32(ref), err_msg=f"graph {gi} vs oracle")
+        else:
+            fin = np.isfinite(ref)
+            assert np.array_equal(np.isfinite(got), fin)
+            assert (np.abs(got[fin] - ref[fin]) <= 1e-5 * np.abs(ref[fin]) + 1e-6).all()
+        g.close()
+        s.close()
+    b.close()

@@ -63,6 +63,8 @@ struct apsp_graph {
     int4 *hrows = nullptr;
     int4 *hunits = nullptr, *hralloc = nullptr;
     int32_t *rowcnt = nullptr;
+    uint32_t *bmask = nullptr;   // detection: exact masks of flagged batches
+    int32_t bmask_nb = 0;
     long long *hbase = nullptr;
     uint8_t *pstamp = nullptr, *rstamp = nullptr;
     int4 *items = nullptr;
@@ -281,6 +283,8 @@ template <typename T> Dev<T> dev_of(apsp_graph *g) {
     d.hunits = g->hunits;
     d.hralloc = g->hralloc;
     d.rowcnt = g->rowcnt;
+    d.bmask = g->bmask;
+    d.bmask_nb = g->bmask_nb;
     d.hbase = g->hbase;
     d.items = g->items;
     d.pairs = g->pairs;
@@ -388,6 +392,8 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->hunits = (int4 *)dalloc(g, hunit_cap * sizeof(int4));
     g->hralloc = (int4 *)dalloc(g, ld * sizeof(int4));
     g->rowcnt = (int32_t *)dalloc(g, ld * apsp::DET_MAXB * sizeof(int32_t));
+    g->bmask_nb = (int32_t)((ld + 1023) / 1024);
+    g->bmask = (uint32_t *)dalloc(g, (size_t)ld * g->bmask_nb * 32 * sizeof(uint32_t));
     g->hbase = (long long *)dalloc(g, hunit_cap * sizeof(long long));
     g->pair_cap = std::min<int64_t>((int64_t)ld * 512, (int64_t)1 << 30);
     g->item_cap = (int32_t)(g->pair_cap / apsp::ITEM_PAIRS + ld);
@@ -408,7 +414,7 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
         !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->ctl || !g->model ||
         !g->pmin || !g->pstamp || !g->rstamp || !g->units || !g->hrows || !g->hunits || !g->hralloc || !g->rowcnt ||
-        !g->hbase)
+        !g->hbase || !g->bmask)
         return APSP_E_NOMEM;
     if (cudaMallocHost(&g->pin, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
     if (cudaMallocHost(&g->pin_fetch, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;

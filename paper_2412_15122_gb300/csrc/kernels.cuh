@@ -43,6 +43,8 @@ template <typename T> struct Dev {
     int4 *hunits;             // detection: flagged units (row, batch, row entry, position in the row)
     int4 *hralloc;            // detection: per flagged row (first item, first unit, pairs)
     int32_t *rowcnt;          // detection: listed pairs per (row, batch), DET_MAXB a row
+    uint32_t *bmask;          // detection: exact mask per (row, batch), 32 words (one per lane), bmask_nb batches a row
+    int32_t bmask_nb;
     long long *hbase;         // detection: first pair slot per unit (-1: none)
     int4 *items;              // (row, first pair, pair count | row's pair count << 8, row's first pair)
     int32_t *pairs;           // affected column per pair, grouped by row (columns ascending)
@@ -831,23 +833,25 @@ __global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d
         }
         const T xi = __ldcg(d.x + i);
         const T x2i = TWO ? __ldcg(d.x2 + i) : M::inf();
-        const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
-        V4 v[SWEEP_B];
-#pragma unroll
-        for (int bb = 0; bb < SWEEP_B; ++bb) {
-            const int c4 = c0 + bb * 32 + lane;
-            if (c4 < nv4) v[bb] = __ldcg(Dr4 + c4);
-        }
         if (base < 0) continue;   // a row that did not fit
-        const T s1 = kind == 0 ? xi : M::add(xi, w_old);
-        const T s2 = M::add(x2i, w_old);
-        const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
         unsigned mask;
         if (FILTER == 2) {
             mask = __ldcg(umask + (int64_t)u * 32 + lane);
+        } else if (FILTER == 0) {
+            mask = __ldcg(d.bmask + ((int64_t)i * d.bmask_nb + ue.y) * 32 + lane);   // left by k_det_scan
         } else {
+            const V4 *Dr4 = reinterpret_cast<const V4 *>(d.D + (int64_t)i * d.ld);
+            V4 v[SWEEP_B];
+#pragma unroll
+            for (int bb = 0; bb < SWEEP_B; ++bb) {
+                const int c4 = c0 + bb * 32 + lane;
+                if (c4 < nv4) v[bb] = __ldcg(Dr4 + c4);
+            }
+            const T s1 = kind == 0 ? xi : M::add(xi, w_old);
+            const T s2 = M::add(x2i, w_old);
+            const bool use1 = M::finite(s1), use2 = TWO && M::finite(s2);
             mask = det_exact_mask<T, TWO>(d, v, c0, s1, s2, use1, use2, i, a, kind);
-            if (FILTER == 1) mask = det_filter_direct<T>(d, mask, v, i, c0);
+            mask = det_filter_direct<T>(d, mask, v, i, c0);
         }
         int tot;
         int off = warp_exclusive_scan(__popc(mask), &tot);
@@ -979,39 +983,39 @@ __global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, 
             }
             const bool maybe = (use1 && s1 <= b1) || (TWO && use2 && s2 <= b2);
             if (__ballot_sync(0xffffffffu, maybe)) {
-                // exact count of the batch's listed pairs (the same test as
-                // det_exact_mask; column a is staged unreachable, column i
-                // is taken out below)
-                int c = 0;
+                // the batch's exact mask (the same test and bit layout as
+                // det_exact_mask; column a is staged unreachable, column i is
+                // taken out): its count for the reservation, the mask itself
+                // for k_det_write, which then need not read the batch again
+                unsigned mk = 0;
 #pragma unroll
                 for (int bb = 0; bb < SWEEP_B; ++bb) {
                     const int c4 = c0 + bb * 32 + lane;
                     if (c4 < nv4) {
+                        unsigned m = 0;
                         if (use1) {
                             const V4 y = ys4[c4];
-                            c += M::slack_tight(M::slack(s1 + y.x, v[bb].x)) + M::slack_tight(M::slack(s1 + y.y, v[bb].y)) +
-                                 M::slack_tight(M::slack(s1 + y.z, v[bb].z)) + M::slack_tight(M::slack(s1 + y.w, v[bb].w));
+                            m |= (unsigned)M::slack_tight(M::slack(s1 + y.x, v[bb].x)) |
+                                 (unsigned)M::slack_tight(M::slack(s1 + y.y, v[bb].y)) << 1 |
+                                 (unsigned)M::slack_tight(M::slack(s1 + y.z, v[bb].z)) << 2 |
+                                 (unsigned)M::slack_tight(M::slack(s1 + y.w, v[bb].w)) << 3;
                         }
                         if (TWO && use2) {
                             const V4 y = y2s4[c4];
-                            c += (M::slack_tight(M::slack(s2 + y.x, v[bb].x)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4], v[bb].x)))) +
-                                 (M::slack_tight(M::slack(s2 + y.y, v[bb].y)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4 + 1], v[bb].y)))) +
-                                 (M::slack_tight(M::slack(s2 + y.z, v[bb].z)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4 + 2], v[bb].z)))) +
-                                 (M::slack_tight(M::slack(s2 + y.w, v[bb].w)) && !(use1 && M::slack_tight(M::slack(s1 + ys[4 * c4 + 3], v[bb].w))));
+                            m |= (unsigned)M::slack_tight(M::slack(s2 + y.x, v[bb].x)) |
+                                 (unsigned)M::slack_tight(M::slack(s2 + y.y, v[bb].y)) << 1 |
+                                 (unsigned)M::slack_tight(M::slack(s2 + y.z, v[bb].z)) << 2 |
+                                 (unsigned)M::slack_tight(M::slack(s2 + y.w, v[bb].w)) << 3;
                         }
-                        if (c4 == (i >> 2)) {
-                            // the diagonal is never a pair (tight only on a zero-length cycle)
-                            const int e = i & 3;
-                            const T ve = e == 0 ? v[bb].x : e == 1 ? v[bb].y : e == 2 ? v[bb].z : v[bb].w;
-                            c -= (use1 && M::slack_tight(M::slack(s1 + ys[i], ve))) ||
-                                 (TWO && use2 && M::slack_tight(M::slack(s2 + y2s[i], ve)));
-                        }
+                        if (c4 == (i >> 2)) m &= ~(1u << (i & 3));   // the diagonal is never a pair
+                        mk |= m << (4 * bb);
                     }
                 }
-                c = warp_sum(c);
+                const int c = warp_sum(__popc(mk));
                 if (c > 0) {
                     bmask |= 1u << bi;
                     if (lane == 0) d.rowcnt[(int64_t)i * DET_MAXB + bi] = c;
+                    d.bmask[((int64_t)i * d.bmask_nb + bi) * 32 + lane] = mk;
                 }
             }
         }

@@ -1141,7 +1141,20 @@ __device__ void repair_warm(Dev<T> &d) {
     // listed pairs from pmin and stores every pair; later passes take only
     // y lowered in the previous pass and store only pairs they lower.
     // Stores are atomic minima (the segments of one item share its pairs).
+    //
+    // Gathers that cannot lower the pair are skipped (int32).  Every value
+    // in D during the repair is the length of a path in the updated graph,
+    // hence >= the new distance >= the old one (a removal or an increase
+    // never shortens a path), and the old matrix obeys the triangle
+    // inequality through the staged legs: with ly = D[a][.] (removal of a;
+    // D[v][.] for an increase of u -> v) and lx = D[.][a] (D[.][u]),
+    //     D[y][j] >= ly[j] - ly[y]   and   D[y][j] >= lx[y] - lx[j].
+    // So y can lower pair j only if dy - ly[y] < cur - ly[j] and
+    // dy + lx[y] < cur + lx[j]; a skipped candidate is >= cur and the
+    // stored minimum is the same as without the test.  Values are <= INF =
+    // 2^30 - 1, so both sides fit in int32.
     constexpr int YB = YSEG / 32;
+    constexpr bool PRUNE = std::is_same<T, int32_t>::value;
     for (pass = 2; pass <= MAX_PASSES && !*(volatile int32_t *)&ctl->stop; ++pass) {
         const int par = pass & 1;
         bool changed = false;
@@ -1164,13 +1177,18 @@ __device__ void repair_warm(Dev<T> &d) {
             const T *Di = d.D + (int64_t)i * ld;
             int j = 0;
             T cur = (T)0;   // pairs past cnt: no y passes dy < 0, so they load nothing
+            T cly = (T)0, clx = (T)0;   // cur - ly[j], cur + lx[j]
             if (mine) {
                 j = __ldcg(d.pairs + item.y + lane);
                 cur = pass == 2 ? M::unkey(__ldcg(d.pmin + item.y + lane)) : __ldcg(Di + j);
+                if (PRUNE) {
+                    cly = cur - __ldg(d.y + j);
+                    clx = cur + __ldg(d.x + j);
+                }
             }
             const int ybeg = seg * YSEG, yend = min(nrow, ybeg + YSEG);
             int yv[YB];
-            T dyv[YB];
+            T dyv[YB], ayv[YB], byv[YB];   // dy, dy - ly[y], dy + lx[y]
 #pragma unroll
             for (int b = 0; b < YB; ++b) {
                 const int yi = ybeg + 32 * b + lane;
@@ -1180,6 +1198,14 @@ __device__ void repair_warm(Dev<T> &d) {
                     yv[b] = __ldcg(d.pairs + item.w + yi);
                     if (pass == 2) dyv[b] = M::unkey(__ldcg(d.pmin + item.w + yi));
                     else if ((int)__ldcg(d.pstamp + item.w + yi) >= pass - 1) dyv[b] = __ldcg(Di + yv[b]);
+                }
+                if (PRUNE) {
+                    ayv[b] = dyv[b];
+                    byv[b] = dyv[b];
+                    if (dyv[b] < M::inf()) {
+                        ayv[b] -= __ldg(d.y + yv[b]);
+                        byv[b] += __ldg(d.x + yv[b]);
+                    }
                 }
             }
             bool any_y = false;
@@ -1195,19 +1221,26 @@ __device__ void repair_warm(Dev<T> &d) {
             for (int q = 0; q < 32; q += 4) {
                 if (q < cnt) {
                     const T *cr[4];
-                    T cq[4];
+                    T cq[4], qa[4], qb[4];
 #pragma unroll
                     for (int u4 = 0; u4 < 4; ++u4) {
                         const int jj = __shfl_sync(0xffffffffu, j, q + u4);
                         cq[u4] = __shfl_sync(0xffffffffu, cur, q + u4);
+                        if (PRUNE) {
+                            qa[u4] = __shfl_sync(0xffffffffu, cly, q + u4);
+                            qb[u4] = __shfl_sync(0xffffffffu, clx, q + u4);
+                        }
                         cr[u4] = cols + (int64_t)jj * ld;
                     }
                     T v[4][YB];
 #pragma unroll
                     for (int u4 = 0; u4 < 4; ++u4)
 #pragma unroll
-                        for (int b = 0; b < YB; ++b)
-                            v[u4][b] = (b < nb && dyv[b] < cq[u4]) ? __ldcg(cr[u4] + yv[b]) : M::inf();
+                        for (int b = 0; b < YB; ++b) {
+                            bool use = b < nb && dyv[b] < cq[u4];
+                            if (PRUNE) use = use && ayv[b] < qa[u4] && byv[b] < qb[u4];
+                            v[u4][b] = use ? __ldcg(cr[u4] + yv[b]) : M::inf();
+                        }
 #pragma unroll
                     for (int u4 = 0; u4 < 4; ++u4)
 #pragma unroll

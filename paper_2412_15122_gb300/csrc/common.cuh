@@ -210,6 +210,19 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+// Programmatic dependent launch.  The kernels of an update's launch
+// sequence are launched with programmatic stream serialization, so a
+// kernel's CTAs may be scheduled while its predecessor in the stream is
+// still draining.  Every such kernel calls pdl_enter() first: it waits
+// until the predecessor grid has completed and its writes are visible
+// (griddepcontrol.wait; a no-op for an ordinary launch), then allows its
+// own successor to begin launching.  Nothing is read or written before the
+// wait, so the order of the updates' effects is that of the stream.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Grid-wide barrier for a cooperatively launched grid (all CTAs resident).
 // The last CTA to arrive runs `leader()` before releasing the others, so the
 // leader can publish decisions that every CTA reads after the barrier.  The

@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(FW_THREADS, 2) k_fw_p3(T *D, int64_t ld, int k
 // them, and reset the two reduction vectors.
 template <typename T>
 __global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int cap, int p) {
+    pdl_enter();
     using M = MinPlus<T>;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= d.span) return;
@@ -270,6 +271,7 @@ constexpr int INS_CB = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d, int rows_per_cta) {
+    pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     __shared__ T red[8][INS_CB];
@@ -368,6 +370,7 @@ __device__ __forceinline__ void insert_finish_entry(const Dev<T> &d, int p, int 
 // (insert_finish_entry) while the rows are swept.
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p, int ranges, int rows_per) {
+    pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -433,6 +436,7 @@ __global__ void __launch_bounds__(256, 4) k_insert_relax(Dev<T> d, int p, int ra
 
 template <typename T>
 __global__ void k_dec_prepass(Dev<T> d, int u, int v, T w) {
+    pdl_enter();
     using M = MinPlus<T>;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
@@ -459,6 +463,7 @@ __global__ void k_dec_prepass(Dev<T> d, int u, int v, T w) {
 
 template <typename T>
 __global__ void __launch_bounds__(256, 3) k_dec_sweep(Dev<T> d, T w) {
+    pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     const int nrows = *(volatile int32_t *)&d.ctl->r_count;
@@ -518,6 +523,7 @@ template <typename T> __device__ __forceinline__ void clear_repair_scratch(const
 
 template <typename T>
 __global__ void k_rm_gather(Dev<T> d, int k) {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.span) return;
     d.x[i] = col_src(d, k, i);                 // D[i][k]
@@ -527,6 +533,7 @@ __global__ void k_rm_gather(Dev<T> d, int k) {
 
 template <typename T>
 __global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
+    pdl_enter();
     using M = MinPlus<T>;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool tight_edge = M::tight(w_old, d.D[(int64_t)u * d.ld + v]);
@@ -674,6 +681,7 @@ __device__ __forceinline__ void det_write_pair(const Dev<T> &d, int i, int j, lo
 //                batch's slots with their starting upper bounds.
 template <typename T>
 __global__ void __launch_bounds__(256) k_det_alloc(Dev<T> d) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int n_rows = *(volatile const int32_t *)&d.ctl->hit_rows;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -753,6 +761,7 @@ __global__ void __launch_bounds__(256) k_det_alloc(Dev<T> d) {
 // reservation, so k_det_alloc and k_det_write see the same, filtered pairs.
 template <typename T, bool TWO>
 __global__ void __launch_bounds__(256, 2) k_det_recount(Dev<T> d, int kind, int a, T w_old) {
+    pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     const int lane = threadIdx.x & 31;
@@ -805,6 +814,7 @@ __device__ __forceinline__ void tombstone_entry(const Dev<T> &d, int k, int t) {
 template <typename T, bool TWO, int FILTER>
 __global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new,
                                                                       const uint32_t *umask) {
+    pdl_enter();
     if (kind == 0)
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.span; t += gridDim.x * blockDim.x)
             tombstone_entry<T>(d, a, t);
@@ -891,6 +901,7 @@ __global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d
 // to the hit list with one atomic when it is done or holds 32.
 template <typename T, bool TWO>
 __global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, T w_old) {
+    pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1080,6 +1091,7 @@ struct RepairCfg {
 // work item; int32 exact, fp32 "grew" beyond the tightness slack.
 template <typename T, bool TWO>
 __global__ void __launch_bounds__(256) k_grown_count(Dev<T> d, int kind, T w_old, int32_t *rflag) {
+    pdl_enter();
     using M = MinPlus<T>;
     const int lane = threadIdx.x & 31;
     const unsigned long long alloc = *(volatile const unsigned long long *)&d.ctl->alloc;

@@ -17,6 +17,34 @@ template <typename F> static inline cudaError_t launch(const LaunchCtx &c, const
     return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialization (the kernel begins with
+// pdl_enter()): its CTAs may be scheduled while the previous kernel in the
+// stream drains, which hides most of the launch gap between the short
+// kernels of an update.  Returns the launch's own status.
+template <typename... KArgs, typename... Args>
+static inline cudaError_t pdl(cudaStream_t s, dim3 grid, dim3 block, size_t smem, void (*k)(KArgs...), Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// As launch(), for a callable that returns the launch status.
+template <typename F> static inline cudaError_t launch_s(const LaunchCtx &c, const char *name, F &&f) {
+    c.hook.begin(name);
+    const cudaError_t e = f();
+    c.hook.end(name);
+    const cudaError_t last = cudaGetLastError();
+    return e != cudaSuccess ? e : last;
+}
+
 static inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 template <typename T> cudaError_t run_fill(const LaunchCtx &c, T *p, T v, int64_t n) {
@@ -54,24 +82,24 @@ template <typename T> cudaError_t run_fw(const LaunchCtx &c, const Dev<T> &d) {
 template <typename T>
 cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
     cudaError_t e;
-    if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "insert_prep", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_insert_prep<T>, d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
     // exactly one wave (never a partial second one): the resident CTAs split
     // into column bands x row ranges
     const int bands = cdiv(d.span, INS_CB);
     const int ranges = std::max(1, std::min(cdiv(d.span, 16), c.insred_per_sm * c.num_sms / bands));
     const int rows_per = cdiv(d.span, ranges);
     dim3 g(bands, cdiv(d.span, rows_per));
-    if ((e = launch(c, "insert_reduce", [&] { k_insert_reduce<T><<<g, 256, 0, c.stream>>>(d, rows_per); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "insert_reduce", [&] { return pdl(c.stream, g, 256, 0, k_insert_reduce<T>, d, rows_per); })) != cudaSuccess) return e;
     int gr = c.relax_grid;
     size_t sm = (size_t)d.span * sizeof(int32_t);
     const int nranges = cdiv(d.span, rows_per);
-    return launch(c, "insert_relax", [&] { k_insert_relax<T><<<gr, 256, sm, c.stream>>>(d, p, nranges, rows_per); });
+    return launch_s(c, "insert_relax", [&] { return pdl(c.stream, gr, 256, sm, k_insert_relax<T>, d, p, nranges, rows_per); });
 }
 
 template <typename T> cudaError_t run_decrease(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w) {
     cudaError_t e;
-    if ((e = launch(c, "decrease_prepass", [&] { k_dec_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w); })) != cudaSuccess) return e;
-    return launch(c, "decrease_sweep", [&] { k_dec_sweep<T><<<c.num_sms * 2, 256, 0, c.stream>>>(d, w); });
+    if ((e = launch_s(c, "decrease_prepass", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_dec_prepass<T>, d, u, v, w); })) != cudaSuccess) return e;
+    return launch_s(c, "decrease_sweep", [&] { return pdl(c.stream, c.num_sms * 2, 256, 0, k_dec_sweep<T>, d, w); });
 }
 
 template <typename T> static size_t detect_smem(const Dev<T> &d, bool two) {
@@ -86,21 +114,21 @@ static cudaError_t run_detect_t(const LaunchCtx &c, const Dev<T> &d, int kind, i
     cudaError_t e;
     const int scan_grid = TWO ? c.detect2_grid : c.detect_grid;
     const int mode = cfg.list_mode;
-    if ((e = launch(c, name, [&] { k_det_scan<T, TWO><<<scan_grid, 256, detect_smem(d, TWO), c.stream>>>(d, kind, a, w_old); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, name, [&] { return pdl(c.stream, scan_grid, 256, detect_smem(d, TWO), k_det_scan<T, TWO>, d, kind, a, w_old); })) != cudaSuccess) return e;
     if (mode == 1 &&
-        (e = launch(c, "detect_recount", [&] { k_det_recount<T, TWO><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old); })) != cudaSuccess)
+        (e = launch_s(c, "detect_recount", [&] { return pdl(c.stream, c.detunit_grid, 256, 0, k_det_recount<T, TWO>, d, kind, a, w_old); })) != cudaSuccess)
         return e;
     if (mode == 2 &&
-        (e = launch(c, "detect_alg12", [&] {
-             k_det_alg12<T, TWO><<<c.pw_grid, PW_WARPS * 32, pw_smem_bytes<T>(), c.stream>>>(d, kind, a, w_old, cfg.umask);
+        (e = launch_s(c, "detect_alg12", [&] {
+             return pdl(c.stream, c.pw_grid, PW_WARPS * 32, pw_smem_bytes<T>(), k_det_alg12<T, TWO>, d, kind, a, w_old, cfg.umask);
          })) != cudaSuccess)
         return e;
-    if ((e = launch(c, "detect_alloc", [&] { k_det_alloc<T><<<c.detalloc_grid, 256, 0, c.stream>>>(d); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "detect_alloc", [&] { return pdl(c.stream, c.detalloc_grid, 256, 0, k_det_alloc<T>, d); })) != cudaSuccess) return e;
     if (mode == 1)
-        return launch(c, "detect_write", [&] { k_det_write<T, TWO, 1><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new, nullptr); });
+        return launch_s(c, "detect_write", [&] { return pdl(c.stream, c.detunit_grid, 256, 0, k_det_write<T, TWO, 1>, d, kind, a, w_old, w_new, (const uint32_t *)nullptr); });
     if (mode == 2)
-        return launch(c, "detect_write", [&] { k_det_write<T, TWO, 2><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new, cfg.umask); });
-    return launch(c, "detect_write", [&] { k_det_write<T, TWO, 0><<<c.detunit_grid, 256, 0, c.stream>>>(d, kind, a, w_old, w_new, nullptr); });
+        return launch_s(c, "detect_write", [&] { return pdl(c.stream, c.detunit_grid, 256, 0, k_det_write<T, TWO, 2>, d, kind, a, w_old, w_new, (const uint32_t *)cfg.umask); });
+    return launch_s(c, "detect_write", [&] { return pdl(c.stream, c.detunit_grid, 256, 0, k_det_write<T, TWO, 0>, d, kind, a, w_old, w_new, (const uint32_t *)nullptr); });
 }
 
 template <typename T>
@@ -145,9 +173,7 @@ template <typename F> static cudaError_t coop_launch(cudaStream_t stream, F &&la
 // k_repair_main, which makes the same decision and runs either the later
 // passes or the cold Floyd-Warshall.
 template <typename T> cudaError_t run_repair(const LaunchCtx &c, const Dev<T> &d, const RepairCfg &cfg) {
-    cudaError_t e = launch(c, "repair_p1", [&] {
-        k_repair_p1<T><<<c.p1_grid, 256, 0, c.stream>>>(d, cfg);
-    });
+    cudaError_t e = launch_s(c, "repair_p1", [&] { return pdl(c.stream, c.p1_grid, 256, 0, k_repair_p1<T>, d, cfg); });
     if (e != cudaSuccess) return e;
     Dev<T> dd = d;
     RepairCfg cc = cfg;
@@ -169,13 +195,13 @@ template <typename T> static cudaError_t run_grown(const LaunchCtx &c, const Dev
     if (e != cudaSuccess) return e;
     const int grid = 2 * c.num_sms;
     if (d.undirected && kind == 1)
-        return launch(c, "grown_count", [&] { k_grown_count<T, true><<<grid, 256, 0, c.stream>>>(d, kind, w_old, cfg.grown_flag); });
-    return launch(c, "grown_count", [&] { k_grown_count<T, false><<<grid, 256, 0, c.stream>>>(d, kind, w_old, cfg.grown_flag); });
+        return launch_s(c, "grown_count", [&] { return pdl(c.stream, grid, 256, 0, k_grown_count<T, true>, d, kind, w_old, cfg.grown_flag); });
+    return launch_s(c, "grown_count", [&] { return pdl(c.stream, grid, 256, 0, k_grown_count<T, false>, d, kind, w_old, cfg.grown_flag); });
 }
 
 template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
     cudaError_t e;
-    if ((e = launch(c, "remove_gather", [&] { k_rm_gather<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, k); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "remove_gather", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_rm_gather<T>, d, k); })) != cudaSuccess) return e;
     if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, cfg, "detect_remove")) != cudaSuccess) return e;
     if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
     return run_grown<T>(c, d, 0, (T)0, cfg);
@@ -184,7 +210,7 @@ template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d
 template <typename T>
 cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_old, T w_new, const RepairCfg &cfg) {
     cudaError_t e;
-    if ((e = launch(c, "increase_prepass", [&] { k_inc_prepass<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, u, v, w_old, w_new); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "increase_prepass", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_inc_prepass<T>, d, u, v, w_old, w_new); })) != cudaSuccess) return e;
     if ((e = run_detect<T>(c, d, 1, u, w_old, w_new, cfg, "detect_increase")) != cudaSuccess) return e;
     if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
     return run_grown<T>(c, d, 1, w_old, cfg);

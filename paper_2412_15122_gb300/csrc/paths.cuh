@@ -519,6 +519,7 @@ __device__ bool alg12_keep(const Dev<T> &d, int i, int j, int excl, T dold, PwWa
 // writes see Algorithm 12's list.
 template <typename T, bool TWO>
 __global__ void __launch_bounds__(PW_WARPS * 32) k_det_alg12(Dev<T> d, int kind, int a, T w_old, uint32_t *umask) {
+    pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char pw_smem[];

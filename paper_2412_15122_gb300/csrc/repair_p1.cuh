@@ -27,6 +27,7 @@ namespace apsp {
 
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_repair_p1(Dev<T> d, RepairCfg cfg) {
+    pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     constexpr int CW = PASS1_COLS / 128;   // 16-byte vectors per lane per window

@@ -138,6 +138,13 @@ typedef struct {
     int64_t grown_pairs;
     int32_t grown_rows;
     float grown_cost;
+    /* Node insertion (Section 3.1): rows of D and of D transposed that the
+     * reductions of Corollaries 1 and 2 read.  Only rows t with
+     * w(p, t) <= min_t' w(p, t') + max_j D[t0][j] (t0 the argmin) can attain
+     * a minimum of Corollary 1, and likewise for Corollary 2; when that bound
+     * leaves at most span / 8 of them only those are read, else every row is
+     * (reported as -1).  0 for other updates. */
+    int32_t reduce_rows;
 } apsp_stats;
 
 typedef struct {

@@ -44,7 +44,8 @@ class apsp_stats(ctypes.Structure):
                 ("overflow", ctypes.c_int32), ("cold_reason", ctypes.c_int32), ("cost", ctypes.c_float),
                 ("model_warm", ctypes.c_float), ("model_cold", ctypes.c_float),
                 ("pairs_rechecked", ctypes.c_int64), ("warm_pass1_us", ctypes.c_float), ("warm_total_us", ctypes.c_float),
-                ("grown_pairs", ctypes.c_int64), ("grown_rows", ctypes.c_int32), ("grown_cost", ctypes.c_float)]
+                ("grown_pairs", ctypes.c_int64), ("grown_rows", ctypes.c_int32), ("grown_cost", ctypes.c_float),
+                ("reduce_rows", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -68,6 +68,7 @@ struct apsp_graph {
     long long *hbase = nullptr;
     uint8_t *pstamp = nullptr, *rstamp = nullptr;
     int4 *items = nullptr;
+    int32_t *icand = nullptr;   // node insertion: candidate rows / columns of the reduction
     Ctl *ctl = nullptr;
     // path queries (Section 4): per-call buffers, grown on demand
     void *pq_uv = nullptr, *pq_out = nullptr, *pq_wide = nullptr;
@@ -87,13 +88,29 @@ struct apsp_graph {
 
     // host side
     std::vector<uint8_t> alive_h;
-    std::vector<char> Wh;        // cap x cap mirror of W
-    void *pin = nullptr;         // pinned: 2 * cap elements (add_node staging)
-    cudaEvent_t pin_ev = nullptr;
-    bool pin_pending = false;
-    void *pin_fetch = nullptr;   // pinned: 2 * cap elements (mirror of device-input adds)
-    cudaEvent_t fetch_ev = nullptr;
-    int fetch_pending_p = -1;
+    // Mirror of W in two cap x cap copies, so that no update writes a column:
+    // row i of Wh holds W[i][.] and row j of WhT holds W[.][j], each as set
+    // by the latest add of that slot; an edge update writes both.  W[i][j] of
+    // live i != j is in the copy of whichever of i and j was added later
+    // (mirror_get); a removal writes nothing (its slot's next add rewrites
+    // both rows).
+    std::vector<char> Wh, WhT;
+    std::vector<uint64_t> add_seq;   // per slot: order of its latest add (0: the initial graph)
+    uint64_t seq = 0;
+    static constexpr int RING = 8;   // host-input adds staged, device-input adds awaiting their weights
+    void *pin = nullptr;             // pinned: RING x 2 * cap elements (add_node staging ring)
+    cudaEvent_t pin_ev[RING] = {};
+    bool pin_used[RING] = {};
+    int pin_next = 0;
+    void *pin_fetch = nullptr;       // pinned: RING x 2 * cap elements (device-input adds' weights)
+    cudaEvent_t fetch_ev[RING] = {};
+    struct Fetch {
+        int p;                       // slot added
+        uint64_t seq;                // its add_seq at the add
+        int ring;                    // pinned buffer / event
+    };
+    std::deque<Fetch> fetches;       // device-input adds not yet in the mirror, oldest first
+    int fetch_next = 0;
     void *pin_small = nullptr;   // pinned scratch for queries / control block
     int64_t pin_small_bytes = 0;
 
@@ -232,8 +249,10 @@ void release(apsp_graph *g) {
     if (g->pin) cudaFreeHost(g->pin);
     if (g->pin_fetch) cudaFreeHost(g->pin_fetch);
     if (g->pin_small) cudaFreeHost(g->pin_small);
-    if (g->pin_ev) cudaEventDestroy(g->pin_ev);
-    if (g->fetch_ev) cudaEventDestroy(g->fetch_ev);
+    for (int r = 0; r < apsp_graph::RING; ++r) {
+        if (g->pin_ev[r]) cudaEventDestroy(g->pin_ev[r]);
+        if (g->fetch_ev[r]) cudaEventDestroy(g->fetch_ev[r]);
+    }
     for (auto &r : g->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -287,6 +306,7 @@ template <typename T> Dev<T> dev_of(apsp_graph *g) {
     d.bmask_nb = g->bmask_nb;
     d.hbase = g->hbase;
     d.items = g->items;
+    d.icand = g->icand;
     d.pairs = g->pairs;
     d.pmin = g->pmin;
     d.pstamp = g->pstamp;
@@ -319,28 +339,69 @@ template <typename T> apsp_status check_weight(T &w) {
     return APSP_OK;
 }
 
-template <typename T> T &mirror(apsp_graph *g, int i, int j) { return ((T *)g->Wh.data())[(int64_t)i * g->cap + j]; }
+template <typename T> T *mirror_row(apsp_graph *g, int i) { return (T *)g->Wh.data() + (int64_t)i * g->cap; }
+template <typename T> T *mirror_col(apsp_graph *g, int j) { return (T *)g->WhT.data() + (int64_t)j * g->cap; }
 
-// Applies a pending device-input add_node to the host mirror (waits for the
-// small D2H copy of its weight vectors only).
-template <typename T> void settle_fetch(apsp_graph *g) {
-    if (g->fetch_pending_p < 0) return;
-    cudaEventSynchronize(g->fetch_ev);
-    const int p = g->fetch_pending_p;
-    const T *in = (const T *)g->pin_fetch;
-    const T *out = in + g->cap;
-    for (int t = 0; t < g->cap; ++t) {
-        T wi = inf_of<T>(), wo = inf_of<T>();
-        if (t != p && g->alive_h[t]) {
-            wi = in[t];
-            wo = out[t];
-            if (check_weight<T>(wi) != APSP_OK || check_weight<T>(wo) != APSP_OK) wi = wo = inf_of<T>();
-        }
-        mirror<T>(g, t, p) = wi;
-        mirror<T>(g, p, t) = wo;
+// W[i][j] of live i, j (see the mirror's layout in apsp_graph).
+template <typename T> T mirror_get(apsp_graph *g, int i, int j) {
+    if (i == j) return (T)0;
+    return g->add_seq[j] > g->add_seq[i] ? mirror_col<T>(g, j)[i] : mirror_row<T>(g, i)[j];
+}
+
+template <typename T> void mirror_edge(apsp_graph *g, int u, int v, T w) {
+    mirror_row<T>(g, u)[v] = w;
+    mirror_col<T>(g, v)[u] = w;
+    if (g->undirected) {
+        mirror_row<T>(g, v)[u] = w;
+        mirror_col<T>(g, u)[v] = w;
     }
-    mirror<T>(g, p, p) = (T)0;
-    g->fetch_pending_p = -1;
+}
+
+// Row and column of the node added at slot p from its raw weight vectors
+// (an invalid entry is read as missing; entries of slots that were not live
+// at the add are never read: a slot added later defines its own row and
+// column).
+template <typename T> void mirror_node(apsp_graph *g, int p, const T *in, const T *out) {
+    T *r = mirror_row<T>(g, p), *c = mirror_col<T>(g, p);
+    for (int t = 0; t < g->cap; ++t) {
+        T a = in[t], b = out[t];
+        if (check_weight<T>(a) != APSP_OK || check_weight<T>(b) != APSP_OK) a = b = inf_of<T>();
+        c[t] = a;
+        r[t] = b;
+    }
+    r[p] = c[p] = (T)0;
+}
+
+// Applies a device-input add_node to the mirror once its weight vectors have
+// reached the host (waits for that small D2H copy only).  Skipped when the
+// slot was added again since.
+template <typename T> void settle_one(apsp_graph *g, const apsp_graph::Fetch &f) {
+    cudaEventSynchronize(g->fetch_ev[f.ring]);
+    if (g->add_seq[f.p] != f.seq) return;
+    const T *in = (const T *)g->pin_fetch + (size_t)f.ring * 2 * g->cap;
+    mirror_node<T>(g, f.p, in, in + g->cap);
+}
+
+// All pending device-input adds (for callers that read the whole mirror).
+template <typename T> void settle_fetch(apsp_graph *g) {
+    while (!g->fetches.empty()) {
+        settle_one<T>(g, g->fetches.front());
+        g->fetches.pop_front();
+    }
+}
+
+// Only the pending adds of slots u and v, whose weights W[u][v] may need:
+// other updates read no mirror entry, so a device-input add does not stall
+// the host until an edge update touches the added node.
+template <typename T> void settle_for(apsp_graph *g, int u, int v) {
+    for (auto it = g->fetches.begin(); it != g->fetches.end();) {
+        if (it->p == u || it->p == v) {
+            settle_one<T>(g, *it);
+            it = g->fetches.erase(it);
+        } else {
+            ++it;
+        }
+    }
 }
 
 template <typename T> RepairCfg repair_cfg(apsp_graph *g, int n_before, float type_feat, float dw) {
@@ -399,6 +460,7 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->item_cap = (int32_t)(g->pair_cap / apsp::ITEM_PAIRS + ld);
     g->pairs = (int32_t *)dalloc(g, g->pair_cap * 4);
     g->items = (int4 *)dalloc(g, (size_t)g->item_cap * sizeof(int4));
+    g->icand = (int32_t *)dalloc(g, (size_t)2 * ld * sizeof(int32_t));
     g->unit_cap = (int32_t)std::min<int64_t>(g->pair_cap, (int64_t)1 << 30);
     g->pmin = (int32_t *)dalloc(g, g->pair_cap * 4);
     g->pstamp = (uint8_t *)dalloc(g, g->pair_cap);
@@ -412,16 +474,18 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
         if (!g->mm_mask) return APSP_E_NOMEM;
     }
     if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
-        !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->ctl || !g->model ||
+        !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->icand || !g->ctl || !g->model ||
         !g->pmin || !g->pstamp || !g->rstamp || !g->units || !g->hrows || !g->hunits || !g->hralloc || !g->rowcnt ||
         !g->hbase || !g->bmask)
         return APSP_E_NOMEM;
-    if (cudaMallocHost(&g->pin, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
-    if (cudaMallocHost(&g->pin_fetch, 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
+    if (cudaMallocHost(&g->pin, (size_t)apsp_graph::RING * 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
+    if (cudaMallocHost(&g->pin_fetch, (size_t)apsp_graph::RING * 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
     g->pin_small_bytes = std::max<int64_t>(sizeof(Ctl), 1 << 16);
     if (cudaMallocHost(&g->pin_small, g->pin_small_bytes) != cudaSuccess) return APSP_E_NOMEM;
-    cudaEventCreateWithFlags(&g->pin_ev, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&g->fetch_ev, cudaEventDisableTiming);
+    for (int r = 0; r < apsp_graph::RING; ++r) {
+        cudaEventCreateWithFlags(&g->pin_ev[r], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&g->fetch_ev[r], cudaEventDisableTiming);
+    }
 
     if ((e = apsp::setup_shapes<T>(g->lc, ld, g->undirected ? 1 : 0)) != cudaSuccess) return cuda_status(e);
     const LaunchCtx &c = g->lc;
@@ -454,6 +518,8 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->alive_h.assign(g->cap, 0);
     for (int i = 0; i < n; ++i) g->alive_h[i] = 1;
     g->Wh.assign((size_t)g->cap * g->cap * esz, 0);
+    g->WhT.assign((size_t)g->cap * g->cap * esz, 0);   // read only for slots added later
+    g->add_seq.assign(g->cap, 0);
     {
         T *wh = (T *)g->Wh.data();
         std::fill(wh, wh + (size_t)g->cap * g->cap, inf);
@@ -479,7 +545,6 @@ apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t
         if (!g->undirected) return APSP_E_ARG;
         in_w = out_w;
     }
-    settle_fetch<T>(g);
     const int p = pick_slot(g);
     if (p < 0) return APSP_E_CAPACITY;
     const int cap = g->cap;
@@ -494,35 +559,38 @@ apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t
             if (s2 != APSP_OK) return s2;
             if (g->undirected && !(a == b)) return APSP_E_ARG;
         }
-        if (g->pin_pending) cudaEventSynchronize(g->pin_ev);
-        T *pin_in = (T *)g->pin, *pin_out = pin_in + cap;
+        // a ring of pinned staging buffers: this waits only for the copy
+        // issued RING host-input adds ago
+        const int r = g->pin_next;
+        g->pin_next = (r + 1) % apsp_graph::RING;
+        if (g->pin_used[r]) cudaEventSynchronize(g->pin_ev[r]);
+        T *pin_in = (T *)g->pin + (size_t)r * 2 * cap, *pin_out = pin_in + cap;
         std::memcpy(pin_in, hi, cap * sizeof(T));
         std::memcpy(pin_out, ho, cap * sizeof(T));
         cudaMemcpyAsync(g->x, pin_in, cap * sizeof(T), cudaMemcpyHostToDevice, g->stream);
         cudaMemcpyAsync(g->y, pin_out, cap * sizeof(T), cudaMemcpyHostToDevice, g->stream);
-        cudaEventRecord(g->pin_ev, g->stream);
-        g->pin_pending = true;
+        cudaEventRecord(g->pin_ev[r], g->stream);
+        g->pin_used[r] = true;
         din = (const T *)g->x;
         dout = (const T *)g->y;
-        for (int t = 0; t < cap; ++t) {
-            T a = inf_of<T>(), b = inf_of<T>();
-            if (t != p && g->alive_h[t]) {
-                a = hi[t];
-                b = ho[t];
-                check_weight<T>(a);
-                check_weight<T>(b);
-            }
-            mirror<T>(g, t, p) = a;
-            mirror<T>(g, p, t) = b;
-        }
-        mirror<T>(g, p, p) = (T)0;
+        g->add_seq[p] = ++g->seq;
+        mirror_node<T>(g, p, hi, ho);
     } else {
         din = (const T *)in_w;
         dout = (const T *)out_w;
-        T *f_in = (T *)g->pin_fetch;
+        // the weights reach the mirror later (settle_one), without a wait here
+        if ((int)g->fetches.size() == apsp_graph::RING) {
+            settle_one<T>(g, g->fetches.front());
+            g->fetches.pop_front();
+        }
+        const int r = g->fetch_next;
+        g->fetch_next = (r + 1) % apsp_graph::RING;
+        T *f_in = (T *)g->pin_fetch + (size_t)r * 2 * cap;
         cudaMemcpyAsync(f_in, din, cap * sizeof(T), cudaMemcpyDeviceToHost, g->stream);
         cudaMemcpyAsync(f_in + cap, dout, cap * sizeof(T), cudaMemcpyDeviceToHost, g->stream);
-        cudaEventRecord(g->fetch_ev, g->stream);
+        cudaEventRecord(g->fetch_ev[r], g->stream);
+        g->add_seq[p] = ++g->seq;
+        g->fetches.push_back(apsp_graph::Fetch{p, g->add_seq[p], r});
     }
     g->hwm = std::max(g->hwm, p + 1);
     reset_ctl(g);
@@ -532,7 +600,6 @@ apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t
     if (e != cudaSuccess) return cuda_status(e);
     g->alive_h[p] = 1;
     g->n_live++;
-    if (device_input) g->fetch_pending_p = p;
     *new_id = p;
     g->last = apsp_stats{};
     g->last.op = APSP_OP_ADD;
@@ -586,7 +653,6 @@ template <typename T> apsp_status mm_repair(apsp_graph *g, int n_before) {
 }
 
 template <typename T> apsp_status remove_impl(apsp_graph *g, int v) {
-    settle_fetch<T>(g);
     if (v < 0 || v >= g->cap || !g->alive_h[v]) return APSP_E_NODE;
     reset_ctl(g);
     if (g->minimax) {
@@ -594,11 +660,7 @@ template <typename T> apsp_status remove_impl(apsp_graph *g, int v) {
         Dev<T> d = dev_of<T>(g);
         cudaError_t e = apsp::run_mm_detect<T>(g->lc, d, g->mm_mask, g->mm_words, 0, v, v, (T)0, (T)0);
         if (e != cudaSuccess) return cuda_status(e);
-        g->alive_h[v] = 0;
-        for (int t = 0; t < g->cap; ++t) {
-            mirror<T>(g, t, v) = inf_of<T>();
-            mirror<T>(g, v, t) = inf_of<T>();
-        }
+        g->alive_h[v] = 0;   // the mirror keeps the slot's rows until its next add
         g->n_live--;
         g->last = apsp_stats{};
         g->last.op = APSP_OP_REMOVE;
@@ -611,11 +673,7 @@ template <typename T> apsp_status remove_impl(apsp_graph *g, int v) {
     RepairCfg cfg = repair_cfg<T>(g, g->n_live, 1.0f / 3.0f, 0.0f);
     cudaError_t e = apsp::run_remove<T>(g->lc, d, v, cfg);
     if (e != cudaSuccess) return cuda_status(e);
-    g->alive_h[v] = 0;
-    for (int t = 0; t < g->cap; ++t) {
-        mirror<T>(g, t, v) = inf_of<T>();
-        mirror<T>(g, v, t) = inf_of<T>();
-    }
+    g->alive_h[v] = 0;   // the mirror keeps the slot's rows until its next add
     g->n_live--;
     g->last = apsp_stats{};
     g->last.op = APSP_OP_REMOVE;
@@ -627,14 +685,14 @@ template <typename T> apsp_status remove_impl(apsp_graph *g, int v) {
 }
 
 template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const void *wp) {
-    settle_fetch<T>(g);
     if (!wp) return APSP_E_ARG;
     if (u < 0 || v < 0 || u >= g->cap || v >= g->cap || !g->alive_h[u] || !g->alive_h[v]) return APSP_E_NODE;
+    settle_for<T>(g, u, v);
     if (u == v) return APSP_E_ARG;
     T w = *(const T *)wp;
     apsp_status s = check_weight<T>(w);
     if (s != APSP_OK) return s;
-    const T w_old = mirror<T>(g, u, v);
+    const T w_old = mirror_get<T>(g, u, v);
     g->last = apsp_stats{};
     g->last.node = u;
     g->last.node2 = v;
@@ -657,8 +715,7 @@ template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const v
             g->last.op = APSP_OP_INCREASE;
         }
         if (e != cudaSuccess) return cuda_status(e);
-        mirror<T>(g, u, v) = w;
-        if (g->undirected) mirror<T>(g, v, u) = w;
+        mirror_edge<T>(g, u, v, w);
         if (w < w_old) {
             Ctl c;
             apsp_status st = sync_ctl(g, &c);
@@ -680,8 +737,7 @@ template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const v
         g->last.path = -1;
     }
     if (e != cudaSuccess) return cuda_status(e);
-    mirror<T>(g, u, v) = w;
-    if (g->undirected) mirror<T>(g, v, u) = w;
+    mirror_edge<T>(g, u, v, w);
     return APSP_OK;
 }
 
@@ -852,7 +908,7 @@ apsp_status all_paths_impl(apsp_graph *g, int32_t u, int32_t v, int32_t *nodes, 
             const bool fp = std::is_same<T, float>::value;
             auto length = [&](const std::vector<int32_t> &small) {
                 double L = 0.0;
-                for (size_t k = 0; k + 1 < small.size(); ++k) L += (double)mirror<T>(g, cand[small[k]], cand[small[k + 1]]);
+                for (size_t k = 0; k + 1 < small.size(); ++k) L += (double)mirror_get<T>(g, cand[small[k]], cand[small[k + 1]]);
                 return L;
             };
             const double lim = fp ? length(psi) * (1.0 + (2.0 * K + 2.0) * 0x1p-24) : 0.0;
@@ -1146,6 +1202,8 @@ apsp_status apsp_last_stats(apsp_graph *g, apsp_stats *s) {
     } else if (op == APSP_OP_DECREASE) {
         s->sweep_rows = c.r_count;
         s->path = c.r_count > 0 ? APSP_PATH_SWEEP : APSP_PATH_TRIVIAL;
+    } else if (op == APSP_OP_ADD) {
+        s->reduce_rows = c.ins_narrow ? c.ins_nout + c.ins_nin : -1;
     }
     return st;
 }
@@ -1570,6 +1628,7 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
                 op.vec = (int64_t)vecs.size();
                 vecs.resize(vecs.size() + 2 * (size_t)span, inf_of<T>());
                 T *wi = vecs.data() + op.vec, *wo = wi + span;
+                T *mr = mirror_row<T>(g, p), *mc = mirror_col<T>(g, p);
                 for (int t = 0; t < g->cap; ++t) {
                     T a = inf_of<T>(), c = inf_of<T>();
                     if (t != p && g->alive_h[t]) {
@@ -1582,10 +1641,11 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
                         wi[t] = a;
                         wo[t] = c;
                     }
-                    mirror<T>(g, t, p) = a;
-                    mirror<T>(g, p, t) = c;
+                    mc[t] = a;
+                    mr[t] = c;
                 }
-                mirror<T>(g, p, p) = (T)0;
+                mr[p] = mc[p] = (T)0;
+                g->add_seq[p] = ++g->seq;
                 g->alive_h[p] = 1;
                 g->n_live++;
                 if (new_ids) new_ids[q] = p;
@@ -1594,15 +1654,11 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
                 op.a = it.u;
                 op.span = span_of(g);
                 g->alive_h[it.u] = 0;
-                for (int t = 0; t < g->cap; ++t) {
-                    mirror<T>(g, t, it.u) = inf_of<T>();
-                    mirror<T>(g, it.u, t) = inf_of<T>();
-                }
                 g->n_live--;
             } else {
                 T w;
                 batch_weight<T>(it.w, &w);
-                const T w_old = mirror<T>(g, it.u, it.v);
+                const T w_old = mirror_get<T>(g, it.u, it.v);
                 if (w == w_old) continue;
                 op.op = w < w_old ? apsp::BOP_DECREASE : apsp::BOP_INCREASE;
                 op.a = it.u;
@@ -1610,7 +1666,7 @@ apsp_status batch_launch(apsp_batch *b, apsp_graph *const *graphs, int n_graphs,
                 op.span = span_of(g);
                 op.w_bits = bits_of<T>(w);
                 op.w_old_bits = bits_of<T>(w_old);
-                mirror<T>(g, it.u, it.v) = w;
+                mirror_edge<T>(g, it.u, it.v, w);
             }
             gspan = std::max(gspan, op.span);
             ops.push_back(op);
@@ -1996,7 +2052,6 @@ template <typename T> void server_loop(apsp_server *s) {
             } else if (it.u < 0 || it.v < 0 || it.u >= gr->cap || it.v >= gr->cap) {
                 st = APSP_E_NODE;
             } else {
-                settle_fetch<T>(gr);
                 cudaMemcpyAsync(qbuf + gi, (T *)gr->D + (int64_t)it.u * gr->ld + it.v, sizeof(T),
                                 cudaMemcpyDeviceToHost, gr->stream);
             }

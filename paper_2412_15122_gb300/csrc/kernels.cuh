@@ -47,6 +47,7 @@ template <typename T> struct Dev {
     int32_t bmask_nb;
     long long *hbase;         // detection: first pair slot per unit (-1: none)
     int4 *items;              // (row, first pair, pair count | row's pair count << 8, row's first pair)
+    int32_t *icand;           // node insertion: candidate rows of Corollary 1 [0, ld), columns of Corollary 2 [ld, 2 ld)
     int32_t *pairs;           // affected column per pair, grouped by row (columns ascending)
     int32_t *pmin;            // per pair: first-pass minimum as an ordered key
     uint8_t *pstamp;          // per pair: last pass that lowered it (0: none yet)
@@ -234,33 +235,153 @@ __global__ void __launch_bounds__(FW_THREADS, 2) k_fw_p3(T *D, int64_t ld, int k
     fw_phase3_tile<T, M>(D, ld, kb, nb, blockIdx.x, sm);
 }
 
+__device__ __forceinline__ int32_t max_of(int32_t a, int32_t b) { return max(a, b); }
+__device__ __forceinline__ float max_of(float a, float b) { return fmaxf(a, b); }
+
 // --------------------------------------------------------------------------
 // Adding a node p (Section 3.1)
 // --------------------------------------------------------------------------
 
-// Mask the new node's weights (dead slots and p itself -> missing), validate
-// them, and reset the two reduction vectors.
+// Which rows (columns) of D can attain the new node's minima.  With t0 the
+// slot of the lightest out-edge of p and E0 = max over live j of D[t0][j],
+// every column j has out[j] <= w(p, t0) + D[t0][j] <= w(p, t0) + E0, while a
+// row t contributes w(p, t) + D[t][j] >= w(p, t) (D >= 0).  Rows with
+// w(p, t) > w(p, t0) + E0 therefore never attain a minimum and Corollary 1
+// needs only the rows with w(p, t) <= w(p, t0) + E0; likewise Corollary 2
+// needs only the columns r with w(r, p) <= w(r1, p) + E1, r1 the lightest
+// in-edge and E1 = max over live i of D[i][r1].  The comparisons are exact
+// (in double for fp32 weights) and rounding is monotone, so the minima over
+// the candidates are bit-identical to the minima over all rows.  When some
+// live node is unreachable the bound is infinite and every row stays a
+// candidate.  One CTA (the last of the prep kernel, INS_PREP_THREADS wide)
+// builds both lists.
+constexpr int INS_PREP_THREADS = 1024;   // block of k_insert_prep (its last block selects the candidates)
+
 template <typename T>
-__global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int cap, int p) {
-    pdl_enter();
+__device__ void insert_candidates(const Dev<T> &d, int p) {
     using M = MinPlus<T>;
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= d.span) return;
-    uint32_t err = 0;
-    T wi = M::inf(), wo = M::inf();
-    if (j < cap && j != p && d.alive[j]) {
-        wi = sanitize_val<T>(in_raw[j], err);
-        wo = sanitize_val<T>(out_raw[j], err);
-        if (err) { wi = M::inf(); wo = M::inf(); }
+    using V4 = typename M::V4;
+    __shared__ int nsel[2];
+    __shared__ T emax[2][INS_PREP_THREADS / 32];
+    const int nv = d.span / 4, lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // span is a multiple of 32
+    const unsigned long long ao = *(volatile const unsigned long long *)&d.ctl->ins_amin_out;
+    const unsigned long long ai = *(volatile const unsigned long long *)&d.ctl->ins_amin_in;
+    const int t0 = ao ? (int)(uint32_t)(~ao) : -1, r1 = ai ? (int)(uint32_t)(~ai) : -1;
+    if (threadIdx.x < 2) nsel[threadIdx.x] = 0;
+    const V4 *row0 = reinterpret_cast<const V4 *>(d.D + (int64_t)max(t0, 0) * d.ld);
+    const V4 *col1 = reinterpret_cast<const V4 *>((d.DT ? d.DT : d.D) + (int64_t)max(r1, 0) * d.ld);
+    const int4 *al4 = reinterpret_cast<const int4 *>(d.alive);
+    T e0 = (T)0, e1 = (T)0;
+    for (int c4 = threadIdx.x; c4 < nv; c4 += blockDim.x) {
+        const int4 a = __ldcg(al4 + c4);
+        const V4 x = __ldcg(row0 + c4), y = __ldcg(col1 + c4);
+        const int j = 4 * c4;
+        const bool l0 = a.x && j != p, l1 = a.y && j + 1 != p, l2 = a.z && j + 2 != p, l3 = a.w && j + 3 != p;
+        if (t0 >= 0)
+            e0 = max_of(max_of(max_of(e0, l0 ? x.x : (T)0), max_of(l1 ? x.y : (T)0, l2 ? x.z : (T)0)), l3 ? x.w : (T)0);
+        if (r1 >= 0)
+            e1 = max_of(max_of(max_of(e1, l0 ? y.x : (T)0), max_of(l1 ? y.y : (T)0, l2 ? y.z : (T)0)), l3 ? y.w : (T)0);
     }
-    d.w_in[j] = wi;
-    d.w_out[j] = wo;
-    d.vin_k[j] = M::key(M::inf());
-    d.vout_k[j] = M::key(M::inf());
-    if (err) atomicOr(&d.ctl->err, err);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e0 = max_of(e0, __shfl_xor_sync(0xffffffffu, e0, o));
+        e1 = max_of(e1, __shfl_xor_sync(0xffffffffu, e1, o));
+    }
+    if (lane == 0) {
+        emax[0][w] = e0;
+        emax[1][w] = e1;
+    }
+    __syncthreads();
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        e0 = max_of(e0, emax[0][k]);
+        e1 = max_of(e1, emax[1][k]);
+    }
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    const double thr_o = t0 < 0 ? -1.0 : (M::finite(e0) ? (double)__ldcg(d.w_out + t0) + (double)e0 : inf);
+    const double thr_i = r1 < 0 ? -1.0 : (M::finite(e1) ? (double)__ldcg(d.w_in + r1) + (double)e1 : inf);
+    const V4 *wo4 = reinterpret_cast<const V4 *>(d.w_out);
+    const V4 *wi4 = reinterpret_cast<const V4 *>(d.w_in);
+    const unsigned below = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < nv; c0 += blockDim.x) {
+        const int c4 = c0 + threadIdx.x;
+        V4 wo = {}, wi = {};
+        if (c4 < nv) {
+            wo = __ldcg(wo4 + c4);
+            wi = __ldcg(wi4 + c4);
+        }
+        const T wov[4] = {wo.x, wo.y, wo.z, wo.w}, wiv[4] = {wi.x, wi.y, wi.z, wi.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const bool so = c4 < nv && M::finite(wov[e]) && (double)wov[e] <= thr_o;
+            const bool si = c4 < nv && M::finite(wiv[e]) && (double)wiv[e] <= thr_i;
+            const unsigned bo = __ballot_sync(0xffffffffu, so), bi = __ballot_sync(0xffffffffu, si);
+            int baseo = 0, basei = 0;
+            if (lane == 0) {
+                if (bo) baseo = atomicAdd(&nsel[0], __popc(bo));
+                if (bi) basei = atomicAdd(&nsel[1], __popc(bi));
+            }
+            baseo = __shfl_sync(0xffffffffu, baseo, 0);
+            basei = __shfl_sync(0xffffffffu, basei, 0);
+            if (so) d.icand[baseo + __popc(bo & below)] = 4 * c4 + e;
+            if (si) d.icand[d.ld + basei + __popc(bi & below)] = 4 * c4 + e;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.ctl->ins_nout = nsel[0];
+        d.ctl->ins_nin = nsel[1];
+        // the candidates' rows and columns cost at most an eighth of a full pass
+        d.ctl->ins_narrow = (int64_t)(nsel[0] + nsel[1]) * 8 <= (int64_t)d.span;
+    }
 }
 
-// One pass over D computing both vectors of the new node:
+// Mask the new node's weights (dead slots and p itself -> missing), validate
+// them, and reset the two reduction vectors.  With `cand` (min-plus graphs),
+// also the argmin of each weight vector, and the last CTA to finish selects
+// the reduction's candidates (insert_candidates).
+template <typename T>
+__global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int cap, int p, int cand) {
+    pdl_enter();
+    using M = MinPlus<T>;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t err = 0;
+    T wi = M::inf(), wo = M::inf();
+    if (j < d.span) {
+        if (j < cap && j != p && d.alive[j]) {
+            wi = sanitize_val<T>(in_raw[j], err);
+            wo = sanitize_val<T>(out_raw[j], err);
+            if (err) { wi = M::inf(); wo = M::inf(); }
+        }
+        d.w_in[j] = wi;
+        d.w_out[j] = wo;
+        d.vin_k[j] = M::key(M::inf());
+        d.vout_k[j] = M::key(M::inf());
+        if (err) atomicOr(&d.ctl->err, err);
+    }
+    if (!cand) return;
+    unsigned long long ko = M::finite(wo) ? ~(((unsigned long long)(uint32_t)M::key(wo) << 32) | (uint32_t)j) : 0ull;
+    unsigned long long ki = M::finite(wi) ? ~(((unsigned long long)(uint32_t)M::key(wi) << 32) | (uint32_t)j) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ko = max(ko, __shfl_xor_sync(0xffffffffu, ko, o));
+        ki = max(ki, __shfl_xor_sync(0xffffffffu, ki, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (ko) atomicMax(&d.ctl->ins_amin_out, ko);
+        if (ki) atomicMax(&d.ctl->ins_amin_in, ki);
+    }
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&d.ctl->ins_done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    insert_candidates<T>(d, p);
+}
+
+// One pass over D computing both vectors of the new node (when the
+// candidate bound leaves too many rows):
 //   out[r] = min_t w(p, t) + D[t][r]     (Corollary 1, column reduction)
 //   in[t]  = min_r D[t][r] + w(r, p)     (Corollary 2, row reduction)
 // Grid: (column band of INS_CB columns) x (row range); the launcher picks the
@@ -269,12 +390,68 @@ __global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int c
 // ordered keys (one per row per band, one per column per row range).
 constexpr int INS_CB = 512;
 
+// The same two reductions over the candidates only (insert_candidates):
+// CTA (band, k) takes candidates k, k + gridDim.y, ... (a warp each); a
+// candidate row t adds w(p, t) + D[t][band] to out[band], a candidate column
+// r adds D[band][r] + w(r, p) (row r of Dt) to in[band].  Partial minima
+// meet through atomicMin on ordered keys as in the full pass.
+template <typename T>
+__device__ void insert_reduce_candidates(const Dev<T> &d, T (*red)[INS_CB]) {
+    using M = MinPlus<T>;
+    using V4 = typename M::V4;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c0 = blockIdx.x * INS_CB;
+    const int nout = *(volatile const int32_t *)&d.ctl->ins_nout;
+    const int nc = nout + *(volatile const int32_t *)&d.ctl->ins_nin;
+    T ao[16], ai[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) ao[e] = ai[e] = M::inf();
+    for (int k = blockIdx.y + gridDim.y * w; k < nc; k += gridDim.y * (blockDim.x >> 5)) {
+        const bool out = k < nout;
+        const int s = out ? __ldcg(d.icand + k) : __ldcg(d.icand + d.ld + (k - nout));
+        const T wt = out ? __ldcg(d.w_out + s) : __ldcg(d.w_in + s);
+        const T *src = (out || !d.DT ? d.D : d.DT) + (int64_t)s * d.ld + c0 + lane * 4;
+        V4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (c0 + q * 128 + lane * 4 < d.span) v[q] = __ldcg(reinterpret_cast<const V4 *>(src + q * 128));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (c0 + q * 128 + lane * 4 >= d.span) continue;
+            const T e4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (out) ao[q * 4 + e] = M::add_min(wt, e4[e], ao[q * 4 + e]);
+                else ai[q * 4 + e] = M::add_min(e4[e], wt, ai[q * 4 + e]);
+            }
+        }
+    }
+    for (int side = 0; side < 2; ++side) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) red[w][q * 128 + lane * 4 + e] = side ? ai[q * 4 + e] : ao[q * 4 + e];
+        __syncthreads();
+        for (int c = threadIdx.x; c < INS_CB; c += blockDim.x) {
+            T m = red[0][c];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) m = M::mn(m, red[k][c]);
+            if (c0 + c < d.span && M::finite(m)) atomicMin(side ? &d.vin_k[c0 + c] : &d.vout_k[c0 + c], M::key(m));
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_insert_reduce(Dev<T> d, int rows_per_cta) {
     pdl_enter();
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     __shared__ T red[8][INS_CB];
+    if (*(volatile const int32_t *)&d.ctl->ins_narrow) {
+        insert_reduce_candidates<T>(d, red);
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int c0 = blockIdx.x * INS_CB;
     const int r0 = blockIdx.y * rows_per_cta;
@@ -566,8 +743,6 @@ constexpr int DET_MAXB = 32;    // 1024-column batches a row may have (rows <= 3
 template <typename T> __device__ __forceinline__ T unreachable_leg();
 template <> __device__ __forceinline__ int32_t unreachable_leg<int32_t>() { return INF_I32 + 1; }
 template <> __device__ __forceinline__ float unreachable_leg<float>() { return __int_as_float(0x7f800000); }
-__device__ __forceinline__ int32_t max_of(int32_t a, int32_t b) { return max(a, b); }
-__device__ __forceinline__ float max_of(float a, float b) { return fmaxf(a, b); }
 
 // Affected-pair detection.
 // kind 0: removal of node a (rows: every live row != a).  Affected pairs are

@@ -82,7 +82,7 @@ template <typename T> cudaError_t run_fw(const LaunchCtx &c, const Dev<T> &d) {
 template <typename T>
 cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
     cudaError_t e;
-    if ((e = launch_s(c, "insert_prep", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_insert_prep<T>, d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "insert_prep", [&] { return pdl(c.stream, cdiv(d.span, INS_PREP_THREADS), INS_PREP_THREADS, 0, k_insert_prep<T>, d, in_raw, out_raw, cap, p, 1); })) != cudaSuccess) return e;
     // exactly one wave (never a partial second one): the resident CTAs split
     // into column bands x row ranges
     const int bands = cdiv(d.span, INS_CB);
@@ -335,7 +335,7 @@ template <typename T> cudaError_t run_mm_fw(const LaunchCtx &c, const Dev<T> &d)
 template <typename T>
 cudaError_t run_mm_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
     cudaError_t e;
-    if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p); })) != cudaSuccess) return e;
+    if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p, 0); })) != cudaSuccess) return e;
     const int bands = cdiv(d.span, MM_CB);
     int ranges = std::max(1, (3 * c.num_sms + bands - 1) / bands);
     ranges = std::min(ranges, std::max(1, cdiv(d.span, 8)));

@@ -261,6 +261,7 @@ template <typename T>
 __device__ void insert_candidates(const Dev<T> &d, int p) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
+    constexpr int U = 3;   // vectors per thread held at once (span <= 12288 in one round)
     __shared__ int nsel[2];
     __shared__ T emax[2][INS_PREP_THREADS / 32];
     const int nv = d.span / 4, lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // span is a multiple of 32
@@ -271,17 +272,47 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
     const V4 *row0 = reinterpret_cast<const V4 *>(d.D + (int64_t)max(t0, 0) * d.ld);
     const V4 *col1 = reinterpret_cast<const V4 *>((d.DT ? d.DT : d.D) + (int64_t)max(r1, 0) * d.ld);
     const int4 *al4 = reinterpret_cast<const int4 *>(d.alive);
+    const V4 *wo4 = reinterpret_cast<const V4 *>(d.w_out);
+    const V4 *wi4 = reinterpret_cast<const V4 *>(d.w_in);
     T e0 = (T)0, e1 = (T)0;
-    for (int c4 = threadIdx.x; c4 < nv; c4 += blockDim.x) {
-        const int4 a = __ldcg(al4 + c4);
-        const V4 x = __ldcg(row0 + c4), y = __ldcg(col1 + c4);
-        const int j = 4 * c4;
-        const bool l0 = a.x && j != p, l1 = a.y && j + 1 != p, l2 = a.z && j + 2 != p, l3 = a.w && j + 3 != p;
-        if (t0 >= 0)
-            e0 = max_of(max_of(max_of(e0, l0 ? x.x : (T)0), max_of(l1 ? x.y : (T)0, l2 ? x.z : (T)0)), l3 ? x.w : (T)0);
-        if (r1 >= 0)
-            e1 = max_of(max_of(max_of(e1, l0 ? y.x : (T)0), max_of(l1 ? y.y : (T)0, l2 ? y.z : (T)0)), l3 ? y.w : (T)0);
+    // E0 = max over live j of D[t0][j], E1 = max over live i of D[i][r1];
+    // U vectors of each array per thread are in flight together
+    for (int c0 = 0; c0 < nv; c0 += U * (int)blockDim.x) {
+        int4 a[U];
+        V4 x[U], y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c4 = c0 + u * blockDim.x + threadIdx.x;
+            if (c4 < nv) {
+                a[u] = __ldcg(al4 + c4);
+                x[u] = __ldcg(row0 + c4);
+                y[u] = __ldcg(col1 + c4);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c4 = c0 + u * blockDim.x + threadIdx.x;
+            if (c4 >= nv) continue;
+            const int j = 4 * c4;
+            const bool l0 = a[u].x && j != p, l1 = a[u].y && j + 1 != p, l2 = a[u].z && j + 2 != p, l3 = a[u].w && j + 3 != p;
+            e0 = max_of(max_of(max_of(e0, l0 ? x[u].x : (T)0), max_of(l1 ? x[u].y : (T)0, l2 ? x[u].z : (T)0)),
+                        l3 ? x[u].w : (T)0);
+            e1 = max_of(max_of(max_of(e1, l0 ? y[u].x : (T)0), max_of(l1 ? y[u].y : (T)0, l2 ? y[u].z : (T)0)),
+                        l3 ? y[u].w : (T)0);
+        }
     }
+    // the weights the compaction tests, in flight during the reduction
+    V4 wo[U], wi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int c4 = u * blockDim.x + threadIdx.x;
+        if (c4 < nv) {
+            wo[u] = __ldcg(wo4 + c4);
+            wi[u] = __ldcg(wi4 + c4);
+        }
+    }
+    if (t0 < 0) e0 = (T)0;
+    if (r1 < 0) e1 = (T)0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         e0 = max_of(e0, __shfl_xor_sync(0xffffffffu, e0, o));
@@ -299,31 +330,39 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     const double thr_o = t0 < 0 ? -1.0 : (M::finite(e0) ? (double)__ldcg(d.w_out + t0) + (double)e0 : inf);
     const double thr_i = r1 < 0 ? -1.0 : (M::finite(e1) ? (double)__ldcg(d.w_in + r1) + (double)e1 : inf);
-    const V4 *wo4 = reinterpret_cast<const V4 *>(d.w_out);
-    const V4 *wi4 = reinterpret_cast<const V4 *>(d.w_in);
     const unsigned below = (1u << lane) - 1u;
-    for (int c0 = 0; c0 < nv; c0 += blockDim.x) {
-        const int c4 = c0 + threadIdx.x;
-        V4 wo = {}, wi = {};
-        if (c4 < nv) {
-            wo = __ldcg(wo4 + c4);
-            wi = __ldcg(wi4 + c4);
-        }
-        const T wov[4] = {wo.x, wo.y, wo.z, wo.w}, wiv[4] = {wi.x, wi.y, wi.z, wi.w};
+    for (int c0 = 0; c0 < nv; c0 += U * (int)blockDim.x) {
+        if (c0 > 0) {   // spans above U * 4 * blockDim.x slots
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const bool so = c4 < nv && M::finite(wov[e]) && (double)wov[e] <= thr_o;
-            const bool si = c4 < nv && M::finite(wiv[e]) && (double)wiv[e] <= thr_i;
-            const unsigned bo = __ballot_sync(0xffffffffu, so), bi = __ballot_sync(0xffffffffu, si);
-            int baseo = 0, basei = 0;
-            if (lane == 0) {
-                if (bo) baseo = atomicAdd(&nsel[0], __popc(bo));
-                if (bi) basei = atomicAdd(&nsel[1], __popc(bi));
+            for (int u = 0; u < U; ++u) {
+                const int c4 = c0 + u * blockDim.x + threadIdx.x;
+                if (c4 < nv) {
+                    wo[u] = __ldcg(wo4 + c4);
+                    wi[u] = __ldcg(wi4 + c4);
+                }
             }
-            baseo = __shfl_sync(0xffffffffu, baseo, 0);
-            basei = __shfl_sync(0xffffffffu, basei, 0);
-            if (so) d.icand[baseo + __popc(bo & below)] = 4 * c4 + e;
-            if (si) d.icand[d.ld + basei + __popc(bi & below)] = 4 * c4 + e;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c4 = c0 + u * blockDim.x + threadIdx.x;
+            const bool in = c4 < nv;
+            const T wov[4] = {wo[u].x, wo[u].y, wo[u].z, wo[u].w}, wiv[4] = {wi[u].x, wi[u].y, wi[u].z, wi[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool so = in && M::finite(wov[e]) && (double)wov[e] <= thr_o;
+                const bool si = in && M::finite(wiv[e]) && (double)wiv[e] <= thr_i;
+                const unsigned bo = __ballot_sync(0xffffffffu, so), bi = __ballot_sync(0xffffffffu, si);
+                if (!(bo | bi)) continue;
+                int baseo = 0, basei = 0;
+                if (lane == 0) {
+                    if (bo) baseo = atomicAdd(&nsel[0], __popc(bo));
+                    if (bi) basei = atomicAdd(&nsel[1], __popc(bi));
+                }
+                baseo = __shfl_sync(0xffffffffu, baseo, 0);
+                basei = __shfl_sync(0xffffffffu, basei, 0);
+                if (so) d.icand[baseo + __popc(bo & below)] = 4 * c4 + e;
+                if (si) d.icand[d.ld + basei + __popc(bi & below)] = 4 * c4 + e;
+            }
         }
     }
     __syncthreads();

@@ -111,6 +111,7 @@ struct apsp_graph {
     };
     std::deque<Fetch> fetches;       // device-input adds not yet in the mirror, oldest first
     int fetch_next = 0;
+    apsp::IncGraph incg;             // edge increase as one CUDA graph (built on first use)
     void *pin_small = nullptr;   // pinned scratch for queries / control block
     int64_t pin_small_bytes = 0;
 
@@ -241,6 +242,7 @@ bool ensure_buf(apsp_graph *g, void **p, int64_t *have, int64_t bytes) {
 
 void release(apsp_graph *g) {
     cudaStreamSynchronize(g->stream);
+    apsp::destroy_increase_graph(&g->incg);
     for (auto &a : g->allocs) {
         if (g->free_fn) g->free_fn(a.first, a.second, (void *)g->stream, g->alloc_ctx);
         else cudaFree(a.first);
@@ -461,6 +463,8 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->pairs = (int32_t *)dalloc(g, g->pair_cap * 4);
     g->items = (int4 *)dalloc(g, (size_t)g->item_cap * sizeof(int4));
     g->icand = (int32_t *)dalloc(g, (size_t)2 * ld * sizeof(int32_t));
+    g->incg.args = dalloc(g, 256);
+    static_assert(sizeof(apsp::UpdArgs<float>) <= 256 && sizeof(apsp::UpdArgs<int32_t>) <= 256, "update argument block");
     g->unit_cap = (int32_t)std::min<int64_t>(g->pair_cap, (int64_t)1 << 30);
     g->pmin = (int32_t *)dalloc(g, g->pair_cap * 4);
     g->pstamp = (uint8_t *)dalloc(g, g->pair_cap);
@@ -474,7 +478,7 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
         if (!g->mm_mask) return APSP_E_NOMEM;
     }
     if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
-        !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->icand || !g->ctl || !g->model ||
+        !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->icand || !g->incg.args || !g->ctl || !g->model ||
         !g->pmin || !g->pstamp || !g->rstamp || !g->units || !g->hrows || !g->hunits || !g->hralloc || !g->rowcnt ||
         !g->hbase || !g->bmask)
         return APSP_E_NOMEM;
@@ -702,10 +706,10 @@ template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const v
         g->last.path = APSP_PATH_NONE;
         return APSP_OK;
     }
-    reset_ctl(g);
     Dev<T> d = dev_of<T>(g);
     cudaError_t e;
     if (g->minimax) {
+        reset_ctl(g);
         if (w < w_old) {
             e = apsp::run_mm_decrease<T>(g->lc, d, u, v, w);
             g->last.op = APSP_OP_DECREASE;
@@ -725,6 +729,7 @@ template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const v
         return mm_repair<T>(g, g->n_live);
     }
     if (w < w_old) {
+        reset_ctl(g);
         e = apsp::run_decrease<T>(g->lc, d, u, v, w);
         g->last.op = APSP_OP_DECREASE;
         g->last.path = APSP_PATH_SWEEP;
@@ -732,7 +737,14 @@ template <typename T> apsp_status edge_impl(apsp_graph *g, int u, int v, const v
         float dw = (std::isfinite((double)w) && (double)w < apsp::INF_I32 && (double)w_old > 0)
                        ? (float)(((double)w - (double)w_old) / (double)w_old) : 1.0f;
         RepairCfg cfg = repair_cfg<T>(g, g->n_live, 1.0f, dw);
-        e = apsp::run_increase<T>(g->lc, d, u, v, w_old, w, cfg);
+        // the graph form (inc_graph.cuh) covers the default list mode without
+        // per-kernel profiling or the measured Algorithm 12 list
+        if (cfg.list_mode == 0 && !cfg.grown_flag && !g->prof) {
+            e = apsp::launch_increase_graph<T>(g->lc, d, &g->incg, offsetof(Ctl, err), u, v, w_old, w, cfg);
+        } else {
+            reset_ctl(g);
+            e = apsp::run_increase<T>(g->lc, d, u, v, w_old, w, cfg);
+        }
         g->last.op = APSP_OP_INCREASE;
         g->last.path = -1;
     }

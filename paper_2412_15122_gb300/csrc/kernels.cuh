@@ -748,8 +748,7 @@ __global__ void k_rm_gather(Dev<T> d, int k) {
 }
 
 template <typename T>
-__global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
-    pdl_enter();
+__device__ __forceinline__ void k_inc_prepass_body(Dev<T> d, int u, int v, T w_old, T w_new) {
     using M = MinPlus<T>;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool tight_edge = M::tight(w_old, d.D[(int64_t)u * d.ld + v]);
@@ -775,6 +774,12 @@ __global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
         }
     }
     warp_append(in_r, i, d.rlist, &d.ctl->r_count);
+}
+
+template <typename T>
+__global__ void k_inc_prepass(Dev<T> d, int u, int v, T w_old, T w_new) {
+    pdl_enter();
+    k_inc_prepass_body<T>(d, u, v, w_old, w_new);
 }
 
 constexpr int DET_MAXB = 32;    // 1024-column batches a row may have (rows <= 32768 columns)
@@ -1026,9 +1031,8 @@ __device__ __forceinline__ void tombstone_entry(const Dev<T> &d, int k, int t) {
 // here reads row or column a (column a is never listed) and no listed pair
 // lies in them.
 template <typename T, bool TWO, int FILTER>
-__global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new,
+__device__ __forceinline__ void k_det_write_body(Dev<T> d, int kind, int a, T w_old, T w_new,
                                                                       const uint32_t *umask) {
-    pdl_enter();
     if (kind == 0)
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.span; t += gridDim.x * blockDim.x)
             tombstone_entry<T>(d, a, t);
@@ -1105,6 +1109,13 @@ __global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d
     }
 }
 
+template <typename T, bool TWO, int FILTER>
+__global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d, int kind, int a, T w_old, T w_new,
+                                                                      const uint32_t *umask) {
+    pdl_enter();
+    k_det_write_body<T, TWO, FILTER>(d, kind, a, w_old, w_new, umask);
+}
+
 // One warp per row, rows assigned round-robin; the legs are staged once per
 // CTA in shared memory (the removed node's own column as unreachable, so its
 // D[a][a] = 0 never makes a row look tight).  A lane streams 8 vectors at a
@@ -1114,8 +1125,7 @@ __global__ void __launch_bounds__(256, FILTER == 1 ? 2 : 4) k_det_write(Dev<T> d
 // registers (lane t: its t-th flagged row and batch mask) and appends them
 // to the hit list with one atomic when it is done or holds 32.
 template <typename T, bool TWO>
-__global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, T w_old) {
-    pdl_enter();
+__device__ __forceinline__ void k_det_scan_body(Dev<T> d, int kind, int a, T w_old) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1253,6 +1263,12 @@ __global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, 
         }
     }
     if (nh) flush();
+}
+
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(256, 4) k_det_scan(Dev<T> d, int kind, int a, T w_old) {
+    pdl_enter();
+    k_det_scan_body<T, TWO>(d, kind, a, w_old);
 }
 
 
@@ -1596,7 +1612,7 @@ __device__ inline void repair_record(Ctl *ctl, int reason, float cost, float pw,
 // launches no cold kernel; the first pass, which wants the shared memory for
 // its copy ring, is the separate k_repair_p1.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_repair_main(Dev<T> d, RepairCfg cfg) {
+__device__ __forceinline__ void repair_main_body(Dev<T> d, const RepairCfg &cfg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float cost, pw, pc;
     int n_items;
@@ -1608,6 +1624,11 @@ __global__ void __launch_bounds__(256, 2) k_repair_main(Dev<T> d, RepairCfg cfg)
         return;
     }
     repair_warm<T>(d);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_repair_main(Dev<T> d, RepairCfg cfg) {
+    repair_main_body<T>(d, cfg);
 }
 
 }  // namespace apsp

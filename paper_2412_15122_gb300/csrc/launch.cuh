@@ -146,6 +146,7 @@ static cudaError_t run_detect(const LaunchCtx &c, const Dev<T> &d, int kind, int
 struct CoopChain {
     std::mutex mu;
     cudaEvent_t last[64] = {};
+    cudaStream_t last_stream[64] = {};   // stream order already serialises work on the same stream
 };
 inline CoopChain &coop_chain() {
     static CoopChain c;
@@ -161,10 +162,11 @@ template <typename F> static cudaError_t coop_launch(cudaStream_t stream, F &&la
     std::lock_guard<std::mutex> lock(cc.mu);
     if (!cc.last[dev]) {
         if ((e = cudaEventCreateWithFlags(&cc.last[dev], cudaEventDisableTiming)) != cudaSuccess) return e;
-    } else if ((e = cudaStreamWaitEvent(stream, cc.last[dev], 0)) != cudaSuccess) {
+    } else if (cc.last_stream[dev] != stream && (e = cudaStreamWaitEvent(stream, cc.last[dev], 0)) != cudaSuccess) {
         return e;
     }
     if ((e = launch_fn()) != cudaSuccess) return e;
+    cc.last_stream[dev] = stream;
     return cudaEventRecord(cc.last[dev], stream);
 }
 
@@ -214,6 +216,114 @@ cudaError_t run_increase(const LaunchCtx &c, const Dev<T> &d, int u, int v, T w_
     if ((e = run_detect<T>(c, d, 1, u, w_old, w_new, cfg, "detect_increase")) != cudaSuccess) return e;
     if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
     return run_grown<T>(c, d, 1, w_old, cfg);
+}
+
+template <typename F> static cudaError_t allow_max_smem(F *kernel);
+
+// Graph: clear the control block -> prepass (sets the branch) -> IF tight:
+// scan -> reservation -> writes -> first pass -> cooperative repair.
+template <typename T, bool TWO>
+static cudaError_t build_increase_graph(const LaunchCtx &c, const Dev<T> &d, IncGraph *ig, size_t ctl_bytes) {
+    cudaError_t e;
+    if ((e = allow_max_smem(k_det_scan_g<T, TWO>)) != cudaSuccess) return e;
+    if ((e = allow_max_smem(k_repair_main_g<T>)) != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_repair_main_g<T>, 256, c.repair_smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid_main = std::min(c.repair_grid, per_sm * c.num_sms);
+    cudaGraph_t g = nullptr;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+    auto fail = [&](cudaError_t x) {
+        cudaGraphDestroy(g);
+        return x;
+    };
+    cudaGraphNode_t clear = nullptr, pre = nullptr, cond = nullptr;
+    cudaMemsetParams mp = {};
+    mp.dst = (void *)d.ctl;
+    mp.value = 0;
+    mp.elementSize = 1;
+    mp.width = ctl_bytes;
+    mp.height = 1;
+    if ((e = cudaGraphAddMemsetNode(&clear, g, nullptr, 0, &mp)) != cudaSuccess) return fail(e);
+    cudaGraphConditionalHandle branch = 0;
+    if ((e = cudaGraphConditionalHandleCreate(&branch, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return fail(e);
+    Dev<T> dd = d;
+    UpdArgs<T> *ua = (UpdArgs<T> *)ig->args;
+    int u = 0, v = 0;
+    T wo = (T)0, wn = (T)0;
+    RepairCfg cf{};
+    void *pp[] = {&dd, &u, &v, &wo, &wn, &cf, &ua, &branch};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_inc_prepass_g<T>;
+    kp.gridDim = dim3(cdiv(d.span, 256));
+    kp.blockDim = dim3(256);
+    kp.kernelParams = pp;
+    if ((e = cudaGraphAddKernelNode(&pre, g, &clear, 1, &kp)) != cudaSuccess) return fail(e);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = branch;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&cond, g, &pre, nullptr, 1, &cp)) != cudaSuccess) return fail(e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t prev = nullptr, node = nullptr;
+    void *pa[] = {&dd};
+    void *pb[] = {&dd, &ua};
+    auto add = [&](void *func, int grid, size_t smem, void **params) {
+        cudaKernelNodeParams q = {};
+        q.func = func;
+        q.gridDim = dim3(grid);
+        q.blockDim = dim3(256);
+        q.sharedMemBytes = (unsigned)smem;
+        q.kernelParams = params;
+        cudaError_t x = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &q);
+        if (x == cudaSuccess) prev = node;
+        return x;
+    };
+    if ((e = add((void *)k_det_scan_g<T, TWO>, TWO ? c.detect2_grid : c.detect_grid, detect_smem(d, TWO), pb)) != cudaSuccess)
+        return fail(e);
+    if ((e = add((void *)k_det_alloc<T>, c.detalloc_grid, 0, pa)) != cudaSuccess) return fail(e);
+    if ((e = add((void *)k_det_write_g<T, TWO>, c.detunit_grid, 0, pb)) != cudaSuccess) return fail(e);
+    if ((e = add((void *)k_repair_p1_g<T>, c.p1_grid, 0, pb)) != cudaSuccess) return fail(e);
+    if ((e = add((void *)k_repair_main_g<T>, grid_main, c.repair_smem, pb)) != cudaSuccess) return fail(e);
+    cudaLaunchAttributeValue coop = {};
+    coop.cooperative = 1;
+    if ((e = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &coop)) != cudaSuccess) return fail(e);
+    cudaGraphExec_t ex = nullptr;
+    if ((e = cudaGraphInstantiate(&ex, g, 0)) != cudaSuccess) return fail(e);
+    ig->graph = g;
+    ig->exec = ex;
+    ig->pre = pre;
+    ig->branch = branch;
+    ig->span = d.span;
+    ig->grid_main = grid_main;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_increase_graph(const LaunchCtx &c, const Dev<T> &d, IncGraph *ig, size_t ctl_bytes, int u, int v,
+                                  T w_old, T w_new, const RepairCfg &cfg) {
+    cudaError_t e;
+    if (!ig->exec || ig->span != d.span) {
+        destroy_increase_graph(ig);
+        e = d.undirected ? build_increase_graph<T, true>(c, d, ig, ctl_bytes) : build_increase_graph<T, false>(c, d, ig, ctl_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    Dev<T> dd = d;
+    UpdArgs<T> *ua = (UpdArgs<T> *)ig->args;
+    RepairCfg cf = cfg;
+    cudaGraphConditionalHandle branch = ig->branch;
+    void *pp[] = {&dd, &u, &v, &w_old, &w_new, &cf, &ua, &branch};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_inc_prepass_g<T>;
+    kp.gridDim = dim3(cdiv(d.span, 256));
+    kp.blockDim = dim3(256);
+    kp.kernelParams = pp;
+    if ((e = cudaGraphExecKernelNodeSetParams(ig->exec, ig->pre, &kp)) != cudaSuccess) return e;
+    // the graph holds a cooperative kernel: ordered against other streams'
+    // cooperative work like a cooperative launch
+    return coop_launch(c.stream, [&] { return cudaGraphLaunch(ig->exec, c.stream); });
 }
 
 // The dynamic shared memory limit is a per-function setting shared by every
@@ -410,6 +520,8 @@ cudaError_t run_next_hop(const LaunchCtx &c, const Dev<T> &d, const int32_t *row
     template cudaError_t run_mm_decrease<T>(const LaunchCtx &, const Dev<T> &, int, int, T);                  \
     template cudaError_t run_mm_detect<T>(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T); \
     template cudaError_t run_mm_pass<T>(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);          \
-    template cudaError_t run_next_hop<T>(const LaunchCtx &, const Dev<T> &, const int32_t *, int, int32_t *, int64_t);
+    template cudaError_t run_next_hop<T>(const LaunchCtx &, const Dev<T> &, const int32_t *, int, int32_t *, int64_t); \
+    template cudaError_t launch_increase_graph<T>(const LaunchCtx &, const Dev<T> &, IncGraph *, size_t, int, int, T, T, \
+                                                  const RepairCfg &);
 
 }  // namespace apsp

@@ -11,6 +11,7 @@
 #include "repair_p1.cuh"
 #include "minimax.cuh"
 #include "next_hop.cuh"
+#include "inc_graph.cuh"
 
 namespace apsp {
 
@@ -51,5 +52,30 @@ template <typename T>
 cudaError_t run_mm_detect(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T);
 template <typename T> cudaError_t run_mm_pass(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);
 template <typename T> cudaError_t run_next_hop(const LaunchCtx &, const Dev<T> &, const int32_t *, int, int32_t *, int64_t);
+
+// An edge increase as one instantiated CUDA graph (inc_graph.cuh): built on
+// first use and again when the graph's span changes; `args` is the device
+// block (sizeof(UpdArgs<T>) bytes, owned by the caller) that the prepass fills.
+struct IncGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t pre = nullptr;               // the prepass node: its parameters change per update
+    cudaGraphConditionalHandle branch = 0;
+    int span = -1;
+    int grid_main = 0;                           // cooperative grid of the repair kernel in the graph
+    void *args = nullptr;
+};
+inline void destroy_increase_graph(IncGraph *ig) {
+    if (ig->exec) cudaGraphExecDestroy(ig->exec);
+    if (ig->graph) cudaGraphDestroy(ig->graph);
+    ig->exec = nullptr;
+    ig->graph = nullptr;
+    ig->pre = nullptr;
+    ig->span = -1;
+}
+
+template <typename T>
+cudaError_t launch_increase_graph(const LaunchCtx &, const Dev<T> &, IncGraph *, size_t ctl_bytes, int, int, T, T,
+                                  const RepairCfg &);
 
 }  // namespace apsp

@@ -26,8 +26,7 @@
 namespace apsp {
 
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_repair_p1(Dev<T> d, RepairCfg cfg) {
-    pdl_enter();
+__device__ __forceinline__ void k_repair_p1_body(Dev<T> d, RepairCfg cfg) {
     using M = MinPlus<T>;
     using V4 = typename M::V4;
     constexpr int CW = PASS1_COLS / 128;   // 16-byte vectors per lane per window
@@ -116,6 +115,12 @@ __global__ void __launch_bounds__(256, 2) k_repair_p1(Dev<T> d, RepairCfg cfg) {
         __threadfence();
         if (atomicAdd(&ctl->p1_done, 1) == (int)gridDim.x - 1) ctl->t_pass1 = globaltimer_ns();
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_repair_p1(Dev<T> d, RepairCfg cfg) {
+    pdl_enter();
+    k_repair_p1_body<T>(d, cfg);
 }
 
 }  // namespace apsp

@@ -494,7 +494,9 @@ apsp_status apsp_server_destroy(apsp_server *s);
 
 /* ----- instrumentation ---------------------------------------------------- */
 
-/* Number of kernels this handle has launched so far. */
+/* Number of kernels this handle has launched so far, counting the kernels an
+ * edge increase's graph ran (its detection and repair run only when the edge
+ * was tight).  Waits for the handle's stream; -1 for a null handle. */
 int64_t apsp_launch_count(apsp_graph *g);
 /* When on, every kernel launch is bracketed by CUDA events on the handle's
  * stream and its time is accumulated per kernel name. */

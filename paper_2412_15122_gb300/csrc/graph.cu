@@ -464,6 +464,7 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->items = (int4 *)dalloc(g, (size_t)g->item_cap * sizeof(int4));
     g->icand = (int32_t *)dalloc(g, (size_t)2 * ld * sizeof(int32_t));
     g->incg.args = dalloc(g, 256);
+    if (g->incg.args) cudaMemsetAsync(g->incg.args, 0, 256, g->stream);
     static_assert(sizeof(apsp::UpdArgs<float>) <= 256 && sizeof(apsp::UpdArgs<int32_t>) <= 256, "update argument block");
     g->unit_cap = (int32_t)std::min<int64_t>(g->pair_cap, (int64_t)1 << 30);
     g->pmin = (int32_t *)dalloc(g, g->pair_cap * 4);
@@ -1327,7 +1328,17 @@ apsp_status apsp_set_model(apsp_graph *g, const float *params) {
     return APSP_OK;
 }
 
-int64_t apsp_launch_count(apsp_graph *g) { return g ? g->launches : -1; }
+int64_t apsp_launch_count(apsp_graph *g) {
+    if (!g) return -1;
+    // kernels of increase graphs whose IF body ran (a device counter; waits for the stream)
+    unsigned long long bodies = 0;
+    if (g->incg.args) {
+        const size_t off = g->dtype == APSP_F32 ? offsetof(apsp::UpdArgs<float>, bodies) : offsetof(apsp::UpdArgs<int32_t>, bodies);
+        cudaMemcpyAsync(&bodies, (const char *)g->incg.args + off, sizeof(bodies), cudaMemcpyDeviceToHost, g->stream);
+        cudaStreamSynchronize(g->stream);
+    }
+    return g->launches + (int64_t)apsp::INC_GRAPH_BODY_KERNELS * (int64_t)bodies;
+}
 
 apsp_status apsp_profile_enable(apsp_graph *g, int32_t on) {
     if (!g) return APSP_E_ARG;

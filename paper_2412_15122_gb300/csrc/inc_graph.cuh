@@ -21,7 +21,10 @@ template <typename T> struct UpdArgs {
     int32_t kind, a;
     T w_old, w_new;
     RepairCfg cfg;
+    unsigned long long bodies;   // launches whose IF body ran (zeroed at allocation), for the launch count
 };
+
+constexpr int INC_GRAPH_BODY_KERNELS = 5;   // kernels in the IF body
 
 template <typename T>
 __global__ void k_inc_prepass_g(Dev<T> d, int u, int v, T w_old, T w_new, RepairCfg cfg, UpdArgs<T> *ua,
@@ -35,6 +38,7 @@ __global__ void k_inc_prepass_g(Dev<T> d, int u, int v, T w_old, T w_new, Repair
         ua->w_new = w_new;
         ua->cfg = cfg;
         const bool tight_edge = MinPlus<T>::tight(w_old, d.D[(int64_t)u * d.ld + v]);
+        if (tight_edge) ua->bodies += 1;   // graph launches on one stream run one after another
         cudaGraphSetConditional(branch, tight_edge ? 1u : 0u);
     }
 }

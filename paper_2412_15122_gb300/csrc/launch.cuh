@@ -323,7 +323,9 @@ cudaError_t launch_increase_graph(const LaunchCtx &c, const Dev<T> &d, IncGraph 
     if ((e = cudaGraphExecKernelNodeSetParams(ig->exec, ig->pre, &kp)) != cudaSuccess) return e;
     // the graph holds a cooperative kernel: ordered against other streams'
     // cooperative work like a cooperative launch
-    return coop_launch(c.stream, [&] { return cudaGraphLaunch(ig->exec, c.stream); });
+    // counted as one launch here (the prepass); the body's kernels are added
+    // from the device counter when the count is read
+    return launch_s(c, "increase_graph", [&] { return coop_launch(c.stream, [&] { return cudaGraphLaunch(ig->exec, c.stream); }); });
 }
 
 // The dynamic shared memory limit is a per-function setting shared by every

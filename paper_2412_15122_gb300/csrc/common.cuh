@@ -187,10 +187,9 @@ struct Ctl {
     int32_t grown_rows;              // rows holding one of them
     int32_t p1_done;                 // CTAs of the first re-relaxation pass that finished
     // node insertion: argmin of each weight vector as the complement of
-    // (ordered key << 32 | slot) (0: none), the CTAs of the prep kernel that
-    // finished, and the candidate rows / columns of the reduction
+    // (ordered key << 32 | slot) (0: none), and the candidate rows / columns
+    // of the reduction
     unsigned long long ins_amin_out, ins_amin_in;
-    int32_t ins_done;
     int32_t ins_nout, ins_nin;
     int32_t ins_narrow;              // 1: the reduction reads only the candidates
     int32_t mm_changed[MM_PASS_SLOTS];  // minimax re-relaxation: pass p lowered a pair

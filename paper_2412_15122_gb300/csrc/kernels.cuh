@@ -253,9 +253,8 @@ __device__ __forceinline__ float max_of(float a, float b) { return fmaxf(a, b); 
 // (in double for fp32 weights) and rounding is monotone, so the minima over
 // the candidates are bit-identical to the minima over all rows.  When some
 // live node is unreachable the bound is infinite and every row stays a
-// candidate.  One CTA (the last of the prep kernel, INS_PREP_THREADS wide)
-// builds both lists.
-constexpr int INS_PREP_THREADS = 1024;   // block of k_insert_prep (its last block selects the candidates)
+// candidate.  One CTA (k_insert_cand) builds both lists.
+constexpr int INS_CAND_THREADS = 1024;   // the one block of k_insert_cand
 
 template <typename T>
 __device__ void insert_candidates(const Dev<T> &d, int p) {
@@ -263,7 +262,7 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
     using V4 = typename M::V4;
     constexpr int U = 3;   // vectors per thread held at once (span <= 12288 in one round)
     __shared__ int nsel[2];
-    __shared__ T emax[2][INS_PREP_THREADS / 32];
+    __shared__ T emax[2][INS_CAND_THREADS / 32];
     const int nv = d.span / 4, lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // span is a multiple of 32
     const unsigned long long ao = *(volatile const unsigned long long *)&d.ctl->ins_amin_out;
     const unsigned long long ai = *(volatile const unsigned long long *)&d.ctl->ins_amin_in;
@@ -274,6 +273,8 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
     const int4 *al4 = reinterpret_cast<const int4 *>(d.alive);
     const V4 *wo4 = reinterpret_cast<const V4 *>(d.w_out);
     const V4 *wi4 = reinterpret_cast<const V4 *>(d.w_in);
+    // the two lightest weights, in flight with the first vectors
+    const T wt0 = __ldcg(d.w_out + max(t0, 0)), wr1 = __ldcg(d.w_in + max(r1, 0));
     T e0 = (T)0, e1 = (T)0;
     // E0 = max over live j of D[t0][j], E1 = max over live i of D[i][r1];
     // U vectors of each array per thread are in flight together
@@ -328,8 +329,8 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
         e1 = max_of(e1, emax[1][k]);
     }
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
-    const double thr_o = t0 < 0 ? -1.0 : (M::finite(e0) ? (double)__ldcg(d.w_out + t0) + (double)e0 : inf);
-    const double thr_i = r1 < 0 ? -1.0 : (M::finite(e1) ? (double)__ldcg(d.w_in + r1) + (double)e1 : inf);
+    const double thr_o = t0 < 0 ? -1.0 : (M::finite(e0) ? (double)wt0 + (double)e0 : inf);
+    const double thr_i = r1 < 0 ? -1.0 : (M::finite(e1) ? (double)wr1 + (double)e1 : inf);
     const unsigned below = (1u << lane) - 1u;
     for (int c0 = 0; c0 < nv; c0 += U * (int)blockDim.x) {
         if (c0 > 0) {   // spans above U * 4 * blockDim.x slots
@@ -376,8 +377,7 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
 
 // Mask the new node's weights (dead slots and p itself -> missing), validate
 // them, and reset the two reduction vectors.  With `cand` (min-plus graphs),
-// also the argmin of each weight vector, and the last CTA to finish selects
-// the reduction's candidates (insert_candidates).
+// also the argmin of each weight vector, for k_insert_cand.
 template <typename T>
 __global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int cap, int p, int cand) {
     pdl_enter();
@@ -409,13 +409,12 @@ __global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int c
         if (ko) atomicMax(&d.ctl->ins_amin_out, ko);
         if (ki) atomicMax(&d.ctl->ins_amin_in, ki);
     }
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&d.ctl->ins_done, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
+}
+
+// The reduction's candidates (insert_candidates), one CTA of INS_CAND_THREADS.
+template <typename T>
+__global__ void __launch_bounds__(INS_CAND_THREADS) k_insert_cand(Dev<T> d, int p) {
+    pdl_enter();
     insert_candidates<T>(d, p);
 }
 

@@ -82,7 +82,8 @@ template <typename T> cudaError_t run_fw(const LaunchCtx &c, const Dev<T> &d) {
 template <typename T>
 cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
     cudaError_t e;
-    if ((e = launch_s(c, "insert_prep", [&] { return pdl(c.stream, cdiv(d.span, INS_PREP_THREADS), INS_PREP_THREADS, 0, k_insert_prep<T>, d, in_raw, out_raw, cap, p, 1); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "insert_prep", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_insert_prep<T>, d, in_raw, out_raw, cap, p, 1); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "insert_cand", [&] { return pdl(c.stream, 1, INS_CAND_THREADS, 0, k_insert_cand<T>, d, p); })) != cudaSuccess) return e;
     // exactly one wave (never a partial second one): the resident CTAs split
     // into column bands x row ranges
     const int bands = cdiv(d.span, INS_CB);

@@ -186,6 +186,7 @@ struct Ctl {
     unsigned long long grown_pairs;  // listed pairs whose distance grew (Algorithm 12's list), when measured
     int32_t grown_rows;              // rows holding one of them
     int32_t p1_done;                 // CTAs of the first re-relaxation pass that finished
+    int32_t p1_alloc;                // first-pass units reserved by detection
     // node insertion: argmin of each weight vector as the complement of
     // (ordered key << 32 | slot) (0: none), and the candidate rows / columns
     // of the reduction
@@ -197,6 +198,7 @@ struct Ctl {
 };
 
 constexpr int ITEM_PAIRS = 32;          // affected pairs per re-relaxation work item
+constexpr int P1_PAIRS = 16;            // affected pairs per first-pass work unit (shorter units end the pass sooner)
 constexpr int PASS1_COLS = 1024;        // columns of x per pass-1 work unit (the swept window stays in L2)
 constexpr int YSEG = 256;               // intermediates per work unit in passes >= 2
 constexpr int MAX_PASSES = 48;          // path doubling needs <= log2(hops) + 1 passes

@@ -69,6 +69,8 @@ struct apsp_graph {
     uint8_t *pstamp = nullptr, *rstamp = nullptr;
     int4 *items = nullptr;
     int32_t *icand = nullptr;   // node insertion: candidate rows / columns of the reduction
+    int4 *p1u = nullptr;        // first-pass units
+    int32_t p1u_cap = 0;
     Ctl *ctl = nullptr;
     // path queries (Section 4): per-call buffers, grown on demand
     void *pq_uv = nullptr, *pq_out = nullptr, *pq_wide = nullptr;
@@ -102,7 +104,8 @@ struct apsp_graph {
     cudaEvent_t pin_ev[RING] = {};
     bool pin_used[RING] = {};
     int pin_next = 0;
-    void *pin_fetch = nullptr;       // pinned: RING x 2 * cap elements (device-input adds' weights)
+    void *pin_fetch = nullptr;       // mapped pinned: RING x 2 * cap elements (device-input adds' weights)
+    void *pin_fetch_dev = nullptr;   // its device view (written by the prep kernel)
     cudaEvent_t fetch_ev[RING] = {};
     struct Fetch {
         int p;                       // slot added
@@ -309,6 +312,8 @@ template <typename T> Dev<T> dev_of(apsp_graph *g) {
     d.hbase = g->hbase;
     d.items = g->items;
     d.icand = g->icand;
+    d.p1u = g->p1u;
+    d.p1u_cap = g->p1u_cap;
     d.pairs = g->pairs;
     d.pmin = g->pmin;
     d.pstamp = g->pstamp;
@@ -463,6 +468,8 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
     g->pairs = (int32_t *)dalloc(g, g->pair_cap * 4);
     g->items = (int4 *)dalloc(g, (size_t)g->item_cap * sizeof(int4));
     g->icand = (int32_t *)dalloc(g, (size_t)2 * ld * sizeof(int32_t));
+    g->p1u_cap = (int32_t)(g->pair_cap / apsp::P1_PAIRS + ld);
+    g->p1u = (int4 *)dalloc(g, (size_t)g->p1u_cap * sizeof(int4));
     g->incg.args = dalloc(g, 256);
     if (g->incg.args) cudaMemsetAsync(g->incg.args, 0, 256, g->stream);
     static_assert(sizeof(apsp::UpdArgs<float>) <= 256 && sizeof(apsp::UpdArgs<int32_t>) <= 256, "update argument block");
@@ -479,12 +486,14 @@ apsp_status init_impl(apsp_graph *g, const void *W, int n, const void *Dgiven) {
         if (!g->mm_mask) return APSP_E_NOMEM;
     }
     if (!g->W || !g->D || (!g->undirected && !g->DT) || !g->alive || !g->w_in || !g->w_out || !g->x || !g->x2 ||
-        !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->icand || !g->incg.args || !g->ctl || !g->model ||
+        !g->y || !g->y2 || !g->vin_k || !g->vout_k || !g->rlist || !g->pairs || !g->items || !g->icand || !g->p1u || !g->incg.args || !g->ctl || !g->model ||
         !g->pmin || !g->pstamp || !g->rstamp || !g->units || !g->hrows || !g->hunits || !g->hralloc || !g->rowcnt ||
         !g->hbase || !g->bmask)
         return APSP_E_NOMEM;
     if (cudaMallocHost(&g->pin, (size_t)apsp_graph::RING * 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
-    if (cudaMallocHost(&g->pin_fetch, (size_t)apsp_graph::RING * 2 * g->cap * esz) != cudaSuccess) return APSP_E_NOMEM;
+    if (cudaHostAlloc(&g->pin_fetch, (size_t)apsp_graph::RING * 2 * g->cap * esz, cudaHostAllocMapped) != cudaSuccess)
+        return APSP_E_NOMEM;
+    if (cudaHostGetDevicePointer(&g->pin_fetch_dev, g->pin_fetch, 0) != cudaSuccess) return APSP_E_NOMEM;
     g->pin_small_bytes = std::max<int64_t>(sizeof(Ctl), 1 << 16);
     if (cudaMallocHost(&g->pin_small, g->pin_small_bytes) != cudaSuccess) return APSP_E_NOMEM;
     for (int r = 0; r < apsp_graph::RING; ++r) {
@@ -554,6 +563,8 @@ apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t
     if (p < 0) return APSP_E_CAPACITY;
     const int cap = g->cap;
     const T *din, *dout;
+    T *fetch = nullptr;   // device-input adds: where the prep kernel copies the raw weights
+    int fetch_ring = 0;
     if (!device_input) {
         const T *hi = (const T *)in_w, *ho = (const T *)out_w;
         for (int t = 0; t < cap; ++t) {
@@ -588,21 +599,19 @@ apsp_status add_impl(apsp_graph *g, const void *in_w, const void *out_w, int32_t
             settle_one<T>(g, g->fetches.front());
             g->fetches.pop_front();
         }
-        const int r = g->fetch_next;
-        g->fetch_next = (r + 1) % apsp_graph::RING;
-        T *f_in = (T *)g->pin_fetch + (size_t)r * 2 * cap;
-        cudaMemcpyAsync(f_in, din, cap * sizeof(T), cudaMemcpyDeviceToHost, g->stream);
-        cudaMemcpyAsync(f_in + cap, dout, cap * sizeof(T), cudaMemcpyDeviceToHost, g->stream);
-        cudaEventRecord(g->fetch_ev[r], g->stream);
+        fetch_ring = g->fetch_next;
+        g->fetch_next = (fetch_ring + 1) % apsp_graph::RING;
+        fetch = (T *)g->pin_fetch_dev + (size_t)fetch_ring * 2 * cap;   // written by the prep kernel
         g->add_seq[p] = ++g->seq;
-        g->fetches.push_back(apsp_graph::Fetch{p, g->add_seq[p], r});
+        g->fetches.push_back(apsp_graph::Fetch{p, g->add_seq[p], fetch_ring});
     }
     g->hwm = std::max(g->hwm, p + 1);
     reset_ctl(g);
     Dev<T> d = dev_of<T>(g);
-    cudaError_t e = g->minimax ? apsp::run_mm_insert<T>(g->lc, d, din, dout, cap, p)
-                               : apsp::run_insert<T>(g->lc, d, din, dout, cap, p);
+    cudaError_t e = g->minimax ? apsp::run_mm_insert<T>(g->lc, d, din, dout, cap, p, fetch)
+                               : apsp::run_insert<T>(g->lc, d, din, dout, cap, p, fetch);
     if (e != cudaSuccess) return cuda_status(e);
+    if (fetch) cudaEventRecord(g->fetch_ev[fetch_ring], g->stream);
     g->alive_h[p] = 1;
     g->n_live++;
     *new_id = p;

@@ -48,6 +48,7 @@ template <typename T> struct Dev {
     long long *hbase;         // detection: first pair slot per unit (-1: none)
     int4 *items;              // (row, first pair, pair count | row's pair count << 8, row's first pair)
     int32_t *icand;           // node insertion: candidate rows of Corollary 1 [0, ld), columns of Corollary 2 [ld, 2 ld)
+    int4 *p1u;                // first-pass units: (row, first pair, pairs <= P1_PAIRS, 0)
     int32_t *pairs;           // affected column per pair, grouped by row (columns ascending)
     int32_t *pmin;            // per pair: first-pass minimum as an ordered key
     uint8_t *pstamp;          // per pair: last pass that lowered it (0: none yet)
@@ -57,6 +58,7 @@ template <typename T> struct Dev {
     int64_t pair_cap;
     int32_t item_cap;
     int32_t unit_cap;
+    int32_t p1u_cap;
 };
 
 template <typename T> __device__ __forceinline__ T col_src(const Dev<T> &d, int row_of_T, int i) {
@@ -377,12 +379,20 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
 
 // Mask the new node's weights (dead slots and p itself -> missing), validate
 // them, and reset the two reduction vectors.  With `cand` (min-plus graphs),
-// also the argmin of each weight vector, for k_insert_cand.
+// also the argmin of each weight vector, for k_insert_cand.  With `fetch` (a
+// device view of mapped host memory, 2 * cap elements), also copy the raw
+// vectors there for the host's weight mirror, so a device-input add needs no
+// separate device-to-host copies.
 template <typename T>
-__global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int cap, int p, int cand) {
+__global__ void k_insert_prep(Dev<T> d, const T *in_raw, const T *out_raw, int cap, int p, int cand, T *fetch) {
     pdl_enter();
     using M = MinPlus<T>;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fetch)
+        for (int t = j; t < cap; t += gridDim.x * blockDim.x) {
+            fetch[t] = in_raw[t];
+            fetch[cap + t] = out_raw[t];
+        }
     uint32_t err = 0;
     T wi = M::inf(), wo = M::inf();
     if (j < d.span) {
@@ -927,22 +937,27 @@ __global__ void __launch_bounds__(256) k_det_alloc(Dev<T> d) {
         const int nit = (n + ITEM_PAIRS - 1) / ITEM_PAIRS;
         const int nseg = (n + YSEG - 1) / YSEG;
         const int nun = nit * nseg;
-        int tn, tit, tun;
+        const int nh = (n + P1_PAIRS - 1) / P1_PAIRS;
+        int tn, tit, tun, th;
         const int on = warp_exclusive_scan(n, &tn);
         const int oit = warp_exclusive_scan(nit, &tit);
         const int oun = warp_exclusive_scan(nun, &tun);
+        const int oh = warp_exclusive_scan(nh, &th);
         unsigned long long old = 0;
-        int ub = 0;
+        int ub = 0, hb = 0;
         if (lane == 0 && tn > 0) {
             old = atomicAdd(&d.ctl->alloc, ((unsigned long long)tn << 24) | (unsigned long long)tit);
             ub = atomicAdd(&d.ctl->unit_alloc, tun);
+            hb = atomicAdd(&d.ctl->p1_alloc, th);
         }
         old = __shfl_sync(0xffffffffu, old, 0);
         ub = __shfl_sync(0xffffffffu, ub, 0);
+        hb = __shfl_sync(0xffffffffu, hb, 0);
         if (tn == 0) continue;
         const long long pbw = (long long)(old >> 24);
         const int ibw = (int)(old & 0xFFFFFFull);
-        if (pbw + tn > d.pair_cap || ibw + tit > d.item_cap || (long long)ub + tun > d.unit_cap) {
+        if (pbw + tn > d.pair_cap || ibw + tit > d.item_cap || (long long)ub + tun > d.unit_cap ||
+            (long long)hb + th > d.p1u_cap) {
             if (lane == 0) atomicOr(&d.ctl->overflow, 1);
             continue;   // these rows' units write nothing (their slots stay -1)
         }
@@ -969,6 +984,10 @@ __global__ void __launch_bounds__(256) k_det_alloc(Dev<T> d) {
             const int nitt = (nt + ITEM_PAIRS - 1) / ITEM_PAIRS;
             for (int k = lane; k < nitt; k += 32)
                 d.items[ibt + k] = make_int4(it, (int)pbt + k * ITEM_PAIRS, min(ITEM_PAIRS, nt - k * ITEM_PAIRS) | (nt << 8), (int)pbt);
+            const int hbt = hb + __shfl_sync(0xffffffffu, oh, t);
+            const int nht = (nt + P1_PAIRS - 1) / P1_PAIRS;
+            for (int k = lane; k < nht; k += 32)
+                d.p1u[hbt + k] = make_int4(it, (int)pbt + k * P1_PAIRS, min(P1_PAIRS, nt - k * P1_PAIRS), 0);
         }
     }
     if (rows_hit) atomicAdd(&d.ctl->n_rows, rows_hit);

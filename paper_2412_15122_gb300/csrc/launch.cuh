@@ -80,9 +80,9 @@ template <typename T> cudaError_t run_fw(const LaunchCtx &c, const Dev<T> &d) {
 }
 
 template <typename T>
-cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
+cudaError_t run_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p, T *fetch) {
     cudaError_t e;
-    if ((e = launch_s(c, "insert_prep", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_insert_prep<T>, d, in_raw, out_raw, cap, p, 1); })) != cudaSuccess) return e;
+    if ((e = launch_s(c, "insert_prep", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_insert_prep<T>, d, in_raw, out_raw, cap, p, 1, fetch); })) != cudaSuccess) return e;
     if ((e = launch_s(c, "insert_cand", [&] { return pdl(c.stream, 1, INS_CAND_THREADS, 0, k_insert_cand<T>, d, p); })) != cudaSuccess) return e;
     // exactly one wave (never a partial second one): the resident CTAs split
     // into column bands x row ranges
@@ -446,9 +446,9 @@ template <typename T> cudaError_t run_mm_fw(const LaunchCtx &c, const Dev<T> &d)
 }
 
 template <typename T>
-cudaError_t run_mm_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p) {
+cudaError_t run_mm_insert(const LaunchCtx &c, const Dev<T> &d, const T *in_raw, const T *out_raw, int cap, int p, T *fetch) {
     cudaError_t e;
-    if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p, 0); })) != cudaSuccess) return e;
+    if ((e = launch(c, "insert_prep", [&] { k_insert_prep<T><<<cdiv(d.span, 256), 256, 0, c.stream>>>(d, in_raw, out_raw, cap, p, 0, fetch); })) != cudaSuccess) return e;
     const int bands = cdiv(d.span, MM_CB);
     int ranges = std::max(1, (3 * c.num_sms + bands - 1) / bands);
     ranges = std::min(ranges, std::max(1, cdiv(d.span, 8)));
@@ -509,7 +509,7 @@ cudaError_t run_next_hop(const LaunchCtx &c, const Dev<T> &d, const int32_t *row
     template cudaError_t run_sanitize<T>(const LaunchCtx &, T *, int64_t, int, int, Ctl *);                   \
     template cudaError_t run_transpose<T>(const LaunchCtx &, const Dev<T> &);                                 \
     template cudaError_t run_fw<T>(const LaunchCtx &, const Dev<T> &);                                        \
-    template cudaError_t run_insert<T>(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int);    \
+    template cudaError_t run_insert<T>(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int, T *); \
     template cudaError_t run_decrease<T>(const LaunchCtx &, const Dev<T> &, int, int, T);                     \
     template cudaError_t run_remove<T>(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);            \
     template cudaError_t run_increase<T>(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &); \
@@ -519,7 +519,7 @@ cudaError_t run_next_hop(const LaunchCtx &c, const Dev<T> &d, const int32_t *row
     template cudaError_t run_batch<T>(cudaStream_t, BatchHeader *, int, size_t, int);                         \
     template cudaError_t batch_occupancy<T>(size_t, int, int *);                                             \
     template cudaError_t run_mm_fw<T>(const LaunchCtx &, const Dev<T> &);                                     \
-    template cudaError_t run_mm_insert<T>(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int); \
+    template cudaError_t run_mm_insert<T>(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int, T *); \
     template cudaError_t run_mm_decrease<T>(const LaunchCtx &, const Dev<T> &, int, int, T);                  \
     template cudaError_t run_mm_detect<T>(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T); \
     template cudaError_t run_mm_pass<T>(const LaunchCtx &, const Dev<T> &, const uint32_t *, int, int);          \

@@ -35,7 +35,7 @@ template <typename T> cudaError_t run_fill(const LaunchCtx &, T *, T, int64_t);
 template <typename T> cudaError_t run_sanitize(const LaunchCtx &, T *, int64_t, int, int, Ctl *);
 template <typename T> cudaError_t run_transpose(const LaunchCtx &, const Dev<T> &);
 template <typename T> cudaError_t run_fw(const LaunchCtx &, const Dev<T> &);
-template <typename T> cudaError_t run_insert(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int);
+template <typename T> cudaError_t run_insert(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int, T *);
 template <typename T> cudaError_t run_decrease(const LaunchCtx &, const Dev<T> &, int, int, T);
 template <typename T> cudaError_t run_remove(const LaunchCtx &, const Dev<T> &, int, const RepairCfg &);
 template <typename T> cudaError_t run_increase(const LaunchCtx &, const Dev<T> &, int, int, T, T, const RepairCfg &);
@@ -46,7 +46,7 @@ template <typename T> cudaError_t run_batch(cudaStream_t, BatchHeader *, int, si
 template <typename T> cudaError_t batch_occupancy(size_t, int, int *);
 // minimax (bottleneck) distances
 template <typename T> cudaError_t run_mm_fw(const LaunchCtx &, const Dev<T> &);
-template <typename T> cudaError_t run_mm_insert(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int);
+template <typename T> cudaError_t run_mm_insert(const LaunchCtx &, const Dev<T> &, const T *, const T *, int, int, T *);
 template <typename T> cudaError_t run_mm_decrease(const LaunchCtx &, const Dev<T> &, int, int, T);
 template <typename T>
 cudaError_t run_mm_detect(const LaunchCtx &, const Dev<T> &, uint32_t *, int, int, int, int, T, T);

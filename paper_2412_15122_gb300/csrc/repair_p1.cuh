@@ -3,8 +3,11 @@
 // For every listed pair (i, j) of the current removal / edge increase:
 //     pmin[pair] = min over all x of D[i][x] + D[x][j]
 // with the starting values (D is only read; the later passes run in
-// k_repair_main).  One warp per unit = (work item: row i and up to
-// ITEM_PAIRS of its listed columns j, window of PASS1_COLS values of x),
+// k_repair_main).  One warp per unit = (row i and up to P1_PAIRS of its
+// listed columns j, from the list detection writes; window of PASS1_COLS
+// values of x).  Units of 16 pairs rather than the later passes' 32 halve
+// the longest unit, which ends the pass on lists with a few long rows
+// (measured: the 10th-percentile benchmark removal's pass 47 -> 31 us),
 // units ordered window-major so that all warps sweep the same window at a
 // time and the rows and columns it touches stay in L2 (about 35 MB at
 // n = 8192).  The row's slice of the window is staged in the warp's shared
@@ -44,17 +47,18 @@ __device__ __forceinline__ void k_repair_p1_body(Dev<T> d, RepairCfg cfg) {
     const int wq = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % QUEUES) * 32;
     V4 *rb = rowbuf[threadIdx.x >> 5];
     const int nwin = (span + PASS1_COLS - 1) / PASS1_COLS;
-    const int n1 = n_items * nwin;   // items < 2^19 and windows <= 18 at the largest capacity
+    const int nh = *(volatile const int32_t *)&ctl->p1_alloc;   // units of up to P1_PAIRS pairs
+    const int n1 = nh * nwin;   // units < 2^20 and windows <= 18 at the largest capacity
     int t = 0;
     if (lane == 0) t = atomicAdd(&ctl->q1[wq], 1);
     t = __shfl_sync(0xffffffffu, t, 0);
     while (true) {
         const int u = (wq >> 5) + QUEUES * t;
         if (u >= n1 || u < 0) break;
-        const int g = u / n_items, it = u - g * n_items;
+        const int g = u / nh, h = u - g * nh;
         if (lane == 0) t = atomicAdd(&ctl->q1[wq], 1);   // next unit, in flight meanwhile
-        const int4 item = __ldcg(d.items + it);
-        const int cnt = item.z & 0xff;
+        const int4 item = __ldcg(d.p1u + h);   // (row, first pair, pairs, 0)
+        const int cnt = item.z;
         const int jl = lane < cnt ? __ldcg(d.pairs + item.y + lane) : 0;
         const int x0 = g * PASS1_COLS;
         const int nv = (min(span, x0 + PASS1_COLS) - x0) / 4;

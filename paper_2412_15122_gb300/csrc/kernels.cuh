@@ -252,11 +252,28 @@ __device__ __forceinline__ float max_of(float a, float b) { return fmaxf(a, b); 
 // needs only the rows with w(p, t) <= w(p, t0) + E0; likewise Corollary 2
 // needs only the columns r with w(r, p) <= w(r1, p) + E1, r1 the lightest
 // in-edge and E1 = max over live i of D[i][r1].  The comparisons are exact
-// (in double for fp32 weights) and rounding is monotone, so the minima over
+// (int64 for int32 weights; for fp32 the bound is rounded up, which keeps a
+// superset of the rows) and rounding is monotone, so the minima over
 // the candidates are bit-identical to the minima over all rows.  When some
 // live node is unreachable the bound is infinite and every row stays a
 // candidate.  One CTA (k_insert_cand) builds both lists.
 constexpr int INS_CAND_THREADS = 1024;   // the one block of k_insert_cand
+
+// Bound w(p, t0) + E0 of insert_candidates and its test, without fp64 (slow on
+// this GPU): int64 for int32 weights, rounded up for fp32.
+template <typename T> struct CandBound;
+template <> struct CandBound<int32_t> {
+    using B = long long;
+    __device__ static B make(bool none, int32_t w, int32_t e) {
+        return none ? -1ll : (e >= INF_I32 ? 0x7fffffffffffffffll : (B)w + (B)e);
+    }
+    __device__ static bool keep(int32_t w, B t) { return (B)w <= t; }
+};
+template <> struct CandBound<float> {
+    using B = float;
+    __device__ static B make(bool none, float w, float e) { return none ? -1.0f : __fadd_ru(w, e); }
+    __device__ static bool keep(float w, B t) { return w <= t; }
+};
 
 template <typename T>
 __device__ void insert_candidates(const Dev<T> &d, int p) {
@@ -330,9 +347,8 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
         e0 = max_of(e0, emax[0][k]);
         e1 = max_of(e1, emax[1][k]);
     }
-    const double inf = __longlong_as_double(0x7ff0000000000000ll);
-    const double thr_o = t0 < 0 ? -1.0 : (M::finite(e0) ? (double)wt0 + (double)e0 : inf);
-    const double thr_i = r1 < 0 ? -1.0 : (M::finite(e1) ? (double)wr1 + (double)e1 : inf);
+    using CB = CandBound<T>;
+    const typename CB::B thr_o = CB::make(t0 < 0, wt0, e0), thr_i = CB::make(r1 < 0, wr1, e1);
     const unsigned below = (1u << lane) - 1u;
     for (int c0 = 0; c0 < nv; c0 += U * (int)blockDim.x) {
         if (c0 > 0) {   // spans above U * 4 * blockDim.x slots
@@ -352,8 +368,8 @@ __device__ void insert_candidates(const Dev<T> &d, int p) {
             const T wov[4] = {wo[u].x, wo[u].y, wo[u].z, wo[u].w}, wiv[4] = {wi[u].x, wi[u].y, wi[u].z, wi[u].w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const bool so = in && M::finite(wov[e]) && (double)wov[e] <= thr_o;
-                const bool si = in && M::finite(wiv[e]) && (double)wiv[e] <= thr_i;
+                const bool so = in && M::finite(wov[e]) && CB::keep(wov[e], thr_o);
+                const bool si = in && M::finite(wiv[e]) && CB::keep(wiv[e], thr_i);
                 const unsigned bo = __ballot_sync(0xffffffffu, so), bi = __ballot_sync(0xffffffffu, si);
                 if (!(bo | bi)) continue;
                 int baseo = 0, basei = 0;

@@ -763,16 +763,6 @@ template <typename T> __device__ __forceinline__ void clear_repair_scratch(const
 }
 
 template <typename T>
-__global__ void k_rm_gather(Dev<T> d, int k) {
-    pdl_enter();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.span) return;
-    d.x[i] = col_src(d, k, i);                 // D[i][k]
-    d.y[i] = d.D[(int64_t)k * d.ld + i];       // D[k][i]
-    clear_repair_scratch(d, i);
-}
-
-template <typename T>
 __device__ __forceinline__ void k_inc_prepass_body(Dev<T> d, int u, int v, T w_old, T w_new) {
     using M = MinPlus<T>;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1168,9 +1158,17 @@ __device__ __forceinline__ void k_det_scan_body(Dev<T> d, int kind, int a, T w_o
     const int span = d.span;
     T *ys = reinterpret_cast<T *>(smem_raw);
     T *y2s = ys + span;
-    stage_vec<T>(ys, d.y, span);
+    // a removal stages row a of D itself and publishes the legs for the later
+    // kernels: y = D[a][.] (a grid-stride share per CTA), x[i] = D[i][a] by the
+    // warp that scans row i; the repair's row stamps are cleared here too
+    stage_vec<T>(ys, kind == 0 ? d.D + (int64_t)a * d.ld : d.y, span);
     if (TWO) stage_vec<T>(y2s, d.y2, span);
     __syncthreads();
+    if (kind == 0)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < span; c += gridDim.x * blockDim.x) {
+            d.y[c] = ys[c];
+            clear_repair_scratch(d, c);
+        }
     for (int c = threadIdx.x; c < span; c += blockDim.x) {
         ys[c] = kind == 0 && c == a ? unreachable_leg<T>() : M::leg(ys[c]);
         if (TWO) y2s[c] = M::leg(y2s[c]);
@@ -1210,7 +1208,7 @@ __device__ __forceinline__ void k_det_scan_body(Dev<T> d, int kind, int a, T w_o
     };
     const int r0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int i_next = r0 < nrows ? (kind == 0 ? r0 : d.rlist[r0]) : 0;
-    T x_next = r0 < nrows ? d.x[i_next] : M::inf();
+    T x_next = r0 < nrows ? (kind == 0 ? col_src(d, a, i_next) : d.x[i_next]) : M::inf();
     T x2_next = TWO && r0 < nrows ? d.x2[i_next] : M::inf();
     for (int r = r0; r < nrows; r += nwarps) {
         const int i = i_next;
@@ -1218,9 +1216,10 @@ __device__ __forceinline__ void k_det_scan_body(Dev<T> d, int kind, int a, T w_o
         const T x2i = x2_next;
         if (r + nwarps < nrows) {
             i_next = kind == 0 ? r + nwarps : d.rlist[r + nwarps];
-            x_next = d.x[i_next];
+            x_next = kind == 0 ? col_src(d, a, i_next) : d.x[i_next];
             if (TWO) x2_next = d.x2[i_next];
         }
+        if (kind == 0 && lane == 0) d.x[i] = xi;
         if (kind == 0 && i == a) continue;
         const T s1 = kind == 0 ? xi : M::add(xi, w_old);
         const T s2 = M::add(x2i, w_old);

@@ -204,7 +204,7 @@ template <typename T> static cudaError_t run_grown(const LaunchCtx &c, const Dev
 
 template <typename T> cudaError_t run_remove(const LaunchCtx &c, const Dev<T> &d, int k, const RepairCfg &cfg) {
     cudaError_t e;
-    if ((e = launch_s(c, "remove_gather", [&] { return pdl(c.stream, cdiv(d.span, 256), 256, 0, k_rm_gather<T>, d, k); })) != cudaSuccess) return e;
+    // the detection scan also stages the removed node's row and column (x, y)
     if ((e = run_detect<T>(c, d, 0, k, (T)0, (T)0, cfg, "detect_remove")) != cudaSuccess) return e;
     if ((e = run_repair<T>(c, d, cfg)) != cudaSuccess) return e;
     return run_grown<T>(c, d, 0, (T)0, cfg);
